@@ -1,0 +1,192 @@
+/*
+ * mips.h -- C ABI of libmips: exact batch top-K maximum inner product
+ * search on one GB300 GPU (sm_103a).
+ *
+ * The operation (Sec. III-A, "Problem Statement: Batch Exact MIPS"): given
+ * user vectors U (|U| x f) and item vectors I (|I| x f), return for every
+ * user u the K items i with the largest u^T i.
+ *
+ * Result semantics shared by every entry point below:
+ *   - out_idx[u * K + k] (int32) and out_score[u * K + k] (double) list the
+ *     user's K best items, best first.  Items rank by u^T i of the FP32
+ *     inputs, descending; equal scores rank by the smaller item index.
+ *   - Indices equal those of the FP64 definition (sequential sum of the
+ *     exact FP32 products, full sort per user) exactly, ties included:
+ *     whenever two candidates are closer than the rescore's error bound the
+ *     library recomputes them with exactly that FP64 arithmetic.
+ *   - Scores are the exact inner product to within 2e-10 relative to
+ *     ||u|| ||i|| (compensated FP32 arithmetic), or the FP64 definition's
+ *     value itself for users resolved by the tie check.
+ *
+ * Conventions:
+ *   - Matrices are row-major FP32, row r at ptr + r * f.
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are asynchronous on it; argument errors return at
+ *     once, device-side errors (non-finite input, a timed-out wait) are
+ *     reported by mips_sync() or by the next call on the same index.
+ *   - Device pointers must be valid on the index's device until the stream
+ *     has reached the end of the call.  The caller owns every buffer it
+ *     passes; the index owns its own copies and workspace.
+ *   - An index is not thread-safe: serialise calls on one handle.
+ *   - No C++ exception crosses this boundary.
+ *   - Status codes: MIPS_ERR_ARG for null pointers, n <= 0, f < 1,
+ *     K < 1 or K > n_items, unsupported sizes; MIPS_ERR_NOMEM when device
+ *     memory runs out; MIPS_ERR_CUDA for any other CUDA failure;
+ *     MIPS_ERR_NONFINITE when an input row holds NaN or Inf;
+ *     MIPS_ERR_TIMEOUT when a bounded wait in a kernel gave up.
+ *     mips_last_error() returns a message for the calling thread.
+ */
+#ifndef MIPS_H_
+#define MIPS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mips_index_s* mips_index_t; /* opaque; owned by the library */
+
+typedef enum {
+  MIPS_OK = 0,
+  MIPS_ERR_ARG = 1,
+  MIPS_ERR_NOMEM = 2,
+  MIPS_ERR_CUDA = 3,
+  MIPS_ERR_TIMEOUT = 4,
+  MIPS_ERR_OVERFLOW = 5,
+  MIPS_ERR_UNIMPLEMENTED = 6,
+  MIPS_ERR_NONFINITE = 7
+} mips_status;
+
+/* Arithmetic of the candidate (filter) pass of the blocked multiply. */
+typedef enum {
+  MIPS_FP32 = 0,     /* FP32 CUDA-core dot products */
+  MIPS_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
+  MIPS_FP8_E4M3 = 2  /* reserved */
+} mips_dtype;
+
+typedef struct {
+  int dtype;          /* mips_dtype of the candidate pass (default MIPS_BF16) */
+  int kmeans_iters;   /* Lloyd iterations for Maximus (Sec. IV-E: i = 3) */
+  int block_items;    /* Maximus item block B; 0 = library default */
+  double sample_frac; /* Optimus user sample fraction (Sec. V: 0.005) */
+  int autotune;       /* reserved */
+  uint64_t seed;      /* seed of the k-means initial centroids and samples */
+} mips_options;
+
+/* Fill *opt with the defaults listed above. */
+void mips_default_options(mips_options* opt);
+
+/*
+ * Build an index over n_items item vectors of dimension f
+ * (items_dev: device FP32 [n_items][f]; read during the call only).
+ * clusters = |C| for Maximus (Sec. IV-A; Algorithm 1 input "# clusters"),
+ * fixed here and used by mips_topk_maximus.  The index copies the items
+ * (FP32 master + quantised copies + per-item bounds); the caller may free
+ * items_dev once the stream has passed this call.
+ * Limits: 1 <= f <= 128, 1 <= n_items < 2^31, 1 <= clusters <= 4096.
+ * *out receives the handle; free it with mips_free_index.
+ */
+mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int clusters,
+                             const mips_options* opt, void* stream, mips_index_t* out);
+
+/*
+ * Blocked matrix multiply with fused top-K selection (Sec. III-B, "BMM"):
+ * every user against every item, nothing pruned.
+ * users_dev: device FP32 [n_users][f]; out_idx_dev: device int32
+ * [n_users][K]; out_score_dev: device double [n_users][K].
+ * 1 <= K <= min(n_items, 128).
+ */
+mips_status mips_topk(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                      int32_t* out_idx_dev, double* out_score_dev, void* stream);
+
+/*
+ * The Maximus index (Sec. IV, Algorithm 1): cluster these users with
+ * k-means into the index's |C| clusters, compute theta_b per cluster and
+ * the per-cluster item lists ordered by CBound (Eq. appx_bound), then walk
+ * each cluster's list in blocks for all of its users, stopping when no
+ * remaining item can enter any user's top-K.  Same arguments and result
+ * as mips_topk; the result is identical to mips_topk's (Theorem "exact").
+ */
+mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                              int32_t* out_idx_dev, double* out_score_dev, void* stream);
+
+/* Report of one Optimus decision (Sec. V, "Overhead of Optimizer"). */
+typedef struct {
+  int choice;           /* 0 = blocked multiply, 1 = Maximus */
+  double t_build;       /* C_I: seconds of Maximus construction on the sample */
+  double q_user;        /* Q_I: Maximus seconds per user (sample) */
+  double m_user;        /* M_I: blocked-multiply seconds per user (sample) */
+  int64_t sample_users; /* s */
+  double est_index;     /* predicted seconds: C_I + n * Q_I */
+  double est_bmm;       /* predicted seconds: n * M_I */
+} mips_select_report;
+
+/*
+ * Optimus (Sec. V): time a random user sample on both paths, extrapolate
+ * to all users, finish the remaining users with the faster one and reuse
+ * the sample's results.  Full results land in out_idx_dev/out_score_dev.
+ * This call synchronises the stream (it reads the sample's timings).
+ * rep may be NULL.
+ */
+mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                        int32_t* out_idx_dev, double* out_score_dev, void* stream,
+                        mips_select_report* rep);
+
+/*
+ * Host-memory variant of mips_topk (method 0) / mips_topk_maximus
+ * (method 1) / mips_select (method 2): copies users_host to the device,
+ * runs the method and copies the results back, all on `stream`, then
+ * synchronises it.  Host buffers are used as given (pinned memory gives
+ * asynchronous copies).  Same result semantics as the device entry points.
+ */
+mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_users, int K,
+                           int method, int32_t* out_idx_host, double* out_score_host,
+                           void* stream);
+
+/* Wait for `stream` and report any device-side error raised by this
+ * index's kernels since the last check (the error word is then cleared). */
+mips_status mips_sync(mips_index_t idx, void* stream);
+
+/* Counters of the last completed call (synchronises the index's work). */
+typedef struct {
+  uint64_t cand_emitted;   /* candidates the score kernels emitted */
+  uint64_t cand_rescored;  /* candidates with upper bound >= final threshold */
+  uint64_t users_overflow; /* users whose candidate list overflowed (exhaustive rescore) */
+  uint64_t users_fp64;     /* users decided by the FP64 tie check */
+  uint64_t pairs_scored;   /* (user, item) pairs scored by the Maximus walk */
+  uint64_t blocks_walked;  /* item blocks the Maximus walk processed */
+  int64_t n_users;         /* users in the last call */
+  int clusters;            /* |C| of the last Maximus call */
+  int dtype;               /* candidate-pass dtype used */
+} mips_stats;
+mips_status mips_get_stats(mips_index_t idx, mips_stats* out);
+
+/*
+ * Read-only view of an internal device array of the index, for tests and
+ * inspection: name is one of "perm" (int32 [n_items], sorted position ->
+ * item id), "item_nrm" (float [n_items], upper bounds of ||i||, sorted
+ * order), and after a Maximus call "assign" (int32 [n_users]), "centroids"
+ * (float [C][f]), "cos_b" (float [C], lower bound of cos theta_b),
+ * "bound_sorted" (float [C][n_items], CBound upper bounds in list order),
+ * "list" (int32 [C][n_items], sorted item positions in list order),
+ * "visited" (int32 [n_users], items scored per user).  *dev_ptr and
+ * *bytes describe the array; it stays valid until the next call on idx.
+ */
+mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev_ptr,
+                            int64_t* bytes);
+
+/* Release the index and everything it allocated.  NULL is a no-op. */
+void mips_free_index(mips_index_t idx);
+
+/* Thread-local message describing the last failed call ("" if none). */
+const char* mips_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int mips_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MIPS_H_ */

@@ -1,0 +1,368 @@
+// The C ABI of libmips (declared in include/mips.h): argument checks, the
+// index object, its workspace arena, and the dispatch of each call to its
+// kernels.  No C++ exception crosses the boundary.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+using namespace mips;
+
+namespace {
+
+thread_local std::string g_err;
+
+mips_status fail(mips_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+mips_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(MIPS_ERR_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(MIPS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MIPS_CUDA(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Bump allocator over one device buffer; grown (stream-ordered) when a call
+// needs more than it holds.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+
+  void reset() { used = 0; }
+  size_t take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return off;
+  }
+  cudaError_t ensure(size_t bytes, cudaStream_t s) {
+    if (bytes <= cap) return cudaSuccess;
+    if (base) {
+      cudaError_t e = cudaFreeAsync(base, s);
+      if (e != cudaSuccess) return e;
+      base = nullptr;
+      cap = 0;
+    }
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMallocAsync((void**)&base, want, s);
+    if (e != cudaSuccess) return e;
+    cap = want;
+    return cudaSuccess;
+  }
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(base + off);
+  }
+};
+
+}  // namespace
+
+struct mips_index_s {
+  int device = 0;
+  int f = 0;
+  int64_t n_items = 0;
+  int clusters = 0;
+  mips_options opt{};
+  // item data, in the index's item order ("sorted position")
+  float* items = nullptr;      // FP32 master rows [n_items][f]
+  int32_t* perm = nullptr;     // sorted position -> item id
+  float* item_nrm = nullptr;   // upper bounds of ||i|| [n_items]
+  // BF16 operand rows with bound columns
+  int fp = 0;
+  void* items_bf16 = nullptr;  // [n_items_pad][fp]
+  float2* item_aux = nullptr;  // {nhat_i, alpha_i}
+  int64_t n_items_pad = 0;
+  // per-call state
+  Arena ws;
+  int* err_dev = nullptr;
+  DevStats* stats_dev = nullptr;
+  cudaEvent_t done = nullptr;   // end of the last call (orders calls on different streams)
+  bool has_done = false;
+  cudaStream_t last_stream = nullptr;
+  int64_t last_users = 0;
+  int last_dtype = 0;
+  int last_clusters = 0;
+};
+
+namespace {
+
+mips_status check_device(mips_index_t idx) {
+  int dev = -1;
+  MIPS_CUDA(cudaGetDevice(&dev));
+  if (dev != idx->device) return fail(MIPS_ERR_ARG, "index lives on device %d, current device is %d", idx->device, dev);
+  return MIPS_OK;
+}
+
+mips_status begin_call(mips_index_t idx, cudaStream_t s) {
+  if (idx->has_done) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
+  MIPS_CUDA(cudaMemsetAsync(idx->stats_dev, 0, sizeof(DevStats), s));
+  return MIPS_OK;
+}
+
+mips_status end_call(mips_index_t idx, cudaStream_t s) {
+  MIPS_CUDA(cudaEventRecord(idx->done, s));
+  idx->has_done = true;
+  idx->last_stream = s;
+  return MIPS_OK;
+}
+
+int cap_for(int K) { return 4 * K + 96; }
+
+// Blocked multiply (Sec. III-B) over the index's items with fused select,
+// then the exact rescore.
+mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
+                    double* out_score, cudaStream_t s) {
+  const int f = idx->f;
+  const int cap = cap_for(K);
+  idx->ws.reset();
+  size_t o_tau = idx->ws.take(sizeof(float) * n_users);
+  size_t o_n = idx->ws.take(sizeof(int) * n_users);
+  size_t o_pos = idx->ws.take(sizeof(int32_t) * n_users * cap);
+  size_t o_ub = idx->ws.take(sizeof(float) * n_users * cap);
+  MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
+  SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
+               idx->ws.at<float>(o_ub), cap};
+  if (idx->opt.dtype == MIPS_FP32) {
+    MIPS_CUDA(launch_fp32_score_select(users, n_users, f, idx->items, idx->item_nrm, idx->n_items, K, so,
+                                       idx->stats_dev, idx->err_dev, s));
+  } else {
+    return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d candidate pass not built", idx->opt.dtype);
+  }
+  MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, idx->n_items, K, so,
+                           out_idx, out_score, idx->stats_dev, idx->err_dev, s));
+  idx->last_users = n_users;
+  idx->last_dtype = idx->opt.dtype;
+  return MIPS_OK;
+}
+
+mips_status check_call(mips_index_t idx, const void* users, int64_t n_users, int K, const void* oi,
+                       const void* os) {
+  if (!idx) return fail(MIPS_ERR_ARG, "null index");
+  if (!users || !oi || !os) return fail(MIPS_ERR_ARG, "null buffer");
+  if (n_users <= 0 || n_users >= (1ll << 31)) return fail(MIPS_ERR_ARG, "n_users out of range: %lld", (long long)n_users);
+  if (K < 1 || K > idx->n_items || K > 128) return fail(MIPS_ERR_ARG, "K out of range: %d", K);
+  return check_device(idx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int mips_version(void) { return 100; }
+
+const char* mips_last_error(void) { return g_err.c_str(); }
+
+void mips_default_options(mips_options* opt) {
+  if (!opt) return;
+  opt->dtype = MIPS_BF16;
+  opt->kmeans_iters = 3;
+  opt->block_items = 0;
+  opt->sample_frac = 0.005;
+  opt->autotune = 0;
+  opt->seed = 0;
+}
+
+mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int clusters,
+                             const mips_options* opt, void* stream, mips_index_t* out) {
+  g_err.clear();
+  if (!out) return fail(MIPS_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (!items_dev) return fail(MIPS_ERR_ARG, "null items");
+  if (f < 1 || f > 128) return fail(MIPS_ERR_ARG, "f out of range [1,128]: %d", f);
+  if (n_items < 1 || n_items >= (1ll << 31)) return fail(MIPS_ERR_ARG, "n_items out of range: %lld", (long long)n_items);
+  if (clusters < 1 || clusters > 4096) return fail(MIPS_ERR_ARG, "clusters out of range [1,4096]: %d", clusters);
+  mips_options o;
+  mips_default_options(&o);
+  if (opt) o = *opt;
+  if (o.dtype != MIPS_FP32) return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d not built", o.dtype);
+  if (o.kmeans_iters < 0 || o.kmeans_iters > 100) return fail(MIPS_ERR_ARG, "kmeans_iters out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  mips_index_s* idx = new (std::nothrow) mips_index_s();
+  if (!idx) return fail(MIPS_ERR_NOMEM, "host allocation failed");
+  auto bail = [&](mips_status st) {
+    mips_free_index(idx);
+    return st;
+  };
+  cudaError_t e;
+#define BUILD_CUDA(call)                                   \
+  do {                                                     \
+    e = (call);                                            \
+    if (e != cudaSuccess) return bail(cuda_fail(e, #call)); \
+  } while (0)
+  BUILD_CUDA(cudaGetDevice(&idx->device));
+  idx->f = f;
+  idx->n_items = n_items;
+  idx->clusters = clusters;
+  idx->opt = o;
+  BUILD_CUDA(cudaEventCreateWithFlags(&idx->done, cudaEventDisableTiming));
+  BUILD_CUDA(cudaMalloc(&idx->err_dev, sizeof(int)));
+  BUILD_CUDA(cudaMemsetAsync(idx->err_dev, 0, sizeof(int), s));
+  BUILD_CUDA(cudaMalloc(&idx->stats_dev, sizeof(DevStats)));
+  BUILD_CUDA(cudaMalloc(&idx->items, sizeof(float) * n_items * f));
+  BUILD_CUDA(cudaMalloc(&idx->perm, sizeof(int32_t) * n_items));
+  BUILD_CUDA(cudaMalloc(&idx->item_nrm, sizeof(float) * n_items));
+  // item order: identity (sorted position == item id)
+  {
+    int32_t* hperm = (int32_t*)malloc(sizeof(int32_t) * n_items);
+    if (!hperm) return bail(fail(MIPS_ERR_NOMEM, "host allocation failed"));
+    for (int64_t i = 0; i < n_items; ++i) hperm[i] = (int32_t)i;
+    e = cudaMemcpyAsync(idx->perm, hperm, sizeof(int32_t) * n_items, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(hperm);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "perm upload"));
+  }
+  launch_gather_rows(items_dev, idx->perm, n_items, f, idx->items, s);
+  launch_row_norm_ub(idx->items, n_items, f, idx->item_nrm, idx->err_dev, s);
+  BUILD_CUDA(cudaGetLastError());
+  BUILD_CUDA(cudaStreamSynchronize(s));
+  int herr = 0;
+  BUILD_CUDA(cudaMemcpy(&herr, idx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (herr & DEV_ERR_NONFINITE) return bail(fail(MIPS_ERR_NONFINITE, "items hold NaN or Inf (or a norm overflows FP32)"));
+#undef BUILD_CUDA
+  *out = idx;
+  return MIPS_OK;
+}
+
+mips_status mips_topk(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                      int32_t* out_idx_dev, double* out_score_dev, void* stream) {
+  g_err.clear();
+  mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
+  if (st != MIPS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = begin_call(idx, s)) != MIPS_OK) return st;
+  if ((st = run_bmm(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s)) != MIPS_OK) return st;
+  return end_call(idx, s);
+}
+
+mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                              int32_t* out_idx_dev, double* out_score_dev, void* stream) {
+  g_err.clear();
+  mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
+  if (st != MIPS_OK) return st;
+  (void)stream;
+  return fail(MIPS_ERR_UNIMPLEMENTED, "Maximus path not built yet");
+}
+
+mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                        int32_t* out_idx_dev, double* out_score_dev, void* stream,
+                        mips_select_report* rep) {
+  g_err.clear();
+  mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
+  if (st != MIPS_OK) return st;
+  (void)stream;
+  (void)rep;
+  return fail(MIPS_ERR_UNIMPLEMENTED, "Optimus selector not built yet");
+}
+
+mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_users, int K, int method,
+                           int32_t* out_idx_host, double* out_score_host, void* stream) {
+  g_err.clear();
+  mips_status st = check_call(idx, users_host, n_users, K, out_idx_host, out_score_host);
+  if (st != MIPS_OK) return st;
+  if (method < 0 || method > 2) return fail(MIPS_ERR_ARG, "method must be 0, 1 or 2");
+  cudaStream_t s = (cudaStream_t)stream;
+  // device staging for this call (stream-ordered allocation)
+  const size_t b_users = sizeof(float) * n_users * idx->f;
+  const size_t b_idx = sizeof(int32_t) * n_users * K;
+  const size_t b_sc = sizeof(double) * n_users * K;
+  char* stage = nullptr;
+  MIPS_CUDA(cudaMallocAsync((void**)&stage, b_users + b_idx + b_sc + 512, s));
+  float* d_users = (float*)stage;
+  int32_t* d_idx = (int32_t*)(stage + ((b_users + 255) & ~size_t(255)));
+  double* d_sc = (double*)(stage + ((b_users + 255) & ~size_t(255)) + ((b_idx + 255) & ~size_t(255)));
+  cudaError_t e = cudaMemcpyAsync(d_users, users_host, b_users, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(stage, s);
+    return cuda_fail(e, "host-to-device copy of users");
+  }
+  if (method == 0)
+    st = mips_topk(idx, d_users, n_users, K, d_idx, d_sc, stream);
+  else if (method == 1)
+    st = mips_topk_maximus(idx, d_users, n_users, K, d_idx, d_sc, stream);
+  else
+    st = mips_select(idx, d_users, n_users, K, d_idx, d_sc, stream, nullptr);
+  if (st == MIPS_OK) {
+    e = cudaMemcpyAsync(out_idx_host, d_idx, b_idx, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_score_host, d_sc, b_sc, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "device-to-host copy of results");
+  }
+  cudaFreeAsync(stage, s);
+  if (st != MIPS_OK) return st;
+  return mips_sync(idx, stream);
+}
+
+mips_status mips_sync(mips_index_t idx, void* stream) {
+  if (!idx) return fail(MIPS_ERR_ARG, "null index");
+  MIPS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int h = 0;
+  MIPS_CUDA(cudaMemcpy(&h, idx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) MIPS_CUDA(cudaMemset(idx->err_dev, 0, sizeof(int)));
+  if (h & DEV_ERR_NONFINITE) return fail(MIPS_ERR_NONFINITE, "an input row holds NaN or Inf");
+  if (h & DEV_ERR_TIMEOUT) return fail(MIPS_ERR_TIMEOUT, "a bounded wait inside a kernel gave up");
+  if (h & DEV_ERR_INTERNAL) return fail(MIPS_ERR_CUDA, "an internal consistency check failed in a kernel");
+  return MIPS_OK;
+}
+
+mips_status mips_get_stats(mips_index_t idx, mips_stats* out) {
+  if (!idx || !out) return fail(MIPS_ERR_ARG, "null argument");
+  if (idx->has_done) MIPS_CUDA(cudaEventSynchronize(idx->done));
+  DevStats d;
+  MIPS_CUDA(cudaMemcpy(&d, idx->stats_dev, sizeof d, cudaMemcpyDeviceToHost));
+  out->cand_emitted = d.cand_emitted;
+  out->cand_rescored = d.cand_rescored;
+  out->users_overflow = d.users_overflow;
+  out->users_fp64 = d.users_fp64;
+  out->pairs_scored = d.pairs_scored;
+  out->blocks_walked = d.blocks_walked;
+  out->n_users = idx->last_users;
+  out->clusters = idx->last_clusters;
+  out->dtype = idx->last_dtype;
+  return MIPS_OK;
+}
+
+mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev_ptr, int64_t* bytes) {
+  if (!idx || !name || !dev_ptr || !bytes) return fail(MIPS_ERR_ARG, "null argument");
+  if (!strcmp(name, "perm")) {
+    *dev_ptr = idx->perm;
+    *bytes = sizeof(int32_t) * idx->n_items;
+  } else if (!strcmp(name, "item_nrm")) {
+    *dev_ptr = idx->item_nrm;
+    *bytes = sizeof(float) * idx->n_items;
+  } else {
+    return fail(MIPS_ERR_ARG, "unknown buffer name: %s", name);
+  }
+  return MIPS_OK;
+}
+
+void mips_free_index(mips_index_t idx) {
+  if (!idx) return;
+  if (idx->has_done) cudaEventSynchronize(idx->done);
+  if (idx->ws.base) cudaFree(idx->ws.base);
+  cudaFree(idx->items);
+  cudaFree(idx->perm);
+  cudaFree(idx->item_nrm);
+  cudaFree(idx->items_bf16);
+  cudaFree(idx->item_aux);
+  cudaFree(idx->err_dev);
+  cudaFree(idx->stats_dev);
+  if (idx->done) cudaEventDestroy(idx->done);
+  delete idx;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Input preparation: row-norm upper bounds, BF16 operand rows with bound
+// columns, row gathers.
+//
+// BF16 operand layout (K-major rows of fp = round_up(f + 2, 16) bf16):
+//   users (A operand): [ RN(u_0) .. RN(u_{f-1}) | beta_u | nhat_u | 0 ... ]
+//   items (B operand): [ RN(i_0) .. RN(i_{f-1}) | nhat_i | alpha_i | 0 ... ]
+// so that one tensor-core product of a user row with an item row yields
+//   H = u~ . i~ + beta_u nhat_i + nhat_u alpha_i,
+// an upper bound on the exact u^T i of the FP32 inputs, where
+//   nhat_x  >= max(||x||, ||x~||)                      (rounded up to BF16)
+//   beta_u  >= (||u - u~|| + g nhat_u)(1 + g)           (rounded up to BF16)
+//   alpha_i >= (||i - i~|| + g nhat_i)(1 + g)           (rounded up to BF16)
+// and g = (fp + 4) 2^-20 + f 2^-50 bounds the relative error of the FP32
+// tensor-core accumulation over fp terms (taken far looser than any
+// rounding or truncation accumulator of 23+ bits needs) together with the
+// rounding of the FP64 definition.  Why H >= u^T i:
+//   u^T i - u~.i~ = (u - u~)^T i + u~^T (i - i~)  <=  ||u-u~|| ||i|| + ||u~|| ||i-i~||,
+// each bound column product covers one of those terms plus g nhat_u nhat_i,
+// which exceeds the accumulation error g (||u~|| ||i~|| + bound terms).
+// The matching lower bound used by the select is
+//   L = H - 2 A - g (nhat_u nhat_i + A),   A = beta_u nhat_i + nhat_u alpha_i.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace mips {
+
+namespace {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32 sum of squares of f terms has relative error below f 2^-24; the
+// square root halves it.  This factor lifts the computed norm above the
+// exact one with room to spare.
+__device__ __forceinline__ float norm_ub(float sumsq, int f) {
+  return __fsqrt_rn(sumsq) * (1.0f + (float)(f + 2) * 1.1920929e-07f);
+}
+
+__global__ void row_norm_ub_kernel(const float* __restrict__ x, int64_t n, int f,
+                                   float* __restrict__ out, int* err) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float* r = x + row * f;
+  float ss = 0.f;
+  for (int k = lane; k < f; k += 32) ss = __fmaf_rn(r[k], r[k], ss);
+  ss = warp_sum(ss);
+  if (lane == 0) {
+    if (!isfinite(ss)) atomicOr(err, DEV_ERR_NONFINITE);
+    out[row] = norm_ub(ss, f);
+  }
+}
+
+__global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role,
+                                  __nv_bfloat16* __restrict__ out, int64_t n_rows_out,
+                                  float2* __restrict__ aux, int* err) {
+  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= n_rows_out) return;
+  __nv_bfloat16* o = out + row * fp;
+  if (row >= n) {  // padding rows
+    for (int k = lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
+    return;
+  }
+  const float* r = x + row * f;
+  float ss_x = 0.f, ss_t = 0.f, ss_d = 0.f;
+  for (int k = lane; k < f; k += 32) {
+    float v = r[k];
+    __nv_bfloat16 q = __float2bfloat16_rn(v);
+    float t = __bfloat162float(q);
+    float d = __fsub_rn(v, t);  // exact: t is v rounded to 8 significant bits
+    ss_x = __fmaf_rn(v, v, ss_x);
+    ss_t = __fmaf_rn(t, t, ss_t);
+    ss_d = __fmaf_rn(d, d, ss_d);
+    o[k] = q;
+  }
+  ss_x = warp_sum(ss_x);
+  ss_t = warp_sum(ss_t);
+  ss_d = warp_sum(ss_d);
+  const float g = (float)(fp + 4) * 9.5367432e-07f + (float)f * 8.8817842e-16f;  // 2^-20, 2^-50
+  float nhat = fmaxf(norm_ub(ss_x, f), norm_ub(ss_t, f));
+  float errn = norm_ub(ss_d, f);
+  __nv_bfloat16 nhat_b = __float2bfloat16_ru(nhat);
+  __nv_bfloat16 eb_b = __float2bfloat16_ru(__fmul_ru(__fmaf_ru(g, nhat, errn), 1.0f + g));
+  if (lane == 0) {
+    if (!isfinite(ss_x) || !isfinite(__bfloat162float(nhat_b))) atomicOr(err, DEV_ERR_NONFINITE);
+    if (role == 0) {
+      o[f] = eb_b;      // beta_u
+      o[f + 1] = nhat_b;  // nhat_u
+      aux[row] = make_float2(__bfloat162float(eb_b), __bfloat162float(nhat_b));
+    } else {
+      o[f] = nhat_b;    // nhat_i
+      o[f + 1] = eb_b;  // alpha_i
+      aux[row] = make_float2(__bfloat162float(nhat_b), __bfloat162float(eb_b));
+    }
+  }
+  for (int k = f + 2 + lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
+}
+
+__global__ void gather_rows_kernel(const float* __restrict__ x, const int32_t* __restrict__ perm,
+                                   int64_t n, int f, float* __restrict__ out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * f) return;
+  int64_t r = t / f;
+  int k = (int)(t - r * f);
+  out[t] = x[(int64_t)perm[r] * f + k];
+}
+
+}  // namespace
+
+void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* err, cudaStream_t s) {
+  if (n <= 0) return;
+  int wpb = 8;
+  row_norm_ub_kernel<<<(unsigned)((n + wpb - 1) / wpb), wpb * 32, 0, s>>>(x, n, f, nrm_ub, err);
+}
+
+void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void* out_bf16,
+                       int64_t n_rows_out, float2* aux, int* err, cudaStream_t s) {
+  if (n_rows_out <= 0) return;
+  int wpb = 8;
+  quant_bf16_kernel<<<(unsigned)((n_rows_out + wpb - 1) / wpb), wpb * 32, 0, s>>>(
+      x, n, f, fp, role, (__nv_bfloat16*)out_bf16, n_rows_out, aux, err);
+}
+
+void launch_gather_rows(const float* x, const int32_t* perm, int64_t n, int f, float* out, cudaStream_t s) {
+  int64_t total = n * f;
+  if (total <= 0) return;
+  gather_rows_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(x, perm, n, f, out);
+}
+
+}  // namespace mips

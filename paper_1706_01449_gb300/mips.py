@@ -1,0 +1,264 @@
+"""Python binding of libmips (include/mips.h): argument marshalling only.
+
+Every step of the search runs in the CUDA library; this module passes
+device pointers (from torch tensors), sizes and the current CUDA stream
+through ctypes and turns status codes into exceptions.  There is no CPU
+fallback: if the library is missing or CUDA is unavailable, calls raise.
+
+Names follow the C ABI: build_index, topk, topk_maximus, select,
+topk_host, sync, get_stats, get_buffer, free_index, last_error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmips.so")
+
+MIPS_OK, MIPS_ERR_ARG, MIPS_ERR_NOMEM, MIPS_ERR_CUDA = 0, 1, 2, 3
+MIPS_ERR_TIMEOUT, MIPS_ERR_OVERFLOW, MIPS_ERR_UNIMPLEMENTED, MIPS_ERR_NONFINITE = 4, 5, 6, 7
+STATUS_NAMES = {0: "MIPS_OK", 1: "MIPS_ERR_ARG", 2: "MIPS_ERR_NOMEM", 3: "MIPS_ERR_CUDA",
+                4: "MIPS_ERR_TIMEOUT", 5: "MIPS_ERR_OVERFLOW", 6: "MIPS_ERR_UNIMPLEMENTED",
+                7: "MIPS_ERR_NONFINITE"}
+DTYPES = {"fp32": 0, "bf16": 1, "fp8": 2}
+METHODS = {"bmm": 0, "maximus": 1, "select": 2}
+
+# every symbol include/mips.h declares
+EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_maximus",
+           "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
+           "mips_free_index", "mips_last_error", "mips_version")
+
+
+class MipsError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("kmeans_iters", ctypes.c_int), ("block_items", ctypes.c_int),
+                ("sample_frac", ctypes.c_double), ("autotune", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class SelectReport(ctypes.Structure):
+    _fields_ = [("choice", ctypes.c_int), ("t_build", ctypes.c_double), ("q_user", ctypes.c_double),
+                ("m_user", ctypes.c_double), ("sample_users", ctypes.c_int64),
+                ("est_index", ctypes.c_double), ("est_bmm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("cand_emitted", ctypes.c_uint64), ("cand_rescored", ctypes.c_uint64),
+                ("users_overflow", ctypes.c_uint64), ("users_fp64", ctypes.c_uint64),
+                ("pairs_scored", ctypes.c_uint64), ("blocks_walked", ctypes.c_uint64),
+                ("n_users", ctypes.c_int64), ("clusters", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load():
+    """Load the in-tree library (build it with __graft_entry__.build() or
+    paper_1706_01449_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmips.so not built ({LIB_PATH}); run paper_1706_01449_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    st = ctypes.c_int
+    lib.mips_default_options.argtypes = [ctypes.POINTER(Options)]
+    lib.mips_default_options.restype = None
+    lib.mips_build_index.argtypes = [P, i64, i32, i32, ctypes.POINTER(Options), P, ctypes.POINTER(P)]
+    lib.mips_build_index.restype = st
+    for name in ("mips_topk", "mips_topk_maximus"):
+        fn = getattr(lib, name)
+        fn.argtypes = [P, P, i64, i32, P, P, P]
+        fn.restype = st
+    lib.mips_select.argtypes = [P, P, i64, i32, P, P, P, ctypes.POINTER(SelectReport)]
+    lib.mips_select.restype = st
+    lib.mips_topk_host.argtypes = [P, P, i64, i32, i32, P, P, P]
+    lib.mips_topk_host.restype = st
+    lib.mips_sync.argtypes = [P, P]
+    lib.mips_sync.restype = st
+    lib.mips_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.mips_get_stats.restype = st
+    lib.mips_get_buffer.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(P), ctypes.POINTER(i64)]
+    lib.mips_get_buffer.restype = st
+    lib.mips_free_index.argtypes = [P]
+    lib.mips_free_index.restype = None
+    lib.mips_last_error.argtypes = []
+    lib.mips_last_error.restype = ctypes.c_char_p
+    lib.mips_version.argtypes = []
+    lib.mips_version.restype = i32
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().mips_last_error().decode()
+
+
+def _check(status: int):
+    if status != MIPS_OK:
+        raise MipsError(status, last_error())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(x, name):
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float32 CUDA tensor")
+    return x.contiguous()
+
+
+class Index:
+    """Owning handle of a libmips index (frees it on close/deletion)."""
+
+    def __init__(self, handle, f, n_items, clusters, dtype):
+        self._h = handle
+        self.f, self.n_items, self.clusters, self.dtype = f, n_items, clusters, dtype
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("index already freed")
+        return self._h
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.mips_free_index(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def build_index(items, clusters: int = 8, dtype: str = "bf16", kmeans_iters: int = 3,
+                block_items: int = 0, sample_frac: float = 0.005, seed: int = 0, stream=None) -> Index:
+    lib = load()
+    items = _dev_f32(items, "items")
+    opt = Options()
+    lib.mips_default_options(ctypes.byref(opt))
+    opt.dtype = DTYPES[dtype]
+    opt.kmeans_iters = kmeans_iters
+    opt.block_items = block_items
+    opt.sample_frac = sample_frac
+    opt.seed = seed
+    h = ctypes.c_void_p()
+    _check(lib.mips_build_index(ctypes.c_void_p(items.data_ptr()), items.shape[0], items.shape[1], clusters,
+                                ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)))
+    return Index(h, items.shape[1], items.shape[0], clusters, dtype)
+
+
+def _outputs(n, K, out_idx, out_score, device):
+    import torch
+    if out_idx is None:
+        out_idx = torch.empty((n, K), dtype=torch.int32, device=device)
+    if out_score is None:
+        out_score = torch.empty((n, K), dtype=torch.float64, device=device)
+    if out_idx.dtype != torch.int32 or out_score.dtype != torch.float64 or not out_idx.is_contiguous() \
+            or not out_score.is_contiguous() or out_idx.numel() < n * K or out_score.numel() < n * K:
+        raise TypeError("out_idx must be int32 and out_score float64, contiguous, n*K elements")
+    return out_idx, out_score
+
+
+def _run(fn, index, users, K, out_idx, out_score, stream):
+    users = _dev_f32(users, "users")
+    if users.shape[1] != index.f:
+        raise ValueError("users have a different f than the index")
+    out_idx, out_score = _outputs(users.shape[0], K, out_idx, out_score, users.device)
+    _check(fn(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0], K,
+              ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()), _stream_ptr(stream)))
+    return out_idx, out_score
+
+
+def topk(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
+    """Blocked multiply + fused top-K (mips_topk).  Asynchronous on the stream."""
+    return _run(load().mips_topk, index, users, K, out_idx, out_score, stream)
+
+
+def topk_maximus(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
+    """Maximus (mips_topk_maximus).  Asynchronous on the stream."""
+    return _run(load().mips_topk_maximus, index, users, K, out_idx, out_score, stream)
+
+
+def select(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
+    """Optimus selector (mips_select): returns (idx, score, report dict)."""
+    lib = load()
+    users = _dev_f32(users, "users")
+    out_idx, out_score = _outputs(users.shape[0], K, out_idx, out_score, users.device)
+    rep = SelectReport()
+    _check(lib.mips_select(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0], K,
+                           ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
+                           _stream_ptr(stream), ctypes.byref(rep)))
+    return out_idx, out_score, rep.as_dict()
+
+
+def topk_host(index: Index, users_host, K: int, method: str = "bmm", out_idx=None, out_score=None,
+              stream=None):
+    """Host-buffer variant (mips_topk_host): numpy or pinned-torch CPU arrays
+    in, host arrays out; synchronous."""
+    import numpy as np
+    import torch
+    if isinstance(users_host, np.ndarray):
+        users_host = torch.from_numpy(np.ascontiguousarray(users_host, dtype=np.float32))
+    n = users_host.shape[0]
+    if out_idx is None:
+        out_idx = torch.empty((n, K), dtype=torch.int32, pin_memory=users_host.is_pinned())
+    if out_score is None:
+        out_score = torch.empty((n, K), dtype=torch.float64, pin_memory=users_host.is_pinned())
+    _check(load().mips_topk_host(index.handle, ctypes.c_void_p(users_host.data_ptr()), n, K, METHODS[method],
+                                 ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
+                                 _stream_ptr(stream)))
+    return out_idx, out_score
+
+
+def sync(index: Index, stream=None):
+    _check(load().mips_sync(index.handle, _stream_ptr(stream)))
+
+
+def get_stats(index: Index) -> dict:
+    st = Stats()
+    _check(load().mips_get_stats(index.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def get_buffer(index: Index, name: str, dtype, shape):
+    """Copy of an internal device array (see mips_get_buffer) as a torch tensor."""
+    import torch
+    p = ctypes.c_void_p()
+    nbytes = ctypes.c_int64()
+    _check(load().mips_get_buffer(index.handle, name.encode(), ctypes.byref(p), ctypes.byref(nbytes)))
+    typestr = {torch.float32: "<f4", torch.int32: "<i4", torch.float64: "<f8", torch.int64: "<i8"}[dtype]
+    esize = torch.empty((), dtype=dtype).element_size()
+    count = 1
+    for d in shape:
+        count *= d
+    if count * esize != nbytes.value:
+        raise ValueError(f"buffer {name} holds {nbytes.value} bytes, shape asks for {count * esize}")
+
+    class _View:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (p.value, True),
+                                    "version": 3, "strides": None}
+
+    return torch.as_tensor(_View(), device="cuda").clone()
+
+
+def free_index(index: Index):
+    index.close()
