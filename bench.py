@@ -1,0 +1,365 @@
+"""Benchmark: exact batch top-K MIPS throughput (users/sec) on GB300.
+
+One step = one mips_topk call (the whole hot path: user quantisation,
+fused score + select, exact rescore) over all users of the workload, with
+users and items already resident in HBM.  Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|fp32]
+                    [--method bmm|maximus|select] [--f 50] [--k 10]
+                    [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own users
+(seed = rank) with no collective on the data path: weak scaling; the time
+is the max over ranks.  --impl reference times the CPU oracle (FP64 brute
+force, all host cores) on a bounded user sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "netflix-480189x17770"
+SM_COUNT_FALLBACK = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--dtype", default="auto", choices=["auto", "bf16", "fp32"])
+    p.add_argument("--method", default="bmm", choices=["bmm", "maximus", "select"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--f", type=int, default=50)
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--clusters", type=int, default=64)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        sm = [r[0] for r in rows]
+        busy = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def kernel_source_hash(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_1706_01449_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key, src_hash):
+    """dram bytes per launch of this kernel from the committed ncu summary, if
+    it was taken on the same kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != src_hash:
+        return None
+    return e.get("bytes_per_launch")
+
+
+def cpu_baseline(U, I, K, target_s=12.0, max_users=20000):
+    """The oracle as it stands (FP64 brute force, full sort, OpenMP over all
+    host cores) on a bounded user sample; users/sec."""
+    import oracle
+    oracle.build()
+    n0 = min(64, U.shape[0])
+    t = time.perf_counter()
+    _, _, nt = oracle.topk(U[:n0], I, K, return_threads=True)
+    per_user = (time.perf_counter() - t) / n0
+    n = int(min(max_users, U.shape[0], max(n0, target_s / max(per_user, 1e-9))))
+    t = time.perf_counter()
+    _, _, nt = oracle.topk(U[:n], I, K, return_threads=True)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "users/s", "cores": nt, "kind": "oracle",
+            "sample": f"first {n} users of the workload ({dt:.1f} s of FP64 brute force, full sort per user)"}
+
+
+def make_inputs(args, rank):
+    from paper_1706_01449_gb300 import synth
+    W = synth.WORKLOADS[args.workload]
+    f = args.f if "fs" in W else W["f"]
+    U = synth.make_users(W, seed=rank, f=f)
+    I = synth.make_items(W, seed=0, f=f)
+    return W, f, U, I
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    _, f, U, I = make_inputs(args, 0)
+    K = args.k
+    n0 = 32
+    t = time.perf_counter()
+    _, _, nt = oracle.topk(U[:n0], I, K, return_threads=True)
+    per_user = (time.perf_counter() - t) / n0
+    n = int(max(n0, min(U.shape[0], 8.0 / max(per_user, 1e-9))))
+    for w in range(args.warmup):
+        oracle.topk(U[:n], I, K)
+    times = []
+    for s in range(args.steps):
+        lo = (s * n) % max(1, U.shape[0] - n)
+        t = time.perf_counter()
+        oracle.topk(U[lo:lo + n], I, K)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": "exact top-K users/sec", "value": value, "unit": "users/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} f={f} K={K}", "users_per_step": n,
+                       "n_items": int(I.shape[0]), "f": f, "K": K, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "users/s", "cores": nt, "kind": "oracle",
+                             "sample": f"{n} users per step, FP64 brute force with full sort per user"},
+            "e2e": {"value": value, "unit": "users/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_1706_01449_gb300 import build as libbuild
+    from paper_1706_01449_gb300 import mips
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(mips.LIB_PATH):
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+
+    W, f, U, I = make_inputs(args, rank)
+    K = args.k
+    nU, nI = U.shape[0], I.shape[0]
+    dtype = args.dtype
+    I_d = torch.from_numpy(I).to(dev)
+    U_d = torch.from_numpy(U).to(dev)
+    index = None
+    for cand in (["bf16", "fp32"] if dtype == "auto" else [dtype]):
+        try:
+            index = mips.build_index(I_d, clusters=args.clusters, dtype=cand)
+            dtype = cand
+            break
+        except mips.MipsError as e:
+            if e.status != mips.MIPS_ERR_UNIMPLEMENTED or cand == "fp32":
+                raise
+    out_idx = torch.empty((nU, K), dtype=torch.int32, device=dev)
+    out_sc = torch.empty((nU, K), dtype=torch.float64, device=dev)
+    fn = {"bmm": mips.topk, "maximus": mips.topk_maximus}.get(args.method)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if args.method == "select":
+            mips.select(index, U_d, K, out_idx, out_sc)
+        else:
+            fn(index, U_d, K, out_idx, out_sc)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    mips.sync(index)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, score_ms, launches = [], [], 0
+    stats = None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats = mips.get_stats(index)
+        score_ms.append(stats["ms_score"] if args.method == "bmm" else stats["ms_walk"] or stats["ms_score"])
+        launches += stats["launches"]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    mips.sync(index)
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * nU / (ms_per_step / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not args.no_e2e:
+        U_h = torch.from_numpy(U).pin_memory()
+        oi_h = torch.empty((nU, K), dtype=torch.int32).pin_memory()
+        os_h = torch.empty((nU, K), dtype=torch.float64).pin_memory()
+        method = {"bmm": "bmm", "maximus": "maximus", "select": "select"}[args.method]
+        mips.topk_host(index, U_h, K, method, oi_h, os_h)
+        ts = []
+        for _ in range(min(3, args.steps)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            mips.topk_host(index, U_h, K, method, oi_h, os_h)
+            ts.append(time.perf_counter() - t)
+        e2e = {"value": nU / statistics.median(ts), "unit": "users/s",
+               "h2d_bytes_per_step": int(U_h.numel() * 4), "d2h_bytes_per_step": int(nU * K * (4 + 8))}
+
+    if rank != 0:
+        index.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks, peak_src = load_peaks()
+    flops = 2.0 * f * nU * nI
+    kms = statistics.mean(score_ms)
+    if dtype == "bf16":
+        bound, peak, unit = "tensor", peaks["bf16_tflops"], "TFLOP/s"
+        kernel_key = f"tc_score_select bf16 {args.workload} f={f} K={K}"
+        src = ["tc_topk.cu"]
+    else:
+        props = torch.cuda.get_device_properties(dev)
+        sm = getattr(props, "multi_processor_count", SM_COUNT_FALLBACK)
+        bound, unit = "alu", "TFLOP/s"
+        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        kernel_key = f"fp32_score_select {args.workload} f={f} K={K}"
+        src = ["fp32_topk.cu"]
+    achieved = flops / (kms / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": traffic_for(kernel_key, kernel_source_hash(src)),
+                "kernel": kernel_key.split()[0], "kernel_ms": kms,
+                "peak_source": (f"{peak_src} bf16 burst" if bound == "tensor"
+                                else f"derived: SMs x 128 FP32 FMA/clk x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"),
+                "algorithmic_flops_per_launch": flops}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(U, I, K)
+
+    line = {
+        "metric": "exact top-K users/sec", "value": value, "unit": "users/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if dtype == "bf16" else "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} f={f} K={K}", "n_users": nU, "n_items": nI, "f": f, "K": K,
+                   "method": args.method, "candidate_pass": dtype, "rescore": "compensated fp32 + fp64 tie check",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "stages_ms_last_step": {k: stats[k] for k in ("ms_prep", "ms_score", "ms_rescore", "ms_kmeans",
+                                                       "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
+        "candidates_per_user": stats["cand_emitted"] / nU, "rescored_per_user": stats["cand_rescored"] / nU,
+        "users_overflow": stats["users_overflow"], "users_fp64": stats["users_fp64"],
+    }
+    print(json.dumps(line), flush=True)
+    index.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,18 @@ typedef struct {
   int64_t n_users;         /* users in the last call */
   int clusters;            /* |C| of the last Maximus call */
   int dtype;               /* candidate-pass dtype used */
+  int launches;            /* kernels the last call launched */
+  int pad_;
+  /* per-stage device time of the last call in milliseconds (CUDA events
+   * recorded on the call's stream; 0 for stages it did not run) */
+  double ms_prep;          /* quantisation / packing of the users */
+  double ms_score;         /* fused score + select (blocked multiply) */
+  double ms_rescore;       /* exact rescore + final top-K */
+  double ms_kmeans;        /* Maximus: k-means iterations */
+  double ms_bounds;        /* Maximus: theta_b + CBound for every (cluster, item) */
+  double ms_sort;          /* Maximus: per-cluster list sort + user grouping */
+  double ms_walk;          /* Maximus: grouped walk (score + select) */
+  double ms_total;         /* whole call */
 } mips_stats;
 mips_status mips_get_stats(mips_index_t idx, mips_stats* out);
 

@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float hs[4] = {h0, h1, h2, h3};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (hs[q] >= st.tau) {
+          if (hs[q] >= st.tau && j0 + q < rows) {
             const float lo = __fmaf_rn(-gu, nrm[j0 + q], accs[q]);
             st.offer(hs[q], lo, (int32_t)(first + j0 + q));
           }

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "internal.h"
+#include "tc_topk.h"
 
 using namespace mips;
 
@@ -70,6 +71,8 @@ struct Arena {
   }
 };
 
+enum Stage { ST_PREP = 0, ST_SCORE, ST_RESCORE, ST_KMEANS, ST_BOUNDS, ST_SORT, ST_WALK, kStages };
+
 }  // namespace
 
 struct mips_index_s {
@@ -87,6 +90,9 @@ struct mips_index_s {
   void* items_bf16 = nullptr;  // [n_items_pad][fp]
   float2* item_aux = nullptr;  // {nhat_i, alpha_i}
   int64_t n_items_pad = 0;
+  CUtensorMap map_items;       // TMA map over items_bf16
+  int num_sms = 0;
+  int max_smem = 0;
   // per-call state
   Arena ws;
   int* err_dev = nullptr;
@@ -97,6 +103,11 @@ struct mips_index_s {
   int64_t last_users = 0;
   int last_dtype = 0;
   int last_clusters = 0;
+  // per-stage timing: ev[0] = call start, ev[1 + stage] = end of stage
+  cudaEvent_t ev[kStages + 1] = {};
+  bool stage_ran[kStages] = {};
+  int last_stage = -1;
+  int launches = 0;
 };
 
 namespace {
@@ -111,6 +122,18 @@ mips_status check_device(mips_index_t idx) {
 mips_status begin_call(mips_index_t idx, cudaStream_t s) {
   if (idx->has_done) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
   MIPS_CUDA(cudaMemsetAsync(idx->stats_dev, 0, sizeof(DevStats), s));
+  for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
+  idx->last_stage = -1;
+  idx->launches = 0;
+  MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
+  return MIPS_OK;
+}
+
+// Mark the end of a stage (stages run in enum order within one call).
+mips_status end_stage(mips_index_t idx, Stage st, cudaStream_t s) {
+  MIPS_CUDA(cudaEventRecord(idx->ev[1 + st], s));
+  idx->stage_ran[st] = true;
+  idx->last_stage = st;
   return MIPS_OK;
 }
 
@@ -140,11 +163,46 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   if (idx->opt.dtype == MIPS_FP32) {
     MIPS_CUDA(launch_fp32_score_select(users, n_users, f, idx->items, idx->item_nrm, idx->n_items, K, so,
                                        idx->stats_dev, idx->err_dev, s));
+    idx->launches += 1;
+    mips_status st = end_stage(idx, ST_SCORE, s);
+    if (st != MIPS_OK) return st;
   } else {
-    return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d candidate pass not built", idx->opt.dtype);
+    TcParams p{};
+    p.n_users = n_users;
+    p.n_items = idx->n_items;
+    p.f = f;
+    p.fp = idx->fp;
+    p.K = K;
+    if (!tc_plan(p, idx->max_smem)) return fail(MIPS_ERR_ARG, "no tcgen05 tiling fits shared memory for f=%d K=%d", f, K);
+    // user operand rows live in the same arena, after the select buffers
+    size_t o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
+    size_t o_uaux = idx->ws.take(sizeof(float2) * n_users);
+    MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
+    so = SelectOut{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
+                   idx->ws.at<float>(o_ub), cap};
+    void* ub16 = idx->ws.at<void>(o_ub16);
+    float2* uaux = idx->ws.at<float2>(o_uaux);
+    launch_quant_bf16(users, n_users, f, idx->fp, 0, ub16, n_users, uaux, idx->err_dev, s);
+    MIPS_CUDA(cudaGetLastError());
+    idx->launches += 1;
+    mips_status st = end_stage(idx, ST_PREP, s);
+    if (st != MIPS_OK) return st;
+    CUtensorMap map_users;
+    if (!tc_make_map(&map_users, ub16, n_users, idx->fp, p.row_bytes))
+      return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the user operand");
+    const int64_t n_ut = (n_users + p.nh * 128 - 1) / (p.nh * 128);
+    const int grid = (int)(n_ut < idx->num_sms ? n_ut : idx->num_sms);
+    MIPS_CUDA(launch_tc_score_select(&map_users, &idx->map_items, p, so, uaux, idx->item_aux, idx->stats_dev,
+                                     idx->err_dev, grid, s));
+    idx->launches += 1;
+    st = end_stage(idx, ST_SCORE, s);
+    if (st != MIPS_OK) return st;
   }
   MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, idx->n_items, K, so,
                            out_idx, out_score, idx->stats_dev, idx->err_dev, s));
+  idx->launches += 1;
+  mips_status st = end_stage(idx, ST_RESCORE, s);
+  if (st != MIPS_OK) return st;
   idx->last_users = n_users;
   idx->last_dtype = idx->opt.dtype;
   return MIPS_OK;
@@ -189,7 +247,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   mips_options o;
   mips_default_options(&o);
   if (opt) o = *opt;
-  if (o.dtype != MIPS_FP32) return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d not built", o.dtype);
+  if (o.dtype != MIPS_FP32 && o.dtype != MIPS_BF16) return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d not built", o.dtype);
   if (o.kmeans_iters < 0 || o.kmeans_iters > 100) return fail(MIPS_ERR_ARG, "kmeans_iters out of range");
   cudaStream_t s = (cudaStream_t)stream;
 
@@ -206,11 +264,14 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
     if (e != cudaSuccess) return bail(cuda_fail(e, #call)); \
   } while (0)
   BUILD_CUDA(cudaGetDevice(&idx->device));
+  BUILD_CUDA(cudaDeviceGetAttribute(&idx->num_sms, cudaDevAttrMultiProcessorCount, idx->device));
+  BUILD_CUDA(cudaDeviceGetAttribute(&idx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, idx->device));
   idx->f = f;
   idx->n_items = n_items;
   idx->clusters = clusters;
   idx->opt = o;
   BUILD_CUDA(cudaEventCreateWithFlags(&idx->done, cudaEventDisableTiming));
+  for (int i = 0; i <= kStages; ++i) BUILD_CUDA(cudaEventCreate(&idx->ev[i]));
   BUILD_CUDA(cudaMalloc(&idx->err_dev, sizeof(int)));
   BUILD_CUDA(cudaMemsetAsync(idx->err_dev, 0, sizeof(int), s));
   BUILD_CUDA(cudaMalloc(&idx->stats_dev, sizeof(DevStats)));
@@ -230,6 +291,22 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   launch_gather_rows(items_dev, idx->perm, n_items, f, idx->items, s);
   launch_row_norm_ub(idx->items, n_items, f, idx->item_nrm, idx->err_dev, s);
   BUILD_CUDA(cudaGetLastError());
+  if (o.dtype == MIPS_BF16) {
+    idx->fp = tc_row_len(f);
+    idx->n_items_pad = round_up(n_items, 128);
+    BUILD_CUDA(cudaMalloc(&idx->items_bf16, sizeof(uint16_t) * idx->n_items_pad * idx->fp));
+    BUILD_CUDA(cudaMalloc(&idx->item_aux, sizeof(float2) * idx->n_items_pad));
+    launch_quant_bf16(idx->items, n_items, f, idx->fp, 1, idx->items_bf16, idx->n_items_pad, idx->item_aux,
+                      idx->err_dev, s);
+    BUILD_CUDA(cudaGetLastError());
+    TcParams p{};
+    p.fp = idx->fp;
+    p.f = f;
+    p.K = 1;
+    if (!tc_plan(p, idx->max_smem)) return bail(fail(MIPS_ERR_ARG, "no tcgen05 tiling fits for f=%d", f));
+    if (!tc_make_map(&idx->map_items, idx->items_bf16, idx->n_items_pad, idx->fp, p.row_bytes))
+      return bail(fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the item operand"));
+  }
   BUILD_CUDA(cudaStreamSynchronize(s));
   int herr = 0;
   BUILD_CUDA(cudaMemcpy(&herr, idx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
@@ -333,6 +410,29 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out) {
   out->n_users = idx->last_users;
   out->clusters = idx->last_clusters;
   out->dtype = idx->last_dtype;
+  out->launches = idx->launches;
+  out->pad_ = 0;
+  double ms[kStages] = {};
+  cudaEvent_t prev = idx->ev[0];
+  float t = 0.f;
+  for (int i = 0; i < kStages; ++i) {
+    if (!idx->stage_ran[i]) continue;
+    MIPS_CUDA(cudaEventElapsedTime(&t, prev, idx->ev[1 + i]));
+    ms[i] = t;
+    prev = idx->ev[1 + i];
+  }
+  out->ms_prep = ms[ST_PREP];
+  out->ms_score = ms[ST_SCORE];
+  out->ms_rescore = ms[ST_RESCORE];
+  out->ms_kmeans = ms[ST_KMEANS];
+  out->ms_bounds = ms[ST_BOUNDS];
+  out->ms_sort = ms[ST_SORT];
+  out->ms_walk = ms[ST_WALK];
+  out->ms_total = 0.0;
+  if (idx->last_stage >= 0) {
+    MIPS_CUDA(cudaEventElapsedTime(&t, idx->ev[0], idx->ev[1 + idx->last_stage]));
+    out->ms_total = t;
+  }
   return MIPS_OK;
 }
 
@@ -362,6 +462,8 @@ void mips_free_index(mips_index_t idx) {
   cudaFree(idx->err_dev);
   cudaFree(idx->stats_dev);
   if (idx->done) cudaEventDestroy(idx->done);
+  for (int i = 0; i <= kStages; ++i)
+    if (idx->ev[i]) cudaEventDestroy(idx->ev[i]);
   delete idx;
 }
 

@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     __syncwarp();
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) n_rescored += __shfl_xor_sync(kFull, n_rescored, off);
   if (lane == 0) {
     if (n_rescored) atomicAdd(&stats->cand_rescored, n_rescored);
     if (n_over) atomicAdd(&stats->users_overflow, n_over);

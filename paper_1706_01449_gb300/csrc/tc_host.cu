@@ -1,0 +1,59 @@
+// Host helpers of the tcgen05 kernel: tiling plan and TMA tensor maps.
+#include <cstring>
+
+#include "tc_topk.h"
+
+namespace mips {
+
+bool tc_plan(TcParams& p, int max_smem) {
+  p.row_bytes = p.fp <= 16 ? 32 : (p.fp <= 32 ? 64 : 128);
+  p.row_elems = p.row_bytes / 2;
+  p.kc = p.fp / p.row_elems;
+  p.swizzle = p.row_bytes == 32 ? 6 : (p.row_bytes == 64 ? 4 : 2);
+  p.g = (float)(p.fp + 4) * 9.5367432e-07f + (float)p.f * 8.8817842e-16f;
+  for (int nh = 2; nh >= 1; --nh) {
+    for (int st = kMaxStages; st >= 2; --st) {
+      p.nh = nh;
+      p.stages = st;
+      if (tc_smem_bytes(p) <= (size_t)max_smem) return true;
+    }
+  }
+  return false;
+}
+
+namespace {
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)ptr;
+  }
+  return fn;
+}
+}  // namespace
+
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  memset(map, 0, sizeof(*map));
+  cuuint64_t dims[2] = {(cuuint64_t)fp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)fp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / 2), 128u};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUtensorMapSwizzle sw = row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                          : (row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace mips

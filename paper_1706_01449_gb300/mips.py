@@ -54,10 +54,14 @@ class Stats(ctypes.Structure):
     _fields_ = [("cand_emitted", ctypes.c_uint64), ("cand_rescored", ctypes.c_uint64),
                 ("users_overflow", ctypes.c_uint64), ("users_fp64", ctypes.c_uint64),
                 ("pairs_scored", ctypes.c_uint64), ("blocks_walked", ctypes.c_uint64),
-                ("n_users", ctypes.c_int64), ("clusters", ctypes.c_int), ("dtype", ctypes.c_int)]
+                ("n_users", ctypes.c_int64), ("clusters", ctypes.c_int), ("dtype", ctypes.c_int),
+                ("launches", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("ms_prep", ctypes.c_double), ("ms_score", ctypes.c_double), ("ms_rescore", ctypes.c_double),
+                ("ms_kmeans", ctypes.c_double), ("ms_bounds", ctypes.c_double), ("ms_sort", ctypes.c_double),
+                ("ms_walk", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 _lib = None
