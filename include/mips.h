@@ -188,6 +188,41 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out);
 mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev_ptr,
                             int64_t* bytes);
 
+/*
+ * Exact top-K without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc/cudaFree
+ * -- code running inside a custom device allocator or an out-of-memory
+ * handler (the allocator must not be re-entered), a latency-critical path
+ * where cudaFree's device-wide synchronisation is unacceptable, or a
+ * process whose whole memory budget is owned by someone else.
+ *
+ * It runs the FP32 blocked multiply with fused select and the exact
+ * rescore (the same kernels, and the same result semantics, as mips_topk on
+ * an MIPS_FP32 index) directly on the caller's buffers: items_dev FP32
+ * [n_items][f], users_dev FP32 [n_users][f], out_idx_dev int32 [n_users][K],
+ * out_score_dev double [n_users][K], all device memory owned by the caller.
+ * No index is needed and none of its state is used.
+ *
+ * Scratch comes from one static device array of 32 MiB per GPU, reserved
+ * when the library's code is loaded on that GPU and held until the process
+ * exits.  A call needs 8 n_items + n_users (8 + 8 (4K + 96)) bytes of it
+ * plus 1 KiB (K = 10: about 30,000 users against 17,770 items); larger
+ * calls return MIPS_ERR_ARG (split the users).  Limits as mips_topk:
+ * 1 <= f <= 128, 1 <= K <= min(n_items, 128).
+ *
+ * All calls share that array and it keeps the last call's contents (each
+ * call clears the counters that must start at zero).  Calls that overlap on
+ * the GPU -- on two streams or from two host threads -- race on it and
+ * return wrong results: serialise them.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  The call returns after `stream` has finished
+ * it, and reports non-finite input as MIPS_ERR_NONFINITE.
+ */
+mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const float* users_dev, int64_t n_users,
+                              int f, int K, int32_t* out_idx_dev, double* out_score_dev, void* stream);
+
 /* Release the index and everything it allocated.  NULL is a no-op. */
 void mips_free_index(mips_index_t idx);
 

@@ -58,4 +58,7 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
                            SelectOut o, int32_t* out_idx, double* out_score, DevStats* stats,
                            int* err, cudaStream_t s);
 
+// Set the calling thread's message returned by mips_last_error().
+void set_last_error_message(const char* msg);
+
 }  // namespace mips

@@ -75,6 +75,8 @@ enum Stage { ST_PREP = 0, ST_SCORE, ST_RESCORE, ST_KMEANS, ST_BOUNDS, ST_SORT, S
 
 }  // namespace
 
+void mips::set_last_error_message(const char* msg) { g_err = msg; }
+
 struct mips_index_s {
   int device = 0;
   int f = 0;

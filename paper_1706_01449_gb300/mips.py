@@ -27,7 +27,7 @@ METHODS = {"bmm": 0, "maximus": 1, "select": 2}
 # every symbol include/mips.h declares
 EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_maximus",
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
-           "mips_free_index", "mips_last_error", "mips_version")
+           "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc")
 
 
 class MipsError(RuntimeError):
@@ -100,6 +100,8 @@ def load():
     lib.mips_free_index.restype = None
     lib.mips_last_error.argtypes = []
     lib.mips_last_error.restype = ctypes.c_char_p
+    lib.mips_topk_noalloc.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
+    lib.mips_topk_noalloc.restype = st
     lib.mips_version.argtypes = []
     lib.mips_version.restype = i32
     _lib = lib
@@ -262,6 +264,22 @@ def get_buffer(index: Index, name: str, dtype, shape):
                                     "version": 3, "strides": None}
 
     return torch.as_tensor(_View(), device="cuda").clone()
+
+
+def topk_noalloc(items, users, K: int, out_idx, out_score, stream=None):
+    """mips_topk_noalloc: exact top-K on caller-owned device buffers with no
+    device allocation inside the library (scratch is a static 32 MiB device
+    array shared by all calls; serialise calls).  Synchronous."""
+    items = _dev_f32(items, "items")
+    users = _dev_f32(users, "users")
+    if users.shape[1] != items.shape[1]:
+        raise ValueError("users and items differ in f")
+    out_idx, out_score = _outputs(users.shape[0], K, out_idx, out_score, users.device)
+    _check(load().mips_topk_noalloc(ctypes.c_void_p(items.data_ptr()), items.shape[0],
+                                    ctypes.c_void_p(users.data_ptr()), users.shape[0], users.shape[1], K,
+                                    ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
+                                    _stream_ptr(stream)))
+    return out_idx, out_score
 
 
 def free_index(index: Index):
