@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--f", type=int, default=50)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--clusters", type=int, default=64)
+    p.add_argument("--users", type=int, default=0,
+                   help="use only the first N users (profiling captures; not the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
@@ -162,7 +164,8 @@ def make_inputs(args, rank):
     from paper_1706_01449_gb300 import synth
     W = synth.WORKLOADS[args.workload]
     f = args.f if "fs" in W else W["f"]
-    U = synth.make_users(W, seed=rank, f=f)
+    n = args.users if getattr(args, "users", 0) else None
+    U = synth.make_users(W, seed=rank, f=f, n=n)
     I = synth.make_items(W, seed=0, f=f)
     return W, f, U, I
 
@@ -342,7 +345,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if dtype == "bf16" else "f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} f={f} K={K}", "n_users": nU, "n_items": nI, "f": f, "K": K,
+        "config": {"workload": f"{args.workload} f={f} K={K}" + (f" first {nU} users" if args.users else ""),
+                   "n_users": nU, "n_items": nI, "f": f, "K": K,
                    "method": args.method, "candidate_pass": dtype, "rescore": "compensated fp32 + fp64 tie check",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
@@ -354,6 +358,8 @@ def main():
                                                        "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
         "candidates_per_user": stats["cand_emitted"] / nU, "rescored_per_user": stats["cand_rescored"] / nU,
         "users_overflow": stats["users_overflow"], "users_fp64": stats["users_fp64"],
+        "select_slow_chunk_frac": (stats["select_slow"] / (((nU + 255) // 256) * 8 * ((nI + 127) // 128) * 8)
+                                   if dtype == "bf16" else None),
     }
     print(json.dumps(line), flush=True)
     index.close()

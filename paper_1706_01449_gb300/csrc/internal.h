@@ -4,7 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/mips.h"
+#include "mips.h"  // include/ is on the include path
 
 namespace mips {
 
@@ -23,8 +23,21 @@ struct DevStats {
   unsigned long long users_fp64;      // users resolved by the FP64 tie check
   unsigned long long pairs_scored;    // (user, item) pairs scored (Maximus walk)
   unsigned long long blocks_walked;   // item blocks processed (Maximus walk)
-  unsigned long long pad[2];
+  unsigned long long select_slow;     // warp-level slow-path entries of the select
+  unsigned long long pad;
 };
+
+// Unsigned key whose ascending order is the float's DESCENDING order.
+__host__ __device__ inline uint32_t float_desc_key(float x) {
+#ifdef __CUDA_ARCH__
+  const uint32_t b = __float_as_uint(x);
+#else
+  uint32_t b;
+  __builtin_memcpy(&b, &x, 4);
+#endif
+  const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+  return ~asc;
+}
 
 // Round n up to a multiple of m.
 inline int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
@@ -40,12 +53,23 @@ void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void*
 void launch_gather_rows(const float* x, const int32_t* perm, int64_t n, int f, float* out, cudaStream_t s);
 
 // ---- FP32 fused score + select (fp32_topk.cu) ------------------------------
+// Candidate output of a score kernel: `lists` sub-lists per user (one per
+// select thread serving the user), sub-list l of user u at index u*lists+l.
 struct SelectOut {
-  float* tau;          // [n_users]
-  int* n_cand;         // [n_users]
-  int32_t* cand_pos;   // [n_users][cap]
-  float* cand_ub;      // [n_users][cap]
-  int cap;
+  float* tau;          // [n_users * lists] final threshold of each sub-list
+  int* n_cand;         // [n_users * lists] candidates emitted (may exceed cap)
+  int32_t* cand_pos;   // [n_users * lists][cap] item positions
+  float* cand_ub;      // [n_users * lists][cap] upper bounds H
+  int cap;             // capacity of one sub-list
+  int lists;
+  // optional: the K largest lower bounds each sub-list's select kept
+  // ([n_users * lists][K]); with two sub-lists the rescore's threshold is the
+  // K-th largest of their union (entries are distinct items)
+  float* topl;
+  int topl_sorted;     // 1: each topl row is sorted descending
+  // users whose candidate list overflowed, for the exhaustive rescore
+  int32_t* ovf_list;   // [n_users]
+  int* ovf_count;      // one counter, zero before the rescore
 };
 bool fp32_supported(int f, int K);
 cudaError_t launch_fp32_score_select(const float* users, int64_t n_users, int f, const float* items,
@@ -57,6 +81,17 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
                            const int32_t* perm, const float* item_nrm_ub, int64_t n_items, int K,
                            SelectOut o, int32_t* out_idx, double* out_score, DevStats* stats,
                            int* err, cudaStream_t s);
+
+// ---- radix sort (sort.cu) --------------------------------------------------
+// Temp bytes for radix_sort_pairs over n_seg segments of n elements.
+size_t radix_sort_temp_bytes(int64_t n, int n_seg);
+// Stable ascending sort of keys[begin_bit, end_bit) with values, per segment;
+// the sorted arrays end up in (keys, vals) (pointers are swapped per pass).
+cudaError_t radix_sort_pairs(uint32_t*& keys, int32_t*& vals, uint32_t*& keys_alt, int32_t*& vals_alt, int64_t n,
+                             int n_seg, int begin_bit, int end_bit, uint32_t* temp, cudaStream_t s, int* launches);
+// keys[i] = float_desc_key(x[i]); iota[i] = i % seg_len (if iota != null).
+cudaError_t make_float_desc_keys(const float* x, int64_t n, uint32_t* keys, int32_t* iota, int64_t seg_len,
+                                 cudaStream_t s);
 
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);

@@ -153,60 +153,66 @@ int cap_for(int K) { return 4 * K + 96; }
 mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
                     double* out_score, cudaStream_t s) {
   const int f = idx->f;
-  const int cap = cap_for(K);
+  // candidate pass: tcgen05 BF16 when the index has BF16 operands and the
+  // tiling fits shared memory for this K, else the FP32 CUDA-core kernel
+  TcParams p{};
+  p.n_users = n_users;
+  p.n_items = idx->n_items;
+  p.f = f;
+  p.fp = idx->fp;
+  p.K = K;
+  const bool use_tc = idx->opt.dtype == MIPS_BF16 && tc_plan(p, idx->max_smem);
+  // BF16: two select threads per user, each with its own sub-list
+  const int lists = use_tc ? 2 : 1;
+  const int cap = lists == 1 ? cap_for(K) : 2 * K + 64;
+  const int64_t nl = n_users * lists;
   idx->ws.reset();
-  size_t o_tau = idx->ws.take(sizeof(float) * n_users);
-  size_t o_n = idx->ws.take(sizeof(int) * n_users);
-  size_t o_pos = idx->ws.take(sizeof(int32_t) * n_users * cap);
-  size_t o_ub = idx->ws.take(sizeof(float) * n_users * cap);
+  size_t o_tau = idx->ws.take(sizeof(float) * nl);
+  size_t o_n = idx->ws.take(sizeof(int) * nl);
+  size_t o_pos = idx->ws.take(sizeof(int32_t) * nl * cap);
+  size_t o_ub = idx->ws.take(sizeof(float) * nl * cap);
+  size_t o_topl = idx->ws.take(sizeof(float) * nl * K);
+  size_t o_ovf = idx->ws.take(sizeof(int32_t) * n_users);
+  size_t o_ovfc = idx->ws.take(sizeof(int));
+  size_t o_ub16 = 0, o_uaux = 0;
+  if (use_tc) {
+    o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
+    o_uaux = idx->ws.take(sizeof(float2) * n_users);
+  }
   MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
-               idx->ws.at<float>(o_ub), cap};
-  if (idx->opt.dtype == MIPS_FP32) {
+               idx->ws.at<float>(o_ub), cap, lists,
+               lists == 2 ? idx->ws.at<float>(o_topl) : nullptr, K <= kRegTopK ? 1 : 0,
+               idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc)};
+  mips_status st;
+  if (!use_tc) {
     MIPS_CUDA(launch_fp32_score_select(users, n_users, f, idx->items, idx->item_nrm, idx->n_items, K, so,
                                        idx->stats_dev, idx->err_dev, s));
     idx->launches += 1;
-    mips_status st = end_stage(idx, ST_SCORE, s);
-    if (st != MIPS_OK) return st;
+    if ((st = end_stage(idx, ST_SCORE, s)) != MIPS_OK) return st;
   } else {
-    TcParams p{};
-    p.n_users = n_users;
-    p.n_items = idx->n_items;
-    p.f = f;
-    p.fp = idx->fp;
-    p.K = K;
-    if (!tc_plan(p, idx->max_smem)) return fail(MIPS_ERR_ARG, "no tcgen05 tiling fits shared memory for f=%d K=%d", f, K);
-    // user operand rows live in the same arena, after the select buffers
-    size_t o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
-    size_t o_uaux = idx->ws.take(sizeof(float2) * n_users);
-    MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
-    so = SelectOut{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
-                   idx->ws.at<float>(o_ub), cap};
     void* ub16 = idx->ws.at<void>(o_ub16);
     float2* uaux = idx->ws.at<float2>(o_uaux);
     launch_quant_bf16(users, n_users, f, idx->fp, 0, ub16, n_users, uaux, idx->err_dev, s);
     MIPS_CUDA(cudaGetLastError());
     idx->launches += 1;
-    mips_status st = end_stage(idx, ST_PREP, s);
-    if (st != MIPS_OK) return st;
+    if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
     CUtensorMap map_users;
-    if (!tc_make_map(&map_users, ub16, n_users, idx->fp, p.row_bytes))
+    if (!tc_make_map(&map_users, ub16, n_users, idx->fp, p.row_bytes, tc_users_per_tile()))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the user operand");
-    const int64_t n_ut = (n_users + p.nh * 128 - 1) / (p.nh * 128);
+    const int64_t n_ut = (n_users + tc_users_per_tile() - 1) / tc_users_per_tile();
     const int grid = (int)(n_ut < idx->num_sms ? n_ut : idx->num_sms);
     MIPS_CUDA(launch_tc_score_select(&map_users, &idx->map_items, p, so, uaux, idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
     idx->launches += 1;
-    st = end_stage(idx, ST_SCORE, s);
-    if (st != MIPS_OK) return st;
+    if ((st = end_stage(idx, ST_SCORE, s)) != MIPS_OK) return st;
   }
   MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, idx->n_items, K, so,
                            out_idx, out_score, idx->stats_dev, idx->err_dev, s));
   idx->launches += 1;
-  mips_status st = end_stage(idx, ST_RESCORE, s);
-  if (st != MIPS_OK) return st;
+  if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
   idx->last_users = n_users;
-  idx->last_dtype = idx->opt.dtype;
+  idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
   return MIPS_OK;
 }
 
@@ -280,22 +286,32 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   BUILD_CUDA(cudaMalloc(&idx->items, sizeof(float) * n_items * f));
   BUILD_CUDA(cudaMalloc(&idx->perm, sizeof(int32_t) * n_items));
   BUILD_CUDA(cudaMalloc(&idx->item_nrm, sizeof(float) * n_items));
-  // item order: identity (sorted position == item id)
+  // item order: by norm bound, descending (ties by item id), so a user's
+  // threshold rises within the first item tiles of every scan
   {
-    int32_t* hperm = (int32_t*)malloc(sizeof(int32_t) * n_items);
-    if (!hperm) return bail(fail(MIPS_ERR_NOMEM, "host allocation failed"));
-    for (int64_t i = 0; i < n_items; ++i) hperm[i] = (int32_t)i;
-    e = cudaMemcpyAsync(idx->perm, hperm, sizeof(int32_t) * n_items, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    free(hperm);
-    if (e != cudaSuccess) return bail(cuda_fail(e, "perm upload"));
+    launch_row_norm_ub(items_dev, n_items, f, idx->item_nrm, idx->err_dev, s);
+    char* tmp = nullptr;
+    const size_t tb = radix_sort_temp_bytes(n_items, 1);
+    const size_t nb4 = round_up(sizeof(uint32_t) * n_items, 256);
+    BUILD_CUDA(cudaMallocAsync((void**)&tmp, 3 * nb4 + tb, s));
+    uint32_t* keys = (uint32_t*)tmp;
+    uint32_t* keys_alt = (uint32_t*)(tmp + nb4);
+    int32_t* vals_alt = (int32_t*)(tmp + 2 * nb4);
+    uint32_t* temp = (uint32_t*)(tmp + 3 * nb4);
+    int32_t* vals = idx->perm;
+    e = make_float_desc_keys(idx->item_nrm, n_items, keys, vals, n_items, s);
+    if (e == cudaSuccess) e = radix_sort_pairs(keys, vals, keys_alt, vals_alt, n_items, 1, 0, 32, temp, s, nullptr);
+    // four passes: the result is back in the first buffers
+    if (e == cudaSuccess && vals != idx->perm) e = cudaErrorUnknown;
+    cudaFreeAsync(tmp, s);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "item norm sort"));
   }
   launch_gather_rows(items_dev, idx->perm, n_items, f, idx->items, s);
   launch_row_norm_ub(idx->items, n_items, f, idx->item_nrm, idx->err_dev, s);
   BUILD_CUDA(cudaGetLastError());
   if (o.dtype == MIPS_BF16) {
     idx->fp = tc_row_len(f);
-    idx->n_items_pad = round_up(n_items, 128);
+    idx->n_items_pad = round_up(n_items, tc_items_per_tile());
     BUILD_CUDA(cudaMalloc(&idx->items_bf16, sizeof(uint16_t) * idx->n_items_pad * idx->fp));
     BUILD_CUDA(cudaMalloc(&idx->item_aux, sizeof(float2) * idx->n_items_pad));
     launch_quant_bf16(idx->items, n_items, f, idx->fp, 1, idx->items_bf16, idx->n_items_pad, idx->item_aux,
@@ -305,8 +321,8 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
     p.fp = idx->fp;
     p.f = f;
     p.K = 1;
-    if (!tc_plan(p, idx->max_smem)) return bail(fail(MIPS_ERR_ARG, "no tcgen05 tiling fits for f=%d", f));
-    if (!tc_make_map(&idx->map_items, idx->items_bf16, idx->n_items_pad, idx->fp, p.row_bytes))
+    tc_plan(p, idx->max_smem);  // chunking only; calls whose tiling does not fit use the FP32 pass
+    if (!tc_make_map(&idx->map_items, idx->items_bf16, idx->n_items_pad, idx->fp, p.row_bytes, tc_items_per_tile()))
       return bail(fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the item operand"));
   }
   BUILD_CUDA(cudaStreamSynchronize(s));
@@ -409,6 +425,7 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out) {
   out->users_fp64 = d.users_fp64;
   out->pairs_scored = d.pairs_scored;
   out->blocks_walked = d.blocks_walked;
+  out->select_slow = d.select_slow;
   out->n_users = idx->last_users;
   out->clusters = idx->last_clusters;
   out->dtype = idx->last_dtype;

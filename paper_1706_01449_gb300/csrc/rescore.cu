@@ -2,29 +2,33 @@
 // of the paper's BMM and of QueryIndex in Algorithm 1: the K best items by
 // u^T i, ties to the smaller item index).
 //
-// One warp per user.  Candidates whose upper bound H reaches the user's
-// final threshold tau are scored with a compensated FP32 dot product (Dot2,
-// see common.cuh) and inserted into a warp-shared list sorted by
-// (score desc, item id asc); the best rejected key is tracked too.  Then
-// every adjacent pair of the list (and the K-th entry against the best
-// rejected one) is checked against the score error bound
-//   e = (2 gamma_2f gamma_f + (f + 2) 2^-53) nhat_u nhat_i_max   (x 2 margin)
-// which covers both this computation and the FP64 definition's own
-// rounding.  Any gap <= 2e (equal values included) makes the user
-// ambiguous, and the user is redone with the FP64 definition's arithmetic
-// itself (sequential sum of exact products), whose ranking is the
-// definition's.  Otherwise the compensated order equals the exact order,
-// which equals the FP64 definition's order.
-//
-// A user whose candidate list overflowed is rescored against every item.
-// A zero user has every score exactly 0: its answer is items 0..K-1.
+// rescore_thread_kernel -- one thread per user:
+//   * threshold tau: the final threshold of its candidate sub-list, or, with
+//     two sub-lists whose K best lower bounds are given, the K-th largest of
+//     their union (the entries belong to distinct items, so this is a valid
+//     lower bound on the user's K-th score);
+//   * every candidate whose upper bound H reaches tau is scored with a
+//     compensated FP32 dot product (Dot2, common.cuh) and inserted into the
+//     thread's sorted list of the K + 1 best keys (score desc, item id asc)
+//     in shared memory;
+//   * tie check: every adjacent pair of that list is compared against the
+//     score error bound
+//       e = (2 gamma_2f gamma_f + (f + 2) 2^-53) nhat_u nhat_i_max  (x 2 margin),
+//     which covers this computation and the FP64 definition's own rounding.
+//     A gap <= 2e (equal values included) redoes the user with the FP64
+//     definition's arithmetic (sequential sum of exact products), whose
+//     ranking is the definition's; otherwise the compensated order equals
+//     the exact order, which equals the FP64 definition's order;
+//   * a zero user has every score exactly 0: its answer is items 0..K-1;
+//   * a user whose candidate list overflowed is queued for
+// rescore_warp_kernel -- one warp per queued user, scoring every item.
 #include "common.cuh"
 
 namespace mips {
 
 namespace {
 
-constexpr int kWarps = 4;
+constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxK = 128;
 constexpr int kMaxF = 128;
 constexpr unsigned kFull = 0xffffffffu;
@@ -33,6 +37,205 @@ __device__ __forceinline__ bool ranks_before(double sa, int ia, double sb, int i
   return sa > sb || (sa == sb && ia < ib);
 }
 
+// Relative score error bound used by the tie check (see the file comment).
+__device__ __forceinline__ double rescore_rel_err(int f) {
+  const double gf = (double)f * 5.9604644775390625e-08;  // f 2^-24
+  const double gamma_f = gf / (1.0 - gf);
+  const double gamma_2f = 2.0 * gamma_f / (1.0 - gamma_f);
+  return 2.0 * (2.0 * gamma_2f * gamma_f + (double)(f + 2) * 1.1102230246251565e-16);
+}
+
+__device__ __forceinline__ double score_dot2(const float* __restrict__ u, const float* __restrict__ v, int f) {
+  Dot2 acc{0.f, 0.f};
+  int k = 0;
+  for (; k + 8 <= f; k += 8) {  // issue the loads of 8 terms before their arithmetic
+    float a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = u[k + j];
+      b[j] = v[k + j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) dot2_step(acc, a[j], b[j]);
+  }
+  for (; k < f; ++k) dot2_step(acc, u[k], v[k]);
+  return dot2_value(acc);
+}
+
+// Sequential FP64 sum of the exact products (the definition's arithmetic),
+// with the loads of 8 terms issued before their arithmetic.
+__device__ __forceinline__ double score_f64(const float* __restrict__ u, const float* __restrict__ v, int f) {
+  double s = 0.0;
+  int k = 0;
+  for (; k + 8 <= f; k += 8) {
+    float a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      a[j] = u[k + j];
+      b[j] = v[k + j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s = __dadd_rn(s, __dmul_rn((double)a[j], (double)b[j]));
+  }
+  for (; k < f; ++k) s = __dadd_rn(s, __dmul_rn((double)u[k], (double)v[k]));
+  return s;
+}
+
+// Binary heap of at most L keys (score, id) in a thread's shared-memory
+// column (entry p at [p * T + t]); the root is the key that ranks last, so a
+// new key that ranks before the root replaces it.
+struct KeyHeap {
+  double* s;
+  int* id;
+  int T;
+  __device__ __forceinline__ double sv(int p) const { return s[p * T]; }
+  __device__ __forceinline__ int iv(int p) const { return id[p * T]; }
+  __device__ __forceinline__ void put(int p, double v, int i) {
+    s[p * T] = v;
+    id[p * T] = i;
+  }
+  // worse(a, b): a ranks after b
+  __device__ __forceinline__ void sift_down(int p, int n, double v, int i) {
+    while (true) {
+      int c = 2 * p + 1;
+      if (c >= n) break;
+      if (c + 1 < n && ranks_before(sv(c), iv(c), sv(c + 1), iv(c + 1))) ++c;  // the worse child
+      if (!ranks_before(v, i, sv(c), iv(c))) break;  // v is already worse than both children
+      put(p, sv(c), iv(c));
+      p = c;
+    }
+    put(p, v, i);
+  }
+  __device__ __forceinline__ void push(int& n, int L, double v, int i) {
+    if (n < L) {
+      int p = n++;
+      while (p > 0) {
+        const int q = (p - 1) / 2;
+        if (!ranks_before(sv(q), iv(q), v, i)) break;  // parent already worse
+        put(p, sv(q), iv(q));
+        p = q;
+      }
+      put(p, v, i);
+    } else if (ranks_before(v, i, sv(0), iv(0))) {
+      sift_down(0, n, v, i);
+    }
+  }
+  // In place: entries 0..n-1 best first.
+  __device__ __forceinline__ void sort(int n) {
+    for (int m = n - 1; m > 0; --m) {
+      const double v = sv(m);
+      const int i = iv(m);
+      put(m, sv(0), iv(0));  // the worst of 0..m goes to m
+      sift_down(0, m, v, i);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// thread per user
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    rescore_thread_kernel(const float* __restrict__ users, int64_t n_users, int f,
+                          const float* __restrict__ items, const int32_t* __restrict__ perm,
+                          const float* __restrict__ item_nrm, int K, SelectOut o, int32_t* __restrict__ out_idx,
+                          double* __restrict__ out_score, DevStats* stats, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int L = K + 1;  // list length: the K best and the best of the rest
+  double* ls = reinterpret_cast<double*>(smem_raw);  // [L][T]
+  int* li = reinterpret_cast<int*>(ls + (size_t)L * T);
+  const int64_t u = (int64_t)blockIdx.x * T + t;
+  unsigned long long n_rescored = 0, n_over = 0, n_fp64 = 0;
+
+  if (u < n_users) {
+    const float* ur = users + u * f;
+    float ss = 0.f;
+    for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
+    if (ss == 0.f) {  // zero user: every score is exactly 0
+      for (int k = 0; k < K; ++k) {
+        out_idx[u * K + k] = k;
+        out_score[u * K + k] = 0.0;
+      }
+    } else {
+      const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
+      // threshold
+      float tau;
+      const int64_t l0 = u * o.lists;
+      if (o.lists == 1) {
+        tau = o.tau[l0];
+      } else if (o.topl && o.topl_sorted) {
+        const float* a = o.topl + l0 * K;
+        const float* b = a + K;
+        int ia = 0, ib = 0;
+        float v = __int_as_float(0xff800000);
+        for (int r = 0; r < K; ++r) {
+          if (a[ia] >= b[ib]) v = a[ia++];
+          else v = b[ib++];
+        }
+        tau = fmaxf(v, fmaxf(o.tau[l0], o.tau[l0 + 1]));
+      } else {
+        tau = fmaxf(o.tau[l0], o.tau[l0 + 1]);
+      }
+      int n[2] = {o.n_cand[l0], o.lists == 2 ? o.n_cand[l0 + 1] : 0};
+      if (n[0] > o.cap || n[1] > o.cap) {
+        const int slot = atomicAdd(o.ovf_count, 1);
+        o.ovf_list[slot] = (int32_t)u;
+        n_over = 1;
+      } else {
+        const double rel_e = rescore_rel_err(f);
+        KeyHeap heap{ls + t, li + t, T};
+        for (int mode = 0; mode < 2; ++mode) {
+          int cnt = 0;
+          float nmax = 0.f;
+          for (int l = 0; l < o.lists; ++l) {
+            const int32_t* cp = o.cand_pos + (l0 + l) * (int64_t)o.cap;
+            const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
+            for (int c = 0; c < n[l]; ++c) {
+              if (cu[c] < tau) continue;
+              const int32_t pos = cp[c];
+              const int id = perm[pos];
+              const float* row = items + (int64_t)pos * f;
+              const double v = mode == 0 ? score_dot2(ur, row, f) : score_f64(ur, row, f);
+              nmax = fmaxf(nmax, item_nrm[pos]);
+              if (mode == 0) ++n_rescored;
+              heap.push(cnt, L, v, id);
+            }
+          }
+          heap.sort(cnt);
+          if (cnt < K) {  // cannot happen: K lower bounds back tau
+            atomicOr(err, DEV_ERR_INTERNAL);
+            break;
+          }
+          if (mode == 1) break;
+          const double e2 = 2.0 * rel_e * nu * (double)nmax;
+          bool amb = false;
+          for (int p = 0; p + 1 < cnt; ++p) amb |= (ls[p * T + t] - ls[(p + 1) * T + t]) <= e2;
+          if (!amb) break;
+          ++n_fp64;
+        }
+        for (int k = 0; k < K; ++k) {
+          out_idx[u * K + k] = li[k * T + t];
+          out_score[u * K + k] = ls[k * T + t];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    n_rescored += __shfl_xor_sync(kFull, n_rescored, off);
+    n_over += __shfl_xor_sync(kFull, n_over, off);
+    n_fp64 += __shfl_xor_sync(kFull, n_fp64, off);
+  }
+  if ((t & 31) == 0) {
+    if (n_rescored) atomicAdd(&stats->cand_rescored, n_rescored);
+    if (n_over) atomicAdd(&stats->users_overflow, n_over);
+    if (n_fp64) atomicAdd(&stats->users_fp64, n_fp64);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// warp per user, every item (users whose candidate list overflowed)
+// ---------------------------------------------------------------------------
 struct WarpList {
   double* s;  // [kMaxK]
   int* id;    // [kMaxK]
@@ -88,23 +291,21 @@ struct WarpList {
   }
 };
 
-__global__ void __launch_bounds__(kWarps * 32)
-    rescore_kernel(const float* __restrict__ users, int64_t n_users, int f,
-                   const float* __restrict__ items, const int32_t* __restrict__ perm,
-                   const float* __restrict__ item_nrm, int64_t n_items, int K, SelectOut o,
-                   int32_t* __restrict__ out_idx, double* __restrict__ out_score, DevStats* stats,
-                   int* err) {
-  __shared__ double s_s[kWarps][kMaxK];
-  __shared__ int s_id[kWarps][kMaxK];
-  __shared__ float s_u[kWarps][kMaxF];
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    rescore_warp_kernel(const float* __restrict__ users, int f, const float* __restrict__ items,
+                        const int32_t* __restrict__ perm, const float* __restrict__ item_nrm, int64_t n_items, int K,
+                        const int32_t* __restrict__ list, const int* __restrict__ list_count,
+                        int32_t* __restrict__ out_idx, double* __restrict__ out_score, DevStats* stats, int* err) {
+  __shared__ double s_s[kWarpsPerBlock][kMaxK];
+  __shared__ int s_id[kWarpsPerBlock][kMaxK];
+  __shared__ float s_u[kWarpsPerBlock][kMaxF];
   const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
-  const float gf = (float)f * 5.9604645e-08f;
-  const double gamma_f = (double)gf / (1.0 - (double)gf);
-  const double gamma_2f = 2.0 * gamma_f / (1.0 - gamma_f);
-  const double rel_e = 2.0 * (2.0 * gamma_2f * gamma_f + (double)(f + 2) * 1.1102230246251565e-16);
-  unsigned long long n_rescored = 0, n_over = 0, n_fp64 = 0;
+  const double rel_e = rescore_rel_err(f);
+  unsigned long long n_fp64 = 0;
+  const int count = *list_count;
 
-  for (int64_t u = (int64_t)blockIdx.x * kWarps + w; u < n_users; u += (int64_t)gridDim.x * kWarps) {
+  for (int q = blockIdx.x * kWarpsPerBlock + w; q < count; q += gridDim.x * kWarpsPerBlock) {
+    const int64_t u = list[q];
     float ss = 0.f;
     for (int k = lane; k < f; k += 32) {
       float v = users[u * f + k];
@@ -114,78 +315,46 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(kFull, ss, off);
     __syncwarp();
-    if (ss == 0.f) {  // zero user: every score is exactly 0
-      for (int k = lane; k < K; k += 32) {
-        out_idx[u * K + k] = k;
-        out_score[u * K + k] = 0.0;
-      }
-      continue;
-    }
     const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
-    const int n = o.n_cand[u];
-    const float tau = o.tau[u];
-    const bool overflow = n > o.cap;
-    const int64_t nn = overflow ? n_items : (int64_t)n;
-    n_over += overflow;
-    const int32_t* cpos = o.cand_pos + u * (int64_t)o.cap;
-    const float* cub = o.cand_ub + u * (int64_t)o.cap;
-
     for (int mode = 0; mode < 2; ++mode) {
-      WarpList L{s_s[w], s_id[w], 0, false, 0.0, 0};
+      WarpList Lw{s_s[w], s_id[w], 0, false, 0.0, 0};
       float nmax = 0.f;
-      for (int64_t base = 0; base < nn; base += 32) {
+      for (int64_t base = 0; base < n_items; base += 32) {
         const int64_t t = base + lane;
-        bool valid = t < nn;
-        int32_t pos = 0;
-        if (valid) {
-          if (overflow) {
-            pos = (int32_t)t;
-          } else {
-            pos = cpos[t];
-            valid = cub[t] >= tau;
-          }
-        }
+        const bool valid = t < n_items;
         double v = 0.0;
         int id = 0;
         if (valid) {
-          id = perm[pos];
-          const float* row = items + (int64_t)pos * f;
-          nmax = fmaxf(nmax, item_nrm[pos]);
-          if (mode == 0) {
-            Dot2 acc{0.f, 0.f};
-            for (int k = 0; k < f; ++k) dot2_step(acc, s_u[w][k], row[k]);
-            v = dot2_value(acc);
-          } else {
-            v = dot_f64_seq(s_u[w], row, f);
-          }
+          id = perm[t];
+          const float* row = items + t * f;
+          nmax = fmaxf(nmax, item_nrm[t]);
+          v = mode == 0 ? score_dot2(s_u[w], row, f) : dot_f64_seq(s_u[w], row, f);
         }
-        if (mode == 0 && !overflow) n_rescored += valid;
         unsigned mask = __ballot_sync(kFull, valid);
         while (mask) {
           const int src = __ffs(mask) - 1;
           mask &= mask - 1;
           const double vs = __shfl_sync(kFull, v, src);
           const int is = __shfl_sync(kFull, id, src);
-          if (L.has_out && !ranks_before(vs, is, L.out_s, L.out_id)) continue;
-          L.insert(vs, is, K, lane);
+          if (Lw.has_out && !ranks_before(vs, is, Lw.out_s, Lw.out_id)) continue;
+          Lw.insert(vs, is, K, lane);
         }
       }
+      if (Lw.cnt < K) {
+        if (lane == 0) atomicOr(err, DEV_ERR_INTERNAL);
+        break;
+      }
       if (mode == 1) break;
-      // tie check on the compensated scores
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(kFull, nmax, off));
       const double e2 = 2.0 * rel_e * nu * (double)nmax;
       bool amb = false;
-      for (int p0 = 0; p0 < L.cnt; p0 += 32) {
+      for (int p0 = 0; p0 < Lw.cnt; p0 += 32) {
         const int p = p0 + lane;
         bool a = false;
-        if (p + 1 < L.cnt) a = (L.s[p] - L.s[p + 1]) <= e2;
-        if (p == L.cnt - 1 && L.has_out && L.cnt == K) a = (L.s[p] - L.out_s) <= e2;
+        if (p + 1 < Lw.cnt) a = (Lw.s[p] - Lw.s[p + 1]) <= e2;
+        if (p == Lw.cnt - 1 && Lw.has_out && Lw.cnt == K) a = (Lw.s[p] - Lw.out_s) <= e2;
         amb |= __any_sync(kFull, a) != 0;
-      }
-      if (L.cnt < K) {  // cannot happen: K lower bounds back tau
-        if (lane == 0) atomicOr(err, DEV_ERR_INTERNAL);
-        break;
       }
       if (!amb) break;
       ++n_fp64;
@@ -197,13 +366,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     __syncwarp();
   }
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) n_rescored += __shfl_xor_sync(kFull, n_rescored, off);
-  if (lane == 0) {
-    if (n_rescored) atomicAdd(&stats->cand_rescored, n_rescored);
-    if (n_over) atomicAdd(&stats->users_overflow, n_over);
-    if (n_fp64) atomicAdd(&stats->users_fp64, n_fp64);
-  }
+  if (lane == 0 && n_fp64) atomicAdd(&stats->users_fp64, n_fp64);
 }
 
 }  // namespace
@@ -213,10 +376,20 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
                            SelectOut o, int32_t* out_idx, double* out_score, DevStats* stats,
                            int* err, cudaStream_t s) {
   if (K > kMaxK || f > kMaxF) return cudaErrorInvalidValue;
-  int64_t blocks = (n_users + kWarps - 1) / kWarps;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  rescore_kernel<<<(unsigned)blocks, kWarps * 32, 0, s>>>(users, n_users, f, items_sorted, perm, item_nrm_ub,
-                                                          n_items, K, o, out_idx, out_score, stats, err);
+  // threads per block so that the per-thread lists of K + 1 keys fit in 96 KiB
+  int T = 128;
+  while (T > 32 && (size_t)T * (K + 1) * 12 > 96 * 1024) T -= 32;
+  const size_t smem = (size_t)T * (K + 1) * 12;
+  cudaError_t e = cudaFuncSetAttribute(rescore_thread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(o.ovf_count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  rescore_thread_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
+                                                                           item_nrm_ub, K, o, out_idx, out_score,
+                                                                           stats, err);
+  rescore_warp_kernel<<<152 * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,
+                                                             o.ovf_list, o.ovf_count, out_idx, out_score, stats,
+                                                             err);
   return cudaGetLastError();
 }
 

@@ -11,12 +11,10 @@ bool tc_plan(TcParams& p, int max_smem) {
   p.kc = p.fp / p.row_elems;
   p.swizzle = p.row_bytes == 32 ? 6 : (p.row_bytes == 64 ? 4 : 2);
   p.g = (float)(p.fp + 4) * 9.5367432e-07f + (float)p.f * 8.8817842e-16f;
-  for (int nh = 2; nh >= 1; --nh) {
-    for (int st = kMaxStages; st >= 2; --st) {
-      p.nh = nh;
-      p.stages = st;
-      if (tc_smem_bytes(p) <= (size_t)max_smem) return true;
-    }
+  p.stages = 2;
+  for (int st = kMaxStages; st >= 2; --st) {
+    p.stages = st;
+    if (tc_smem_bytes(p) <= (size_t)max_smem) return true;
   }
   return false;
 }
@@ -40,13 +38,13 @@ EncodeTiledFn encode_fn() {
 }
 }  // namespace
 
-bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes) {
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows) {
   EncodeTiledFn enc = encode_fn();
   if (!enc) return false;
   memset(map, 0, sizeof(*map));
   cuuint64_t dims[2] = {(cuuint64_t)fp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)fp * 2};
-  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / 2), 128u};
+  cuuint32_t box[2] = {(cuuint32_t)(row_bytes / 2), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   CUtensorMapSwizzle sw = row_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                           : (row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);

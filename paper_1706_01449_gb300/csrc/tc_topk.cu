@@ -2,24 +2,27 @@
 // cores (the paper's BMM, Sec. III-B, with the per-user selection fused so
 // the |U| x |I| score matrix never leaves the SM).
 //
-// Persistent kernel, one CTA per SM, 12 warps:
-//   warp 0      TMA producer: the CTA's user tile (UT = 128 * NH rows, NH in
-//               {1, 2}) once per tile, then item tiles of 128 rows through an
-//               S-stage shared-memory ring;
-//   warp 1      MMA issuer (one thread): for each item tile and user half h,
-//               D[h] = A[h] . B^T with tcgen05.mma kind::f16 (BF16 x BF16 ->
-//               FP32) into a TMEM accumulator of 128 lanes x 128 columns;
-//               two accumulator buffers, so the MMAs of item tile j+1 overlap
-//               the select of tile j;
+// Persistent kernel, one CTA per SM, 12 warps, user tiles of 128 rows and
+// item tiles of 256 rows (an M = 128, N = 256 MMA runs at the tensor pipe's
+// full rate; N = 128 costs nearly the same time per instruction):
+//   warp 0      TMA producer: the user tile once per tile, then item tiles
+//               through an S-stage shared-memory ring;
+//   warp 1      MMA issuer (one thread): D = A . B^T with tcgen05.mma
+//               kind::f16 (BF16 x BF16 -> FP32) into one of two TMEM
+//               accumulators of 128 lanes x 256 columns, so the MMAs of item
+//               tile j+1 overlap the select of tile j;
 //   warp 2      allocates / frees TMEM;
-//   warps 4..   select: thread t of epilogue warp e owns user row
-//               h * 128 + 32 * (e % 4) + t (TMEM lane restriction: a warp
-//               reads lanes 32 * (warp % 4) .. + 31), loads its 128 scores
-//               per item tile with tcgen05.ld, and keeps the per-user select
-//               state of common.cuh.
-// Operands are K-major rows (see prep.cu): the two bound columns make every
+//   warps 4-11  select: epilogue warp e reads TMEM lanes 32 * (e % 4) .. +31
+//               (a warp may only touch the lane quarter of its warp % 4) and
+//               columns 128 * (e / 4) .. +127 of each item tile, so every
+//               user is served by two threads, each with its own threshold,
+//               top-K of lower bounds and candidate sub-list; the two share
+//               their thresholds through shared memory (either one is a valid
+//               lower bound on the user's K-th score, so the larger filters
+//               both halves).
+// Operands are K-major rows (prep.cu): the two bound columns make every
 // accumulator entry an upper bound H >= u^T i, so the common case costs one
-// three-input max per two scores plus one compare per 64 scores.
+// maximum over 16 scores and a compare.
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel
 // raises DEV_ERR_TIMEOUT, every role leaves its loop, the MMA thread drains
@@ -37,8 +40,12 @@ namespace {
 
 constexpr int kWarps = 12;
 constexpr int kEpiWarp0 = 4;
-constexpr int kTileN = 128;    // items per tile (MMA N)
-constexpr int kTileM = 128;    // users per half (MMA M)
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTileN = 256;    // items per tile (MMA N)
+constexpr int kTileM = 128;    // users per tile (MMA M)
+constexpr int kHalfN = 128;    // columns per epilogue thread and tile
+constexpr int kQueue = 16;     // hit-queue slots per thread
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -73,8 +80,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity.  Returns false when the
 // CTA is aborting (this or another role timed out).
-__device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -85,6 +91,11 @@ __device__ __noinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile 
       return false;
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, err);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
@@ -148,44 +159,179 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   return r;
 }
 
-struct TcUser {
-  UserSelect st;
-  float beta_u, nhat_u;  // bound columns of this user (prep.cu)
-  float g;               // accumulation-error factor of prep.cu
-};
-
-// Slow path for one score: lower bound L from the bound columns, then offer.
-//   A = beta_u nhat_i + nhat_u alpha_i,  L = H - 2A - g (nhat_u nhat_i + A),
-// evaluated with outward margins for the FP32 rounding of this arithmetic.
-__device__ __noinline__ void tc_offer(TcUser& s, float H, int32_t pos, const float2* __restrict__ item_aux) {
-  const float2 ia = item_aux[pos];  // {nhat_i, alpha_i}
-  const float A = __fmaf_rn(s.beta_u, ia.x, s.nhat_u * ia.y);
-  const float nn = s.nhat_u * ia.x;
-  const float slack = __fmaf_rn(2.0f, A, s.g * (nn + A)) * (1.0f + 3.814697265625e-06f);  // 2^-18
-  const float L = (H - slack) - fabsf(H) * 2.384185791015625e-07f;                     // 2^-22
-  s.st.offer(H, L, pos);
+// A threshold published for the partner thread, tagged with its user tile
+// so that a value from another user is never taken.
+__device__ __forceinline__ unsigned long long pack_tau(float t, int ut) {
+  return ((unsigned long long)(uint32_t)ut << 32) | (unsigned long long)__float_as_uint(t);
 }
 
-__device__ __forceinline__ void select64(TcUser& s, uint32_t (&r)[64], int32_t pos0, int valid,
-                                         const float2* __restrict__ item_aux) {
+// Per-thread select state (registers).  KR > 0: the K largest lower bounds
+// live in a register array d[0..KR-1] sorted descending (K <= KR); KR = 0:
+// in the shared-memory min-heap of common.cuh.
+template <int KR>
+struct TcUser {
+  float tau;      // this thread's K-th largest lower bound so far
+  float tau_eff;  // max(tau, partner thread's tau): the filter threshold
+  int n_cand;
+  int ut;         // current user tile (tag of the published threshold)
+  float beta_u, nhat_u;  // bound columns of this user (prep.cu)
+  float d[KR > 0 ? KR : 1];
+};
+
+// Warp-uniform parameters of the select.
+struct TcSel {
+  float* heap;        // &heap_base[slot] (stride kEpiThreads), KR = 0 only
+  int K;
+  int cap;
+  int32_t* cand_pos;  // this thread's candidate sub-list
+  float* cand_ub;
+  float* qh;          // hit queue: qh[t * kEpiThreads]
+  int32_t* qp;
+  volatile unsigned long long* tau_mine;  // published thresholds: mine, partner's
+  const volatile unsigned long long* tau_partner;
+  float g;            // accumulation-error factor of prep.cu
+};
+
+template <int KR>
+__device__ __forceinline__ void topk_init(TcUser<KR>& s, const TcSel& c) {
+  if constexpr (KR > 0) {
+#pragma unroll
+    for (int i = 0; i < KR; ++i) s.d[i] = kNegInf;
+  } else {
+    heap_init(c.heap, kEpiThreads, c.K);
+  }
+}
+
+// Insert lower bound L (> the current K-th largest) and return the new K-th
+// largest.
+template <int KR>
+__device__ __forceinline__ float topk_insert(TcUser<KR>& s, const TcSel& c, float L) {
+  if constexpr (KR > 0) {
+    float nd[KR];
+    nd[0] = fmaxf(s.d[0], L);
+#pragma unroll
+    for (int i = 1; i < KR; ++i) nd[i] = (L > s.d[i - 1]) ? s.d[i - 1] : fmaxf(s.d[i], L);
+    float t = nd[0];  // ends as nd[K - 1] (static indices keep d in registers)
+#pragma unroll
+    for (int i = 0; i < KR; ++i) {
+      s.d[i] = nd[i];
+      t = (i < c.K) ? nd[i] : t;
+    }
+    return t;
+  } else {
+    return heap_replace_min(c.heap, kEpiThreads, c.K, L);
+  }
+}
+
+// Lower bound of the exact score from the upper bound H and the bound
+// columns:  A = beta_u nhat_i + nhat_u alpha_i,  L = H - 2A - g (nhat_u nhat_i + A),
+// evaluated with outward margins for the FP32 rounding of this arithmetic.
+template <int KR>
+__device__ __forceinline__ float tc_lower(const TcUser<KR>& s, const TcSel& c, float H, float2 ia) {
+  const float A = __fmaf_rn(s.beta_u, ia.x, s.nhat_u * ia.y);
+  const float nn = s.nhat_u * ia.x;
+  const float slack = __fmaf_rn(2.0f, A, c.g * (nn + A)) * (1.0f + 3.814697265625e-06f);  // 2^-18
+  return (H - slack) - fabsf(H) * 2.384185791015625e-07f;                             // 2^-22
+}
+
+// Publish this thread's threshold (tagged with its user tile) for the partner.
+template <int KR>
+__device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) {
+  *c.tau_mine = pack_tau(s.tau, s.ut);
+}
+
+// One hit (H >= tau_eff when queued): threshold update from its lower bound,
+// then the candidate emission.  Lower bounds at or below the current filter
+// threshold cannot raise it and are not kept.  With emit_only (second pass
+// over a user tile's first item tile, whose lower bounds are already in the
+// top-K) only the emission is done, so no item is counted twice.
+template <int KR>
+__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int32_t pos, const float2* aux_tile,
+                                         bool emit_only) {
+  if (H < s.tau_eff) return;  // the threshold rose since the hit was queued
+  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux_tile[pos & (kHalfN - 1)]);
+  if (L > s.tau_eff) {
+    s.tau = topk_insert(s, c, L);
+    if (s.tau > s.tau_eff) {
+      s.tau_eff = s.tau;
+      tc_publish(s, c);
+    }
+  }
+  if (H >= s.tau_eff) {
+    if (s.n_cand < c.cap) {
+      c.cand_pos[s.n_cand] = pos;
+      c.cand_ub[s.n_cand] = H;
+    }
+    ++s.n_cand;
+  }
+}
+
+// 16 scores r[0..15] of items pos0.. (valid: how many are real items).
+// Fast path: one maximum over the 16 and a compare.  Slow path (any lane of
+// the warp has a hit): this thread's hits are queued in shared memory, then
+// drained in order through one offer site.
+template <int KR>
+__device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const uint32_t* r, int32_t pos0, int valid,
+                                         const float2* aux_tile, unsigned long long& slow, bool emit_only) {
+  const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
+  const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
+  const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
+  const float m3 = max3(__uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
+  const float m4 = max3(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]));
+  const float mm = max3(max3(m0, m1, m2), m3, fmaxf(m4, __uint_as_float(r[15])));
+  const bool hit = mm >= s.tau_eff;
+  if (__any_sync(0xffffffffu, hit)) {
+    ++slow;
+    int n = 0;
+    if (hit) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float v = __uint_as_float(r[q]);
+        if (v >= s.tau_eff && q < valid) {
+          c.qh[n * kEpiThreads] = v;
+          c.qp[n * kEpiThreads] = pos0 + q;
+          ++n;
+        }
+      }
+    }
+    for (int t = 0; t < n; ++t) tc_offer(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, emit_only);
+  }
+}
+
+template <int KR>
+__device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t (&r)[64], int32_t pos0, int valid,
+                                         const float2* aux_tile, unsigned long long& slow, bool emit_only) {
   if (valid < 64) {
 #pragma unroll
     for (int q = 0; q < 64; ++q)
       if (q >= valid) r[q] = 0xff800000u;  // -inf
   }
-  float m[21];
 #pragma unroll
-  for (int q = 0; q < 21; ++q)
-    m[q] = max3(__uint_as_float(r[3 * q]), __uint_as_float(r[3 * q + 1]), __uint_as_float(r[3 * q + 2]));
-  float a = max3(m[0], m[1], m[2]), b = max3(m[3], m[4], m[5]), c = max3(m[6], m[7], m[8]);
-  float d = max3(m[9], m[10], m[11]), e = max3(m[12], m[13], m[14]), f = max3(m[15], m[16], m[17]);
-  float g = max3(m[18], m[19], m[20]);
-  float mm = max3(max3(a, b, c), max3(d, e, f), fmaxf(g, __uint_as_float(r[63])));
-  if (mm >= s.st.tau) {
+  for (int g = 0; g < 4; ++g) select16(s, c, r + 16 * g, pos0 + 16 * g, valid - 16 * g, aux_tile, slow, emit_only);
+}
+
+// First pass over a user tile's first item tile: every score's lower bound
+// goes through the top-K (nothing is emitted), so the threshold starts the
+// scan near its final value instead of at -inf.  The columns are the items
+// of largest norm (the index stores items by norm, descending).
+template <int KR>
+__device__ __forceinline__ void seed64(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[64], int col0, int valid,
+                                       const float2* aux_tile) {
 #pragma unroll
-    for (int q = 0; q < 64; ++q) {
-      const float v = __uint_as_float(r[q]);
-      if (v >= s.st.tau && q < valid) tc_offer(s, v, pos0 + q, item_aux);
+  for (int g = 0; g < 4; ++g) {
+    // lower bounds above the current threshold are queued, then inserted
+    int n = 0;
+#pragma unroll
+    for (int q = 16 * g; q < 16 * g + 16; ++q) {
+      const float L = tc_lower(s, c, __uint_as_float(r[q]), aux_tile[col0 + q]);
+      if (L > s.tau && q < valid) {
+        c.qh[n * kEpiThreads] = L;
+        ++n;
+      }
+    }
+    for (int t = 0; t < n; ++t) {
+      const float L = c.qh[t * kEpiThreads];
+      if (L > s.tau) s.tau = topk_insert(s, c, L);
     }
   }
 }
@@ -200,24 +346,30 @@ struct Smem {
   int abort_flag;
 };
 
+template <int KR>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     tc_score_select_kernel(const __grid_constant__ CUtensorMap map_users, const __grid_constant__ CUtensorMap map_items,
                            TcParams p, SelectOut o, const float2* __restrict__ user_aux,
                            const float2* __restrict__ item_aux, DevStats* stats, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-up: A tiles, B ring, heap, control block
+  // 1024-byte aligned carve-up (sizes in tc_smem_bytes)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const uint32_t chunk_bytes = kTileM * p.row_bytes;  // one K chunk of a 128-row tile
-  unsigned char* a_tiles = base;                                            // [NH][KC][chunk]
-  unsigned char* b_tiles = a_tiles + (size_t)p.nh * p.kc * chunk_bytes;    // [S][KC][chunk]
-  float* heap_base = (float*)(b_tiles + (size_t)p.stages * p.kc * chunk_bytes);  // [K][NH*128]
-  Smem* ctl = (Smem*)(heap_base + (size_t)p.K * p.nh * kTileM);
+  const uint32_t a_chunk = kTileM * p.row_bytes;  // one K chunk of the user tile
+  const uint32_t b_chunk = kTileN * p.row_bytes;  // one K chunk of an item tile
+  unsigned char* a_tiles = base;                                              // [KC][a_chunk]
+  unsigned char* b_tiles = a_tiles + (size_t)p.kc * a_chunk;                  // [S][KC][b_chunk]
+  float* heap_base = (float*)(b_tiles + (size_t)p.stages * p.kc * b_chunk);   // [K][256] (KR = 0)
+  float2* aux_base = (float2*)(heap_base + (KR > 0 ? 0 : (size_t)p.K * kEpiThreads));  // [8 warps][128]
+  float* qh_base = (float*)(aux_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
+  int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
+  unsigned long long* tau_sh = (unsigned long long*)(qp_base + (size_t)kQueue * kEpiThreads);  // [256]
+  Smem* ctl = (Smem*)(tau_sh + kEpiThreads);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ctl->abort_flag;
-  const int n_ut = (int)((p.n_users + p.nh * kTileM - 1) / (p.nh * kTileM));
+  const int n_ut = (int)((p.n_users + kTileM - 1) / kTileM);
   const int n_it = (int)((p.n_items + kTileN - 1) / kTileN);
-  const uint32_t tmem_cols = p.nh == 2 ? 512u : 256u;
+  constexpr uint32_t kTmemCols = 2 * kTileN;  // two accumulators
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -228,15 +380,16 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     mbar_init(&ctl->a_empty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->acc_full[b], 1);
-      mbar_init(&ctl->acc_empty[b], 4 * p.nh);
+      mbar_init(&ctl->acc_empty[b], kEpiWarps);
     }
     mbar_init(&ctl->drain, 1);
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  for (int i = threadIdx.x; i < kEpiThreads; i += blockDim.x) tau_sh[i] = pack_tau(kNegInf, -1);
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
-                 "r"(tmem_cols)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -250,25 +403,29 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_users)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_items)) : "memory");
-      long long g = 0;
+      long long g = 0;  // item tiles issued so far
+      int st = 0;        // ring stage of tile g
+      uint32_t ph = 0;   // ring pass parity of tile g
       int lt = 0;
       bool ok = true;
+      const uint32_t b_bytes = p.kc * b_chunk;
       for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
         if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
         if (!ok) break;
-        mbar_expect_tx(&ctl->a_full, p.nh * p.kc * chunk_bytes);
-        for (int h = 0; h < p.nh; ++h)
-          for (int c = 0; c < p.kc; ++c)
-            tma_load_2d(a_tiles + (size_t)(h * p.kc + c) * chunk_bytes, &map_users, c * p.row_elems,
-                        ut * p.nh * kTileM + h * kTileM, &ctl->a_full);
+        mbar_expect_tx(&ctl->a_full, p.kc * a_chunk);
+        for (int c = 0; c < p.kc; ++c)
+          tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, ut * kTileM, &ctl->a_full);
         for (int j = 0; j < n_it; ++j, ++g) {
-          const int s = (int)(g % p.stages);
-          if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[s], (uint32_t)(((g / p.stages) - 1) & 1), abort_flag, err);
+          if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
           if (!ok) break;
-          mbar_expect_tx(&ctl->b_full[s], p.kc * chunk_bytes);
+          mbar_expect_tx(&ctl->b_full[st], b_bytes);
+          unsigned char* dst = b_tiles + (size_t)st * b_bytes;
           for (int c = 0; c < p.kc; ++c)
-            tma_load_2d(b_tiles + (size_t)(s * p.kc + c) * chunk_bytes, &map_items, c * p.row_elems, j * kTileN,
-                        &ctl->b_full[s]);
+            tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, j * kTileN, &ctl->b_full[st]);
+          if (++st == p.stages) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
       }
       if (!ok) {  // drain the copies still in flight before the CTA exits
@@ -288,7 +445,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
                              ((uint32_t)(kTileM >> 4) << 24);
       const uint32_t sbo = 8 * p.row_bytes;
       const int ksteps = p.row_bytes / 32;  // K = 16 BF16 = 32 bytes per MMA
+      // descriptors of the first A chunk and of ring stage 0; every other
+      // operand is a fixed address offset, added to the 14-bit address field
+      // (addresses >> 4), as is the 32-byte step of each K = 16 slice
+      const uint64_t a_desc0 = smem_desc(smem_u32(a_tiles), sbo, p.swizzle);
+      const uint64_t b_desc0 = smem_desc(smem_u32(b_tiles), sbo, p.swizzle);
+      const uint32_t a16 = a_chunk >> 4, b16 = b_chunk >> 4;
+      const uint32_t stage16 = (p.kc * b_chunk) >> 4;
       long long g = 0;
+      int st = 0;
+      uint32_t ph = 0;   // ring pass parity
+      int b = 0;         // accumulator of tile g
+      uint32_t aph = 0;  // accumulator pass parity
       int lt = 0;
       bool ok = true;
       for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
@@ -296,25 +464,26 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         if (!ok) break;
         tc_fence_after();
         for (int j = 0; j < n_it; ++j, ++g) {
-          const int s = (int)(g % p.stages);
-          const int b = (int)(g & 1);
-          ok = mbar_wait(&ctl->b_full[s], (uint32_t)((g / p.stages) & 1), abort_flag, err);
-          if (ok && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], (uint32_t)(((g >> 1) - 1) & 1), abort_flag, err);
+          ok = mbar_wait(&ctl->b_full[st], ph, abort_flag, err);
+          if (ok && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, abort_flag, err);
           if (!ok) break;
           tc_fence_after();
-          for (int h = 0; h < p.nh; ++h) {
-            const uint32_t d = tmem + (uint32_t)(b * p.nh * kTileN + h * kTileN);
-            for (int c = 0; c < p.kc; ++c) {
-              const uint32_t a_addr = smem_u32(a_tiles + (size_t)(h * p.kc + c) * chunk_bytes);
-              const uint32_t b_addr = smem_u32(b_tiles + (size_t)(s * p.kc + c) * chunk_bytes);
-              for (int k = 0; k < ksteps; ++k) {
-                mma_bf16(d, smem_desc(a_addr + 32 * k, sbo, p.swizzle), smem_desc(b_addr + 32 * k, sbo, p.swizzle),
-                         idesc, (c | k) != 0);
-              }
-            }
+          const uint32_t d = tmem + (uint32_t)(b * kTileN);
+          const uint64_t bst = b_desc0 + (uint64_t)(st * stage16);
+          for (int c = 0; c < p.kc; ++c) {
+            const uint64_t ad = a_desc0 + (uint64_t)(c * a16);
+            const uint64_t bd = bst + (uint64_t)(c * b16);
+            for (int k = 0; k < ksteps; ++k)
+              mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (c | k) != 0);
           }
-          mma_commit(&ctl->b_empty[s]);
+          mma_commit(&ctl->b_empty[st]);
           mma_commit(&ctl->acc_full[b]);
+          if (++st == p.stages) {
+            st = 0;
+            ph ^= 1u;
+          }
+          b ^= 1;
+          if (b == 0) aph ^= 1u;
         }
         if (ok) mma_commit(&ctl->a_empty);
       }
@@ -324,28 +493,44 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < kWaitNs) {
       }
     }
-  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4 * p.nh) {
+  } else if (warp >= kEpiWarp0) {
     // ------------------------------------------------------------ select
     const int e = warp - kEpiWarp0;
-    const int h = e / 4, q = e % 4;
-    const int row = h * kTileM + 32 * q + lane;  // row within the user tile
-    TcUser s;
-    s.st.heap = heap_base + row;
-    s.st.stride = p.nh * kTileM;
-    s.st.K = p.K;
-    s.st.cap = o.cap;
-    s.g = p.g;
+    const int q = e % 4, c2 = e / 4;       // lane quarter, column half
+    const int row = 32 * q + lane;         // user row within the tile
+    const int slot = c2 * kTileM + row;    // this thread's index among the 256
+    TcUser<KR> s;
+    TcSel c;
+    c.heap = heap_base + slot;
+    c.K = p.K;
+    c.cap = o.cap;
+    c.qh = qh_base + slot;
+    c.qp = qp_base + slot;
+    c.tau_mine = tau_sh + slot;
+    c.tau_partner = tau_sh + (c2 ^ 1) * kTileM + row;
+    c.g = p.g;
     long long g = 0;
     bool ok = true;
-    unsigned long long emitted = 0;
+    unsigned long long emitted = 0, slow = 0;
+    // this warp's copy of the bound columns of its 128 items of the current
+    // tile, prefetched one tile ahead into registers (4 entries per lane)
+    float2* aux_tile = aux_base + (size_t)e * kHalfN;
+    float2 pre[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) pre[t] = item_aux[c2 * kHalfN + lane * 4 + t];
     for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x) {
-      const int64_t u = (int64_t)ut * p.nh * kTileM + row;
+      const int64_t u = (int64_t)ut * kTileM + row;
       const bool active = u < p.n_users;
-      s.st.tau = active ? kNegInf : __int_as_float(0x7f800000);
-      s.st.n_cand = 0;
-      s.st.cand_pos = o.cand_pos + (active ? u : 0) * (int64_t)o.cap;
-      s.st.cand_ub = o.cand_ub + (active ? u : 0) * (int64_t)o.cap;
-      heap_init(s.st.heap, s.st.stride, p.K);
+      s.tau = active ? kNegInf : __int_as_float(0x7f800000);  // inactive: never a hit
+      s.tau_eff = s.tau;
+      s.n_cand = 0;
+      s.ut = ut;
+      s.beta_u = 0.f;
+      s.nhat_u = 0.f;
+      const int64_t list = (active ? u : 0) * 2 + c2;
+      c.cand_pos = o.cand_pos + list * (int64_t)o.cap;
+      c.cand_ub = o.cand_ub + list * (int64_t)o.cap;
+      topk_init(s, c);
       if (active) {
         const float2 ua = user_aux[u];
         s.beta_u = ua.x;
@@ -354,46 +539,90 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       for (int j = 0; j < n_it; ++j, ++g) {
         const int b = (int)(g & 1);
         ok = mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), abort_flag, err);
+        // lanes leave together: the tcgen05.ld below needs the whole warp
+        ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
-        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * p.nh * kTileN + h * kTileN);
-        const int valid = (int)min((int64_t)kTileN, p.n_items - (int64_t)j * kTileN);
+        __syncwarp();  // the previous tile's offers are done with aux_tile
+#pragma unroll
+        for (int t = 0; t < 4; ++t) aux_tile[lane * 4 + t] = pre[t];
+        __syncwarp();
+        {
+          const int jn = (j + 1 < n_it) ? j + 1 : 0;  // next tile (wraps to the next user tile)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) pre[t] = item_aux[(int64_t)jn * kTileN + c2 * kHalfN + lane * 4 + t];
+        }
+        {  // the partner's threshold, if it is for this user tile
+          const unsigned long long pt = *c.tau_partner;
+          if ((int)(pt >> 32) == ut) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
+        }
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
+        const int32_t pos0 = j * kTileN + c2 * kHalfN;
+        const int valid = (int)min((int64_t)kHalfN, p.n_items - (int64_t)pos0);
         uint32_t r[64];
+        if (j == 0) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
+          // (inactive lanes hold tau = +inf and insert nothing)
+          tmem_ld64(taddr, r);
+          seed64(s, c, r, 0, valid, aux_tile);
+          tmem_ld64(taddr + 64, r);
+          seed64(s, c, r, 64, valid - 64, aux_tile);
+          if (active) {
+            s.tau_eff = s.tau;
+            tc_publish(s, c);
+          }
+        }
+        const bool emit_only = j == 0;
         tmem_ld64(taddr, r);
-        select64(s, r, j * kTileN, valid, item_aux);
+        select64(s, c, r, pos0, valid, aux_tile, slow, emit_only);
         tmem_ld64(taddr + 64, r);
-        select64(s, r, j * kTileN + 64, valid - 64, item_aux);
+        select64(s, c, r, pos0 + 64, valid - 64, aux_tile, slow, emit_only);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->acc_empty[b]);
       }
       if (!ok) break;
       if (active) {
-        o.tau[u] = s.st.tau;
-        o.n_cand[u] = s.st.n_cand;
-        emitted += (unsigned long long)s.st.n_cand;
+        o.tau[list] = s.tau_eff;
+        o.n_cand[list] = s.n_cand;
+        emitted += (unsigned long long)s.n_cand;
+        if (o.topl) {  // the K largest lower bounds this thread kept
+          float* dst = o.topl + list * (int64_t)p.K;
+          if constexpr (KR > 0) {
+#pragma unroll
+            for (int i = 0; i < KR; ++i)
+              if (i < p.K) dst[i] = s.d[i];
+          } else {
+            for (int i = 0; i < p.K; ++i) dst[i] = c.heap[i * kEpiThreads];
+          }
+        }
       }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) emitted += __shfl_xor_sync(0xffffffffu, emitted, off);
     if (lane == 0 && emitted) atomicAdd(&stats->cand_emitted, emitted);
+    if (lane == 0 && slow) atomicAdd(&stats->select_slow, slow);  // warp-level slow-path entries
   }
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   if (warp == 2) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
 }  // namespace
 
 size_t tc_smem_bytes(const TcParams& p) {
-  const size_t chunk = (size_t)kTileM * p.row_bytes;
-  return 1024 + (size_t)p.nh * p.kc * chunk + (size_t)p.stages * p.kc * chunk +
-         sizeof(float) * (size_t)p.K * p.nh * kTileM + sizeof(Smem);
+  const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = (size_t)kTileN * p.row_bytes;
+  const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
+  return 1024 + (size_t)p.kc * a_chunk + (size_t)p.stages * p.kc * b_chunk + heap +
+         sizeof(float2) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
+         sizeof(unsigned long long) * kEpiThreads + sizeof(Smem);
 }
+
+int tc_users_per_tile() { return kTileM; }
+int tc_items_per_tile() { return kTileN; }
 
 cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p,
                                    SelectOut o, const float2* user_aux, const float2* item_aux, DevStats* stats,
@@ -405,9 +634,18 @@ cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorM
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
-  cudaError_t e = cudaFuncSetAttribute(tc_score_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  tc_score_select_kernel<<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux, stats, err);
+  cudaError_t e;
+  if (p.K <= kRegTopK) {
+    e = cudaFuncSetAttribute(tc_score_select_kernel<kRegTopK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_score_select_kernel<kRegTopK><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux,
+                                                                     stats, err);
+  } else {
+    e = cudaFuncSetAttribute(tc_score_select_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    tc_score_select_kernel<0><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux, stats,
+                                                              err);
+  }
   return cudaGetLastError();
 }
 

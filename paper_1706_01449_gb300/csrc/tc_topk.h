@@ -7,6 +7,7 @@
 namespace mips {
 
 constexpr int kMaxStages = 8;
+constexpr int kRegTopK = 16;  // K up to this keeps its top-K in registers
 
 struct TcParams {
   int64_t n_users, n_items;
@@ -16,7 +17,6 @@ struct TcParams {
   int row_elems;  // BF16 elements of one chunk row
   int swizzle;    // tcgen05 descriptor layout code: 6 = 32B, 4 = 64B, 2 = 128B
   int stages;     // item-tile ring depth
-  int nh;         // user halves of 128 rows per CTA tile (1 or 2)
   float g;        // accumulation-error factor used by prep.cu for this fp
 };
 
@@ -29,13 +29,15 @@ inline int tc_row_len(int f) {
   return (int)round_up(n, 64);
 }
 
-// Fill chunking, swizzle, stages and halves for this problem so the shared
-// memory fits; returns false if no configuration fits.
+// Fill chunking, swizzle and stages for this problem so the shared memory
+// fits; returns false if no configuration fits.
 bool tc_plan(TcParams& p, int max_smem);
 size_t tc_smem_bytes(const TcParams& p);
 
-// K-major BF16 operand map [rows][fp], boxes of row_elems x 128 rows.
-bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes);
+// K-major BF16 operand map [rows][fp], boxes of row_elems x box_rows rows.
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows);
+int tc_users_per_tile();  // rows of a user tile (MMA M)
+int tc_items_per_tile();  // rows of an item tile (MMA N)
 
 cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p,
                                    SelectOut o, const float2* user_aux, const float2* item_aux, DevStats* stats,
