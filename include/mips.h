@@ -206,8 +206,8 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
  *
  * Scratch comes from one static device array of 32 MiB per GPU, reserved
  * when the library's code is loaded on that GPU and held until the process
- * exits.  A call needs 8 n_items + n_users (12 + 8 (4K + 96)) bytes of it
- * plus 1.5 KiB (K = 10: about 30,000 users against 17,770 items); larger
+ * exits.  A call needs 8 n_items + n_users (16 + 20 (4K + 96)) bytes of it
+ * plus 2 KiB (K = 10: about 12,000 users against 17,770 items); larger
  * calls return MIPS_ERR_ARG (split the users).  Limits as mips_topk:
  * 1 <= f <= 128, 1 <= K <= min(n_items, 128).
  *

@@ -70,7 +70,19 @@ struct SelectOut {
   // users whose candidate list overflowed, for the exhaustive rescore
   int32_t* ovf_list;   // [n_users]
   int* ovf_count;      // one counter, zero before the rescore
+  // rescore scratch: valid candidate slots, their exact scores, thresholds
+  uint32_t* work;      // [n_users * lists * cap]
+  int* work_count;     // one counter
+  double* cand_sc;     // [n_users * lists][cap]
+  float* tau_final;    // [n_users]
 };
+
+// Bytes of rescore scratch (ovf list, work list, scores, thresholds, counters)
+// for n_users users with `lists` sub-lists of `cap` candidates each.
+inline size_t rescore_scratch_bytes(int64_t n_users, int lists, int cap) {
+  const size_t slots = (size_t)n_users * lists * cap;
+  return 4 * (size_t)n_users + 4 * slots + 8 * slots + 4 * (size_t)n_users + 1024;
+}
 bool fp32_supported(int f, int K);
 cudaError_t launch_fp32_score_select(const float* users, int64_t n_users, int f, const float* items,
                                      const float* item_nrm_ub, int64_t n_items, int K, SelectOut o,

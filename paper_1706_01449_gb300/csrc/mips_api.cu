@@ -164,7 +164,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   const bool use_tc = idx->opt.dtype == MIPS_BF16 && tc_plan(p, idx->max_smem);
   // BF16: two select threads per user, each with its own sub-list
   const int lists = use_tc ? 2 : 1;
-  const int cap = lists == 1 ? cap_for(K) : 2 * K + 64;
+  const int cap = lists == 1 ? cap_for(K) : (K <= kRegTopK ? 2 * K + 64 : 4 * K + 64);
   const int64_t nl = n_users * lists;
   idx->ws.reset();
   size_t o_tau = idx->ws.take(sizeof(float) * nl);
@@ -174,6 +174,10 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_topl = idx->ws.take(sizeof(float) * nl * K);
   size_t o_ovf = idx->ws.take(sizeof(int32_t) * n_users);
   size_t o_ovfc = idx->ws.take(sizeof(int));
+  size_t o_work = idx->ws.take(sizeof(uint32_t) * nl * cap);
+  size_t o_workc = idx->ws.take(sizeof(int));
+  size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
+  size_t o_tauf = idx->ws.take(sizeof(float) * n_users);
   size_t o_ub16 = 0, o_uaux = 0;
   if (use_tc) {
     o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
@@ -183,7 +187,8 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
                idx->ws.at<float>(o_ub), cap, lists,
                lists == 2 ? idx->ws.at<float>(o_topl) : nullptr, K <= kRegTopK ? 1 : 0,
-               idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc)};
+               idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc), idx->ws.at<uint32_t>(o_work),
+               idx->ws.at<int>(o_workc), idx->ws.at<double>(o_sc), idx->ws.at<float>(o_tauf)};
   mips_status st;
   if (!use_tc) {
     MIPS_CUDA(launch_fp32_score_select(users, n_users, f, idx->items, idx->item_nrm, idx->n_items, K, so,

@@ -13,7 +13,7 @@
 // Limits and sharing (also stated in include/mips.h):
 //   * the scratch is kNoAllocScratchBytes (32 MiB) on every GPU that loads
 //     the library, held until the process exits;
-//   * a call needs 8 n_items + n_users (12 + 8 (4K + 96)) bytes plus 1.5 KiB of
+//   * a call needs 8 n_items + n_users (16 + 20 (4K + 96)) bytes plus 2 KiB of
 //     headers and is rejected with MIPS_ERR_ARG beyond that;
 //   * every call uses the same array: calls that overlap on the GPU (two
 //     streams, two host threads) race and corrupt each other's results, so
@@ -92,8 +92,9 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
       K > 128 || K > n_items)
     return report(MIPS_ERR_ARG, "size out of range (1<=f<=128, 1<=K<=min(n_items,128), n>=1)");
   const int cap = 4 * K + 96;
-  const size_t need = up256(sizeof(DevStats)) + up256(sizeof(int)) * 2 + up256(4 * (size_t)n_items) * 2 +
-                      up256(4 * (size_t)n_users) * 3 + up256(4 * (size_t)n_users * cap) * 2;
+  const size_t slots = (size_t)n_users * cap;
+  const size_t need = up256(sizeof(DevStats)) + up256(sizeof(int)) * 3 + up256(4 * (size_t)n_items) * 2 +
+                      up256(4 * (size_t)n_users) * 4 + up256(4 * slots) * 3 + up256(8 * slots);
   if (need > kNoAllocScratchBytes)
     return report(MIPS_ERR_ARG, "problem needs %zu scratch bytes, the static scratch holds %zu (use fewer users per call)",
                   need, kNoAllocScratchBytes);
@@ -126,6 +127,14 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
   so.ovf_list = (int32_t*)p;
   p += up256(4 * (size_t)n_users);
   so.ovf_count = (int*)p;
+  p += up256(sizeof(int));
+  so.work = (uint32_t*)p;
+  p += up256(4 * slots);
+  so.work_count = (int*)p;
+  p += up256(sizeof(int));
+  so.cand_sc = (double*)p;
+  p += up256(8 * slots);
+  so.tau_final = (float*)p;
 
   // counters and the error word must start at zero; the rest is overwritten
   e = cudaMemsetAsync(base, 0, up256(sizeof(DevStats)) + up256(sizeof(int)), s);

@@ -2,15 +2,17 @@
 // of the paper's BMM and of QueryIndex in Algorithm 1: the K best items by
 // u^T i, ties to the smaller item index).
 //
-// rescore_thread_kernel -- one thread per user:
-//   * threshold tau: the final threshold of its candidate sub-list, or, with
-//     two sub-lists whose K best lower bounds are given, the K-th largest of
-//     their union (the entries belong to distinct items, so this is a valid
-//     lower bound on the user's K-th score);
-//   * every candidate whose upper bound H reaches tau is scored with a
-//     compensated FP32 dot product (Dot2, common.cuh) and inserted into the
-//     thread's sorted list of the K + 1 best keys (score desc, item id asc)
-//     in shared memory;
+// Three kernels, then one for overflowed users:
+//   (A) collect, thread per user: the threshold tau -- the final threshold
+//       of its candidate sub-list, or, with two sub-lists whose K best lower
+//       bounds are given, the K-th largest of their union (the entries
+//       belong to distinct items, so this is a valid lower bound on the
+//       user's K-th score) -- and the slots of the candidates whose upper
+//       bound H reaches tau, appended to a work list;
+//   (B) dot, thread per listed candidate: its compensated FP32 dot product
+//       (Dot2, common.cuh), so every lane of a warp has work;
+//   (C) select, thread per user: the K + 1 best keys (score desc, item id
+//       asc) in a shared-memory heap, sorted;
 //   * tie check: every adjacent pair of that list is compared against the
 //     score error bound
 //       e = (2 gamma_2f gamma_f + (f + 2) 2^-53) nhat_u nhat_i_max  (x 2 margin),
@@ -20,8 +22,8 @@
 //     ranking is the definition's; otherwise the compensated order equals
 //     the exact order, which equals the FP64 definition's order;
 //   * a zero user has every score exactly 0: its answer is items 0..K-1;
-//   * a user whose candidate list overflowed is queued for
-// rescore_warp_kernel -- one warp per queued user, scoring every item.
+//   * a user whose candidate list overflowed is queued for the warp kernel,
+//     one warp per queued user, scoring every item.
 #include "common.cuh"
 
 namespace mips {
@@ -132,35 +134,36 @@ struct KeyHeap {
 };
 
 // ---------------------------------------------------------------------------
-// thread per user
+// (A) thread per user: threshold, overflow / zero-user handling, and the
+//     valid candidate slots appended to the work list
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128)
-    rescore_thread_kernel(const float* __restrict__ users, int64_t n_users, int f,
-                          const float* __restrict__ items, const int32_t* __restrict__ perm,
-                          const float* __restrict__ item_nrm, int K, SelectOut o, int32_t* __restrict__ out_idx,
-                          double* __restrict__ out_score, DevStats* stats, int* err) {
-  extern __shared__ unsigned char smem_raw[];
-  const int T = blockDim.x, t = threadIdx.x;
-  const int L = K + 1;  // list length: the K best and the best of the rest
-  double* ls = reinterpret_cast<double*>(smem_raw);  // [L][T]
-  int* li = reinterpret_cast<int*>(ls + (size_t)L * T);
-  const int64_t u = (int64_t)blockIdx.x * T + t;
-  unsigned long long n_rescored = 0, n_over = 0, n_fp64 = 0;
-
+__global__ void __launch_bounds__(256)
+    rescore_collect_kernel(const float* __restrict__ users, int64_t n_users, int f, int K, SelectOut o,
+                           int32_t* __restrict__ out_idx, double* __restrict__ out_score, DevStats* stats) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int nvalid = 0;
+  int n[2] = {0, 0};
+  float tau = 0.f;
+  bool live = false;  // this user goes through the work list
+  unsigned long long n_over = 0;
   if (u < n_users) {
     const float* ur = users + u * f;
     float ss = 0.f;
     for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
+    const int64_t l0 = u * o.lists;
+    n[0] = o.n_cand[l0];
+    n[1] = o.lists == 2 ? o.n_cand[l0 + 1] : 0;
     if (ss == 0.f) {  // zero user: every score is exactly 0
       for (int k = 0; k < K; ++k) {
         out_idx[u * K + k] = k;
         out_score[u * K + k] = 0.0;
       }
+    } else if (n[0] > o.cap || n[1] > o.cap) {
+      const int slot = atomicAdd(o.ovf_count, 1);
+      o.ovf_list[slot] = (int32_t)u;
+      n_over = 1;
     } else {
-      const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
-      // threshold
-      float tau;
-      const int64_t l0 = u * o.lists;
       if (o.lists == 1) {
         tau = o.tau[l0];
       } else if (o.topl && o.topl_sorted) {
@@ -176,61 +179,123 @@ __global__ void __launch_bounds__(128)
       } else {
         tau = fmaxf(o.tau[l0], o.tau[l0 + 1]);
       }
-      int n[2] = {o.n_cand[l0], o.lists == 2 ? o.n_cand[l0 + 1] : 0};
-      if (n[0] > o.cap || n[1] > o.cap) {
-        const int slot = atomicAdd(o.ovf_count, 1);
-        o.ovf_list[slot] = (int32_t)u;
-        n_over = 1;
-      } else {
-        const double rel_e = rescore_rel_err(f);
-        KeyHeap heap{ls + t, li + t, T};
-        for (int mode = 0; mode < 2; ++mode) {
-          int cnt = 0;
-          float nmax = 0.f;
-          for (int l = 0; l < o.lists; ++l) {
-            const int32_t* cp = o.cand_pos + (l0 + l) * (int64_t)o.cap;
-            const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
-            for (int c = 0; c < n[l]; ++c) {
-              if (cu[c] < tau) continue;
-              const int32_t pos = cp[c];
-              const int id = perm[pos];
-              const float* row = items + (int64_t)pos * f;
-              const double v = mode == 0 ? score_dot2(ur, row, f) : score_f64(ur, row, f);
-              nmax = fmaxf(nmax, item_nrm[pos]);
-              if (mode == 0) ++n_rescored;
-              heap.push(cnt, L, v, id);
-            }
+      o.tau_final[u] = tau;
+      live = true;
+      for (int l = 0; l < o.lists; ++l) {
+        const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
+        for (int c = 0; c < n[l]; ++c) nvalid += cu[c] >= tau;
+      }
+    }
+  }
+  // warp-aggregated append: one atomic per warp
+  int incl = nvalid;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, off);
+    if (lane >= off) incl += y;
+  }
+  const int total = __shfl_sync(kFull, incl, 31);
+  int base = 0;
+  if (lane == 31 && total) base = atomicAdd(o.work_count, total);
+  base = __shfl_sync(kFull, base, 31) + incl - nvalid;
+  if (live && nvalid) {
+    const int64_t l0 = u * o.lists;
+    for (int l = 0; l < o.lists; ++l) {
+      const int64_t row = (l0 + l) * (int64_t)o.cap;
+      const float* cu = o.cand_ub + row;
+      for (int c = 0; c < n[l]; ++c)
+        if (cu[c] >= tau) o.work[base++] = (uint32_t)(row + c);
+    }
+  }
+  unsigned long long r = nvalid;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    r += __shfl_xor_sync(kFull, r, off);
+    n_over += __shfl_xor_sync(kFull, n_over, off);
+  }
+  if (lane == 0) {
+    if (r) atomicAdd(&stats->cand_rescored, r);
+    if (n_over) atomicAdd(&stats->users_overflow, n_over);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (B) thread per valid candidate: its compensated dot product
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    rescore_dot_kernel(const float* __restrict__ users, int f, const float* __restrict__ items, SelectOut o) {
+  const int count = *o.work_count;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+    const uint32_t slot = o.work[w];
+    const int64_t u = (int64_t)(slot / (uint32_t)o.cap) / o.lists;
+    const int32_t pos = o.cand_pos[slot];
+    o.cand_sc[slot] = score_dot2(users + u * f, items + (int64_t)pos * f, f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// (C) thread per user: the K + 1 best keys, the tie check, the output
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    rescore_select_kernel(const float* __restrict__ users, int64_t n_users, int f,
+                          const float* __restrict__ items, const int32_t* __restrict__ perm,
+                          const float* __restrict__ item_nrm, int K, SelectOut o, int32_t* __restrict__ out_idx,
+                          double* __restrict__ out_score, DevStats* stats, int* err) {
+  extern __shared__ unsigned char smem_raw[];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int L = K + 1;  // the K best and the best of the rest
+  double* ls = reinterpret_cast<double*>(smem_raw);  // [L][T]
+  int* li = reinterpret_cast<int*>(ls + (size_t)L * T);
+  const int64_t u = (int64_t)blockIdx.x * T + t;
+  unsigned long long n_fp64 = 0;
+  if (u < n_users) {
+    const float* ur = users + u * f;
+    const int64_t l0 = u * o.lists;
+    const int n0 = o.n_cand[l0], n1 = o.lists == 2 ? o.n_cand[l0 + 1] : 0;
+    float ss = 0.f;
+    for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
+    // zero users are done; overflowed users belong to the warp kernel
+    if (ss != 0.f && n0 <= o.cap && n1 <= o.cap) {
+      const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
+      const float tau = o.tau_final[u];
+      const double rel_e = rescore_rel_err(f);
+      KeyHeap heap{ls + t, li + t, T};
+      for (int mode = 0; mode < 2; ++mode) {
+        int cnt = 0;
+        float nmax = 0.f;
+        for (int l = 0; l < o.lists; ++l) {
+          const int64_t row = (l0 + l) * (int64_t)o.cap;
+          const int nl = l == 0 ? n0 : n1;
+          for (int c = 0; c < nl; ++c) {
+            if (o.cand_ub[row + c] < tau) continue;
+            const int32_t pos = o.cand_pos[row + c];
+            const double v =
+                mode == 0 ? o.cand_sc[row + c] : score_f64(ur, items + (int64_t)pos * f, f);
+            nmax = fmaxf(nmax, item_nrm[pos]);
+            heap.push(cnt, L, v, perm[pos]);
           }
-          heap.sort(cnt);
-          if (cnt < K) {  // cannot happen: K lower bounds back tau
-            atomicOr(err, DEV_ERR_INTERNAL);
-            break;
-          }
-          if (mode == 1) break;
-          const double e2 = 2.0 * rel_e * nu * (double)nmax;
-          bool amb = false;
-          for (int p = 0; p + 1 < cnt; ++p) amb |= (ls[p * T + t] - ls[(p + 1) * T + t]) <= e2;
-          if (!amb) break;
-          ++n_fp64;
         }
-        for (int k = 0; k < K; ++k) {
-          out_idx[u * K + k] = li[k * T + t];
-          out_score[u * K + k] = ls[k * T + t];
+        heap.sort(cnt);
+        if (cnt < K) {  // cannot happen: K lower bounds back tau
+          atomicOr(err, DEV_ERR_INTERNAL);
+          break;
         }
+        if (mode == 1) break;
+        const double e2 = 2.0 * rel_e * nu * (double)nmax;
+        bool amb = false;
+        for (int p = 0; p + 1 < cnt; ++p) amb |= (ls[p * T + t] - ls[(p + 1) * T + t]) <= e2;
+        if (!amb) break;
+        ++n_fp64;
+      }
+      for (int k = 0; k < K; ++k) {
+        out_idx[u * K + k] = li[k * T + t];
+        out_score[u * K + k] = ls[k * T + t];
       }
     }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    n_rescored += __shfl_xor_sync(kFull, n_rescored, off);
-    n_over += __shfl_xor_sync(kFull, n_over, off);
-    n_fp64 += __shfl_xor_sync(kFull, n_fp64, off);
-  }
-  if ((t & 31) == 0) {
-    if (n_rescored) atomicAdd(&stats->cand_rescored, n_rescored);
-    if (n_over) atomicAdd(&stats->users_overflow, n_over);
-    if (n_fp64) atomicAdd(&stats->users_fp64, n_fp64);
-  }
+  for (int off = 16; off > 0; off >>= 1) n_fp64 += __shfl_xor_sync(kFull, n_fp64, off);
+  if ((t & 31) == 0 && n_fp64) atomicAdd(&stats->users_fp64, n_fp64);
 }
 
 // ---------------------------------------------------------------------------
@@ -376,15 +441,19 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
                            SelectOut o, int32_t* out_idx, double* out_score, DevStats* stats,
                            int* err, cudaStream_t s) {
   if (K > kMaxK || f > kMaxF) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(o.ovf_count, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(o.work_count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  rescore_collect_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, K, o, out_idx,
+                                                                            out_score, stats);
+  rescore_dot_kernel<<<152 * 8, 256, 0, s>>>(users, f, items_sorted, o);
   // threads per block so that the per-thread lists of K + 1 keys fit in 96 KiB
   int T = 128;
   while (T > 32 && (size_t)T * (K + 1) * 12 > 96 * 1024) T -= 32;
   const size_t smem = (size_t)T * (K + 1) * 12;
-  cudaError_t e = cudaFuncSetAttribute(rescore_thread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(rescore_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(o.ovf_count, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  rescore_thread_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
+  rescore_select_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
                                                                            item_nrm_ub, K, o, out_idx, out_score,
                                                                            stats, err);
   rescore_warp_kernel<<<152 * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,

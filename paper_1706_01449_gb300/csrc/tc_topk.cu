@@ -189,6 +189,10 @@ struct TcSel {
   int32_t* qp;
   volatile unsigned long long* tau_mine;  // published thresholds: mine, partner's
   const volatile unsigned long long* tau_partner;
+  volatile int* seed_mine;                // [2][256] user tile whose seed list is published
+  const volatile int* seed_partner;
+  float* seed_list;                       // [2][K][256] first-tile top-K lists
+  const float* seed_list_partner;
   float g;            // accumulation-error factor of prep.cu
 };
 
@@ -232,6 +236,54 @@ __device__ __forceinline__ float tc_lower(const TcUser<KR>& s, const TcSel& c, f
   const float nn = s.nhat_u * ia.x;
   const float slack = __fmaf_rn(2.0f, A, c.g * (nn + A)) * (1.0f + 3.814697265625e-06f);  // 2^-18
   return (H - slack) - fabsf(H) * 2.384185791015625e-07f;                             // 2^-22
+}
+
+// After the first-tile pass: this thread's K best lower bounds go to its
+// queue slots (shared memory), published with a tagged flag; it then waits a
+// bounded time for the partner's (the other half of the same user) and
+// takes the K-th largest of the union as its threshold.  The two halves
+// hold distinct items, so the union's K-th largest is a valid lower bound.
+// If the partner's list is not there within the bound, the thread goes on
+// with its own threshold, which is valid too.
+// The lists are double-buffered by user-tile parity: a partner that is one
+// user tile ahead cannot overwrite the list being read (the accumulator
+// handshake keeps the halves within one user tile of each other).
+template <int KR>
+__device__ __forceinline__ void seed_merge(TcUser<KR>& s, const TcSel& c, int ut, int par) {
+  if constexpr (KR > 0) {
+    float* mine = c.seed_list + par * c.K * kEpiThreads;
+#pragma unroll
+    for (int i = 0; i < KR; ++i)
+      if (i < c.K) mine[i * kEpiThreads] = s.d[i];
+    __threadfence_block();
+    c.seed_mine[par * kEpiThreads] = ut;
+    const float* pq = c.seed_list_partner + par * c.K * kEpiThreads;
+    const volatile int* pflag = c.seed_partner + par * kEpiThreads;
+    int spins = 0;
+    while (*pflag != ut && ++spins < 20000) {
+    }
+    if (*pflag == ut) {
+      __threadfence_block();
+      // K-th largest of two descending lists of K
+      int ia = 0, ib = 0;
+      float v = s.d[0];
+      for (int r = 0; r < c.K; ++r) {
+        float a = kNegInf;
+#pragma unroll
+        for (int i = 0; i < KR; ++i)
+          if (i == ia) a = s.d[i];
+        const float b = ((volatile const float*)pq)[ib * kEpiThreads];
+        if (a >= b) {
+          v = a;
+          ++ia;
+        } else {
+          v = b;
+          ++ib;
+        }
+      }
+      if (v > s.tau_eff) s.tau_eff = v;
+    }
+  }
 }
 
 // Publish this thread's threshold (tagged with its user tile) for the partner.
@@ -280,20 +332,29 @@ __device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const ui
   const float m4 = max3(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]));
   const float mm = max3(max3(m0, m1, m2), m3, fmaxf(m4, __uint_as_float(r[15])));
   const bool hit = mm >= s.tau_eff;
-  if (__any_sync(0xffffffffu, hit)) {
+  if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: counts warp-level entries
     ++slow;
     int n = 0;
     if (hit) {
+      // only the groups of three whose maximum reached the threshold
+      const float t = s.tau_eff;
+      const float gm[6] = {m0, m1, m2, m3, m4, __uint_as_float(r[15])};
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float v = __uint_as_float(r[q]);
-        if (v >= s.tau_eff && q < valid) {
-          c.qh[n * kEpiThreads] = v;
-          c.qp[n * kEpiThreads] = pos0 + q;
-          ++n;
+      for (int gq = 0; gq < 6; ++gq) {
+        if (gm[gq] >= t) {
+#pragma unroll
+          for (int q = 3 * gq; q < (gq < 5 ? 3 * gq + 3 : 16); ++q) {
+            const float v = __uint_as_float(r[q]);
+            if (v >= t && q < valid) {
+              c.qh[n * kEpiThreads] = v;
+              c.qp[n * kEpiThreads] = pos0 + q;
+              ++n;
+            }
+          }
         }
       }
     }
+    // one offer site for the queued hits (keeps the code small)
     for (int t = 0; t < n; ++t) tc_offer(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, emit_only);
   }
 }
@@ -323,10 +384,13 @@ __device__ __forceinline__ void seed64(TcUser<KR>& s, const TcSel& c, const uint
     int n = 0;
 #pragma unroll
     for (int q = 16 * g; q < 16 * g + 16; ++q) {
-      const float L = tc_lower(s, c, __uint_as_float(r[q]), aux_tile[col0 + q]);
-      if (L > s.tau && q < valid) {
-        c.qh[n * kEpiThreads] = L;
-        ++n;
+      const float H = __uint_as_float(r[q]);
+      if (H > s.tau && q < valid) {  // L <= H: nothing at or below tau can enter
+        const float L = tc_lower(s, c, H, aux_tile[col0 + q]);
+        if (L > s.tau) {
+          c.qh[n * kEpiThreads] = L;
+          ++n;
+        }
       }
     }
     for (int t = 0; t < n; ++t) {
@@ -363,7 +427,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   float* qh_base = (float*)(aux_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
   int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
   unsigned long long* tau_sh = (unsigned long long*)(qp_base + (size_t)kQueue * kEpiThreads);  // [256]
-  Smem* ctl = (Smem*)(tau_sh + kEpiThreads);
+  int* seed_sh = (int*)(tau_sh + kEpiThreads);                                                // [2][256]
+  float* seed_lists = (float*)(seed_sh + 2 * kEpiThreads);  // [2][K][256] (KR > 0)
+  Smem* ctl = (Smem*)(seed_lists + (KR > 0 ? (size_t)2 * p.K * kEpiThreads : 0));
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ctl->abort_flag;
@@ -386,7 +452,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < kEpiThreads; i += blockDim.x) tau_sh[i] = pack_tau(kNegInf, -1);
+  for (int i = threadIdx.x; i < kEpiThreads; i += blockDim.x) {
+    tau_sh[i] = pack_tau(kNegInf, -1);
+    seed_sh[i] = -1;
+    seed_sh[kEpiThreads + i] = -1;
+  }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                  "r"(kTmemCols)
@@ -508,6 +578,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     c.qp = qp_base + slot;
     c.tau_mine = tau_sh + slot;
     c.tau_partner = tau_sh + (c2 ^ 1) * kTileM + row;
+    c.seed_mine = seed_sh + slot;
+    c.seed_partner = seed_sh + (c2 ^ 1) * kTileM + row;
+    c.seed_list = seed_lists + slot;
+    c.seed_list_partner = seed_lists + (c2 ^ 1) * kTileM + row;
     c.g = p.g;
     long long g = 0;
     bool ok = true;
@@ -518,7 +592,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     float2 pre[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) pre[t] = item_aux[c2 * kHalfN + lane * 4 + t];
-    for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x) {
+    int lt = 0;  // user tiles done by this CTA
+    for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
       const int64_t u = (int64_t)ut * kTileM + row;
       const bool active = u < p.n_users;
       s.tau = active ? kNegInf : __int_as_float(0x7f800000);  // inactive: never a hit
@@ -569,6 +644,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if (active) {
             s.tau_eff = s.tau;
             tc_publish(s, c);
+            if constexpr (KR > 0) seed_merge(s, c, ut, lt & 1);
           }
         }
         const bool emit_only = j == 0;
@@ -618,7 +694,8 @@ size_t tc_smem_bytes(const TcParams& p) {
   const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
   return 1024 + (size_t)p.kc * a_chunk + (size_t)p.stages * p.kc * b_chunk + heap +
          sizeof(float2) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
-         sizeof(unsigned long long) * kEpiThreads + sizeof(Smem);
+         sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
+         (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
 }
 
 int tc_users_per_tile() { return kTileM; }
