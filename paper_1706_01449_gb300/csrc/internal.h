@@ -105,6 +105,22 @@ cudaError_t radix_sort_pairs(uint32_t*& keys, int32_t*& vals, uint32_t*& keys_al
 cudaError_t make_float_desc_keys(const float* x, int64_t n, uint32_t* keys, int32_t* iota, int64_t seg_len,
                                  cudaStream_t s);
 
+// ---- Maximus (maximus.cu) -------------------------------------------------
+cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
+                           float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
+                           uint32_t* absmax, float* scale, cudaStream_t s, int* launches);
+cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int32_t* assign, const float* cent, int C,
+                           const float* items, const float* item_nrm, int64_t n_items, uint32_t* cosb_ord,
+                           uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches);
+cudaError_t maximus_group(const int32_t* assign, int64_t n_users, int C, uint32_t* keys, int32_t* ids, uint32_t* keys_alt,
+                          int32_t* ids_alt, uint32_t* temp, int* counts, int* offsets, int* tile_off,
+                          int32_t** user_perm, cudaStream_t s, int* launches);
+cudaError_t maximus_walk(const float* users, int f, const float* items, const float* item_nrm, int64_t n_items,
+                         const int32_t* lists, const float* bounds, const int32_t* user_perm, const int* offsets,
+                         const int* tile_off, int C, int K, SelectOut o, int32_t* visited, int* work_counter,
+                         DevStats* stats, int* err, int num_sms, cudaStream_t s);
+cudaError_t maximus_keys_to_bounds(const uint32_t* keys, int64_t n, float* out, cudaStream_t s);
+
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);
 

@@ -1,0 +1,518 @@
+// Maximus (Sec. IV, Algorithm 1) on the GPU: k-means user clusters,
+// theta_b per cluster, CBound (Eq. appx_bound) for every (cluster, item),
+// per-cluster item lists sorted by CBound, users grouped by cluster, and a
+// grouped walk of each cluster's list that stops once no remaining item can
+// enter any of the walking users' top-K.  The walk emits candidates into the
+// same per-user lists as the blocked multiply, so the exact rescore is
+// shared.
+//
+// Rounding: every quantity that decides pruning is rounded outward so that
+// the exactness argument (Lemma "upper bound in index lists" and Theorem
+// "exact") holds for the computed values:
+//   * cos_b[j] = a LOWER bound of min over members of cos(u, c_j);
+//   * x = an UPPER bound of cos(c_j, i);
+//   * CBound = nhat_i g(x, cos_b) with g(x, y) = 1 if x >= y, else
+//     x y + sqrt((1 - x)(1 + x)) sqrt((1 - y)(1 + y))   (= cos(theta_ic - theta_b)),
+//     g rounded up; g increases with x and decreases with y on x < y, so
+//     the outward inputs give an upper bound.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace mips {
+
+namespace {
+
+constexpr int kThreads = 128;   // users per walk / assign block
+constexpr int kBlockItems = 32; // items per walk shared-memory tile (a "block" of Algorithm 1's walk)
+
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// float <-> order-preserving unsigned (ascending)
+__device__ __forceinline__ uint32_t f2ord(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// ---------------------------------------------------------------- k-means
+__global__ void gather_rows_i64(const float* __restrict__ x, const int64_t* __restrict__ ids, int n, int f,
+                                float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * f) return;
+  const int r = (int)(t / f), k = (int)(t % f);
+  out[t] = x[ids[r] * f + k];
+}
+
+// max |x| over all entries, as an order-preserving unsigned
+__global__ void absmax_kernel(const float* __restrict__ x, int64_t n, uint32_t* out) {
+  float m = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative: bits are ordered
+}
+
+// ||c_j||^2 / 2 per centroid
+__global__ void half_norm2_kernel(const float* __restrict__ cent, int C, int f, float* __restrict__ hn2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= C) return;
+  float s = 0.f;
+  for (int k = 0; k < f; ++k) s = __fmaf_rn(cent[j * f + k], cent[j * f + k], s);
+  hn2[j] = 0.5f * s;
+}
+
+// Assignment step: argmin_j ||u - c_j||^2 = argmax_j (u . c_j - ||c_j||^2 / 2);
+// ties to the smaller j.  Centroids are staged through shared memory in
+// tiles of 64.
+template <int FP>
+__global__ void __launch_bounds__(kThreads) kmeans_assign_kernel(const float* __restrict__ users, int64_t n_users,
+                                                                 int f, const float* __restrict__ cent,
+                                                                 const float* __restrict__ hn2, int C,
+                                                                 int32_t* __restrict__ assign) {
+  __shared__ float cs[64 * FP];
+  __shared__ float hs[64];
+  const int64_t u = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  const bool active = u < n_users;
+  float ur[FP];
+#pragma unroll
+  for (int k = 0; k < FP; ++k) ur[k] = (active && k < f) ? users[u * f + k] : 0.f;
+  float best = -__int_as_float(0x7f800000);
+  int bj = 0;
+  for (int j0 = 0; j0 < C; j0 += 64) {
+    const int nj = min(64, C - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * FP; e += kThreads) {
+      const int r = e / FP, k = e % FP;
+      cs[e] = (r < nj && k < f) ? cent[(int64_t)(j0 + r) * f + k] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 64; e += kThreads) hs[e] = e < nj ? hn2[j0 + e] : 0.f;
+    __syncthreads();
+    for (int r = 0; r < nj; ++r) {
+      float d = 0.f;
+#pragma unroll
+      for (int k = 0; k < FP; ++k) d = __fmaf_rn(ur[k], cs[r * FP + k], d);
+      const float v = d - hs[r];
+      if (v > best) {
+        best = v;
+        bj = j0 + r;
+      }
+    }
+  }
+  if (active) assign[u] = bj;
+}
+
+// Fixed-point scale 2^e for the centroid sums: n_users entries of
+// magnitude <= max|x| sum to less than 2^62.  scale[0] = 2^e, scale[1] = 2^-e.
+__global__ void kmeans_scale_kernel(const uint32_t* __restrict__ absmax_bits, int64_t n_users, float* scale) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  float amax = __uint_as_float(*absmax_bits);
+  if (!(amax > 0.f)) amax = 1.f;
+  const double mag = (double)amax * (double)n_users;
+  int ex = 61 - (int)ceil(log2(mag));
+  if (ex > 100) ex = 100;
+  scale[0] = ldexpf(1.f, ex);
+  scale[1] = ldexpf(1.f, -ex);
+}
+
+// Update step, part 1: per-cluster sums in fixed point (int64, scale 2^e),
+// so that the result does not depend on the order of the atomic adds.
+__global__ void kmeans_accum_kernel(const float* __restrict__ users, int64_t n_users, int f,
+                                    const int32_t* __restrict__ assign, int C, const float* __restrict__ scale,
+                                    unsigned long long* __restrict__ sums, unsigned int* __restrict__ counts) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_users * f) return;
+  const int64_t u = t / f;
+  const int k = (int)(t - u * f);
+  const int j = assign[u];
+  const long long q = __float2ll_rn(users[t] * scale[0]);
+  atomicAdd(&sums[(int64_t)j * f + k], (unsigned long long)q);
+  if (k == 0) atomicAdd(&counts[j], 1u);
+}
+
+// Update step, part 2: mean of the members; an empty cluster keeps its centroid.
+__global__ void kmeans_update_kernel(const unsigned long long* __restrict__ sums, const unsigned int* __restrict__ counts,
+                                    int C, int f, const float* __restrict__ scale, float* __restrict__ cent) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= C * f) return;
+  const int j = t / f;
+  const unsigned int n = counts[j];
+  if (n == 0) return;
+  const double s = (double)(long long)sums[t];
+  cent[t] = (float)(s * (double)scale[1] / (double)n);
+}
+
+// ---------------------------------------------------------------- bounds
+// cos_b[j] (as order-preserving bits, initialised to +1): a lower bound of
+// the smallest cosine between a member of cluster j and c_j.  Zero users are
+// left out; a zero centroid gives -1 (theta_b = pi).
+__global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, int f, const int32_t* __restrict__ assign,
+                            const float* __restrict__ cent, uint32_t* __restrict__ cosb_ord) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_users) return;
+  const int j = assign[u];
+  const float* ur = users + u * f;
+  const float* cr = cent + (int64_t)j * f;
+  float d = 0.f, su = 0.f, sc = 0.f;
+  for (int k = 0; k < f; ++k) {
+    d = __fmaf_rn(ur[k], cr[k], d);
+    su = __fmaf_rn(ur[k], ur[k], su);
+    sc = __fmaf_rn(cr[k], cr[k], sc);
+  }
+  if (su == 0.f) return;
+  float c;
+  if (sc == 0.f) {
+    c = -1.f;
+  } else {
+    // each factor carries a relative error below (f + 2) 2^-24; |cos| <= 1
+    c = __fdiv_rn(d, __fsqrt_rn(su) * __fsqrt_rn(sc)) - (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
+    c = fmaxf(c, -1.f);
+  }
+  atomicMin(cosb_ord + j, f2ord(c));
+}
+
+// CBound of every (cluster, item): key = float_desc_key(bound) (sorts
+// descending), value = item position.  [C][n_items], cluster-major.
+__global__ void cbound_kernel(const float* __restrict__ cent, int C, int f, const float* __restrict__ items,
+                              const float* __restrict__ item_nrm, int64_t n_items, const uint32_t* __restrict__ cosb_ord,
+                              uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)C * n_items) return;
+  const int j = (int)(t / n_items);
+  const int64_t i = t - (int64_t)j * n_items;
+  const float* cr = cent + (int64_t)j * f;
+  const float* ir = items + i * f;
+  float d = 0.f, sc = 0.f, si = 0.f;
+  for (int k = 0; k < f; ++k) {
+    d = __fmaf_rn(cr[k], ir[k], d);
+    sc = __fmaf_rn(cr[k], cr[k], sc);
+    si = __fmaf_rn(ir[k], ir[k], si);
+  }
+  const float ni = item_nrm[i];  // upper bound of ||i||
+  const float y = ord2f(cosb_ord[j]);
+  float g;
+  if (si == 0.f) {
+    g = 0.f;  // zero item: bound 0 = its score
+  } else if (sc == 0.f || y <= -1.f) {
+    g = 1.f;  // theta_b = pi: no pruning
+  } else {
+    float x = __fdiv_rn(d, __fsqrt_rn(sc) * __fsqrt_rn(si)) + (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
+    x = fminf(x, 1.f);
+    if (x >= y) {
+      g = 1.f;
+    } else {
+      const float sx = __fsqrt_rn((1.f - x) * (1.f + x));
+      const float sy = __fsqrt_rn((1.f - y) * (1.f + y));
+      g = fminf(1.f, __fmaf_rn(x, y, sx * sy) + 9.5367432e-07f);  // + 2^-20
+    }
+  }
+  // bound = ||i|| g: ni is an upper bound of ||i||, and ||i|| >= ni (1 - (2f + 4) 2^-23)
+  const float bound = g >= 0.f ? ni * g * (1.f + 2.3841858e-07f)
+                               : ni * (1.f - (float)(2 * f + 4) * 1.1920929e-07f) * g * (1.f - 2.3841858e-07f);
+  keys[t] = float_desc_key(bound);
+  vals[t] = (int32_t)i;
+}
+
+__global__ void cosb_init_kernel(uint32_t* __restrict__ cosb_ord, int C) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < C) cosb_ord[j] = f2ord(1.f);
+}
+
+__global__ void cosb_to_float_kernel(const uint32_t* __restrict__ cosb_ord, int C, float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < C) out[j] = ord2f(cosb_ord[j]);
+}
+
+// sorted key -> bound value (float_desc_key is invertible)
+__global__ void keys_to_bounds_kernel(const uint32_t* __restrict__ keys, int64_t n, float* __restrict__ out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  out[t] = ord2f(~keys[t]);
+}
+
+// ---------------------------------------------------------------- grouping
+__global__ void iota_u32_kernel(const int32_t* __restrict__ assign, int64_t n, uint32_t* __restrict__ keys,
+                                int32_t* __restrict__ ids) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  keys[t] = (uint32_t)assign[t];
+  ids[t] = (int32_t)t;
+}
+
+__global__ void cluster_count_kernel(const int32_t* __restrict__ assign, int64_t n, int* __restrict__ counts) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) atomicAdd(&counts[assign[t]], 1);
+}
+
+// offsets[j] = users before cluster j; tile_off[j] = walk tiles before j
+// (128 users per tile); tile_off[C] = total tiles.  One block.
+__global__ void cluster_offsets_kernel(const int* __restrict__ counts, int C, int* __restrict__ offsets,
+                                       int* __restrict__ tile_off) {
+  if (threadIdx.x != 0) return;
+  int o = 0, t = 0;
+  for (int j = 0; j < C; ++j) {
+    offsets[j] = o;
+    tile_off[j] = t;
+    o += counts[j];
+    t += (counts[j] + kThreads - 1) / kThreads;
+  }
+  offsets[C] = o;
+  tile_off[C] = t;
+}
+
+// ---------------------------------------------------------------- walk
+// One block per work item (cluster j, tile of its users), taken from a
+// global counter (persistent grid).  Each thread owns one user: its FP32
+// vector in registers, the select state of common.cuh.  The cluster's
+// sorted list is walked in shared-memory tiles of 32 items (rows gathered
+// by position with cp.async); before each tile every thread checks the stop
+// test of Algorithm 1 with the tile's leading bound (the largest bound of
+// everything not yet visited, the list being sorted):
+//     nhat_u * bound  <  tau_u   (strictly),
+// and the block stops when it holds for all of its users.
+template <int FP>
+__global__ void __launch_bounds__(kThreads, 2)
+    maximus_walk_kernel(const float* __restrict__ users, int f, const float* __restrict__ items,
+                        const float* __restrict__ item_nrm, int64_t n_items, const int32_t* __restrict__ lists,
+                        const float* __restrict__ bounds, const int32_t* __restrict__ user_perm,
+                        const int* __restrict__ offsets, const int* __restrict__ tile_off, int C, int K,
+                        SelectOut o, int32_t* __restrict__ visited, int* __restrict__ work_counter,
+                        DevStats* stats, int* err) {
+  extern __shared__ float4 smem4[];
+  float* tiles = reinterpret_cast<float*>(smem4);     // [2][32][FP]
+  float* nrms = tiles + 2 * kBlockItems * FP;          // [2][32]
+  int32_t* poss = reinterpret_cast<int32_t*>(nrms + 2 * kBlockItems);  // [2][32]
+  float* heap_base = reinterpret_cast<float*>(poss + 2 * kBlockItems); // [K][128]
+  __shared__ int s_work;
+  const int tid = threadIdx.x;
+  const int total = tile_off[C];
+  unsigned long long pairs = 0, blocks = 0;
+
+  for (int e = tid; e < 2 * kBlockItems * FP; e += kThreads) tiles[e] = 0.f;
+
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_work = atomicAdd(work_counter, 1);
+    __syncthreads();
+    const int w = s_work;
+    if (w >= total) break;
+    // cluster of work item w: the last j with tile_off[j] <= w
+    int lo = 0, hi = C - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) / 2;
+      if (tile_off[mid] <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    const int j = lo;
+    const int r0 = offsets[j] + (w - tile_off[j]) * kThreads;
+    const int r = r0 + tid;
+    const bool active = r < offsets[j + 1];
+    const int64_t u = active ? user_perm[r] : 0;
+    float ur[FP];
+    float ss = 0.f;
+#pragma unroll
+    for (int k = 0; k < FP; ++k) {
+      ur[k] = (active && k < f) ? users[u * f + k] : 0.f;
+      ss = __fmaf_rn(ur[k], ur[k], ss);
+    }
+    const float nu = __fsqrt_rn(ss) * (1.0f + (float)(f + 2) * 1.1920929e-07f);
+    const float gu = fp32_score_gamma(f) * nu;
+    UserSelect st;
+    st.tau = active ? kNegInf : __int_as_float(0x7f800000);
+    st.n_cand = 0;
+    st.heap = heap_base + tid;
+    st.stride = kThreads;
+    st.K = K;
+    st.cap = o.cap;
+    st.cand_pos = o.cand_pos + u * (int64_t)o.cap;
+    st.cand_ub = o.cand_ub + u * (int64_t)o.cap;
+    heap_init(st.heap, st.stride, K);
+    const int32_t* L = lists + (int64_t)j * n_items;
+    const float* B = bounds + (int64_t)j * n_items;
+    bool done = !active;
+    int64_t seen = 0;
+    const int64_t n_tiles = (n_items + kBlockItems - 1) / kBlockItems;
+
+    auto load = [&](int buf, int64_t t0) {
+      const int rows = (int)min((int64_t)kBlockItems, n_items - t0);
+      float* tile = tiles + buf * kBlockItems * FP;
+      for (int e = tid; e < rows * f; e += kThreads) {
+        const int rr = e / f, k = e - rr * f;
+        cp_async4(tile + rr * FP + k, items + (int64_t)L[t0 + rr] * f + k);
+      }
+      if (tid < rows) {
+        const int32_t pos = L[t0 + tid];
+        poss[buf * kBlockItems + tid] = pos;
+        cp_async4(nrms + buf * kBlockItems + tid, item_nrm + pos);
+      }
+      cp_async_commit();
+    };
+
+    load(0, 0);
+    for (int64_t t = 0; t < n_tiles; ++t) {
+      const int buf = (int)(t & 1);
+      const int64_t t0 = t * kBlockItems;
+      // stop test with the leading bound of this tile (K items must be seen first)
+      if (!done && seen >= K) {
+        float bnd = nu * B[t0];
+        bnd += fabsf(bnd) * 9.5367432e-07f;  // rounded up whatever its sign (2^-20)
+        if (bnd < st.tau) done = true;
+      }
+      cp_async_wait_all();
+      const int go = __syncthreads_or(!done);
+      if (!go) break;
+      if (t + 1 < n_tiles) load(buf ^ 1, t0 + kBlockItems);
+      ++blocks;
+      const int rows = (int)min((int64_t)kBlockItems, n_items - t0);
+      if (!done) {
+        const float* tile = tiles + buf * kBlockItems * FP;
+        const float* nrm = nrms + buf * kBlockItems;
+        const int32_t* pp = poss + buf * kBlockItems;
+        for (int q = 0; q < rows; ++q) {
+          float acc = 0.f;
+          const float4* row = reinterpret_cast<const float4*>(tile + q * FP);
+#pragma unroll
+          for (int k4 = 0; k4 < FP / 4; ++k4) {
+            const float4 a = row[k4];
+            acc = __fmaf_rn(ur[4 * k4 + 0], a.x, acc);
+            acc = __fmaf_rn(ur[4 * k4 + 1], a.y, acc);
+            acc = __fmaf_rn(ur[4 * k4 + 2], a.z, acc);
+            acc = __fmaf_rn(ur[4 * k4 + 3], a.w, acc);
+          }
+          const float h = __fmaf_rn(gu, nrm[q], acc);
+          if (h >= st.tau) st.offer(h, __fmaf_rn(-gu, nrm[q], acc), pp[q]);
+        }
+        seen += rows;
+      }
+    }
+    cp_async_wait_all();
+    if (active) {
+      o.tau[u] = st.tau;
+      o.n_cand[u] = st.n_cand;
+      visited[u] = (int32_t)seen;
+      pairs += (unsigned long long)seen;
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, off);
+  if ((tid & 31) == 0 && pairs) atomicAdd(&stats->pairs_scored, pairs);
+  if (tid == 0 && blocks) atomicAdd(&stats->blocks_walked, blocks);
+}
+
+template <int FP>
+cudaError_t launch_walk_fp(const float* users, int f, const float* items, const float* item_nrm, int64_t n_items,
+                           const int32_t* lists, const float* bounds, const int32_t* user_perm, const int* offsets,
+                           const int* tile_off, int C, int K, SelectOut o, int32_t* visited, int* work_counter,
+                           DevStats* stats, int* err, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)(2 * kBlockItems * FP + 2 * kBlockItems + 2 * kBlockItems + K * kThreads) * 4;
+  cudaError_t e = cudaFuncSetAttribute(maximus_walk_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  maximus_walk_kernel<FP><<<grid, kThreads, smem, s>>>(users, f, items, item_nrm, n_items, lists, bounds, user_perm,
+                                                       offsets, tile_off, C, K, o, visited, work_counter, stats, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
+                           float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
+                           uint32_t* absmax, float* scale, cudaStream_t s, int* launches) {
+  const int fp = (int)round_up(f, 8);
+  gather_rows_i64<<<(unsigned)((C * f + 255) / 256), 256, 0, s>>>(users, init_ids_dev, C, f, cent);
+  cudaError_t e = cudaMemsetAsync(absmax, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  absmax_kernel<<<152 * 4, 256, 0, s>>>(users, n_users * f, absmax);
+  *launches += 2;
+  kmeans_scale_kernel<<<1, 32, 0, s>>>(absmax, n_users, scale);
+  *launches += 1;
+  for (int it = 0; it < iters; ++it) {
+    half_norm2_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f, hn2);
+    const unsigned blocks = (unsigned)((n_users + kThreads - 1) / kThreads);
+    switch (fp) {
+#define MIPS_KM_CASE(N) \
+  case N:               \
+    kmeans_assign_kernel<N><<<blocks, kThreads, 0, s>>>(users, n_users, f, cent, hn2, C, assign); \
+    break;
+      MIPS_KM_CASE(8) MIPS_KM_CASE(16) MIPS_KM_CASE(24) MIPS_KM_CASE(32) MIPS_KM_CASE(40) MIPS_KM_CASE(48)
+      MIPS_KM_CASE(56) MIPS_KM_CASE(64) MIPS_KM_CASE(72) MIPS_KM_CASE(80) MIPS_KM_CASE(88) MIPS_KM_CASE(96)
+      MIPS_KM_CASE(104) MIPS_KM_CASE(112) MIPS_KM_CASE(120) MIPS_KM_CASE(128)
+#undef MIPS_KM_CASE
+      default:
+        return cudaErrorInvalidValue;
+    }
+    e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * C * f, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned int) * C, s);
+    if (e != cudaSuccess) return e;
+    kmeans_accum_kernel<<<(unsigned)((n_users * f + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, C, scale, sums,
+                                                                            counts);
+    kmeans_update_kernel<<<(C * f + 255) / 256, 256, 0, s>>>(sums, counts, C, f, scale, cent);
+    *launches += 4;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int32_t* assign, const float* cent, int C,
+                           const float* items, const float* item_nrm, int64_t n_items, uint32_t* cosb_ord,
+                           uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches) {
+  cosb_init_kernel<<<(C + 127) / 128, 128, 0, s>>>(cosb_ord, C);
+  cosb_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, cent, cosb_ord);
+  const int64_t n = (int64_t)C * n_items;
+  cbound_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cent, C, f, items, item_nrm, n_items, cosb_ord, keys, vals);
+  cosb_to_float_kernel<<<(C + 127) / 128, 128, 0, s>>>(cosb_ord, C, cosb_f);
+  *launches += 4;
+  return cudaGetLastError();
+}
+
+cudaError_t maximus_group(const int32_t* assign, int64_t n_users, int C, uint32_t* keys, int32_t* ids, uint32_t* keys_alt,
+                          int32_t* ids_alt, uint32_t* temp, int* counts, int* offsets, int* tile_off,
+                          int32_t** user_perm, cudaStream_t s, int* launches) {
+  iota_u32_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, n_users, keys, ids);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * C, s);
+  if (e != cudaSuccess) return e;
+  cluster_count_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, n_users, counts);
+  cluster_offsets_kernel<<<1, 32, 0, s>>>(counts, C, offsets, tile_off);
+  *launches += 3;
+  int bits = 8;
+  while ((1 << bits) < C) bits += 8;
+  e = radix_sort_pairs(keys, ids, keys_alt, ids_alt, n_users, 1, 0, bits, temp, s, launches);
+  *user_perm = ids;
+  return e;
+}
+
+cudaError_t maximus_walk(const float* users, int f, const float* items, const float* item_nrm, int64_t n_items,
+                         const int32_t* lists, const float* bounds, const int32_t* user_perm, const int* offsets,
+                         const int* tile_off, int C, int K, SelectOut o, int32_t* visited, int* work_counter,
+                         DevStats* stats, int* err, int num_sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(work_counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const int grid = num_sms * 4;
+  switch ((int)round_up(f, 8)) {
+#define MIPS_W_CASE(N) \
+  case N:              \
+    return launch_walk_fp<N>(users, f, items, item_nrm, n_items, lists, bounds, user_perm, offsets, tile_off, C, K, o, \
+                             visited, work_counter, stats, err, grid, s);
+    MIPS_W_CASE(8) MIPS_W_CASE(16) MIPS_W_CASE(24) MIPS_W_CASE(32) MIPS_W_CASE(40) MIPS_W_CASE(48) MIPS_W_CASE(56)
+    MIPS_W_CASE(64) MIPS_W_CASE(72) MIPS_W_CASE(80) MIPS_W_CASE(88) MIPS_W_CASE(96) MIPS_W_CASE(104) MIPS_W_CASE(112)
+    MIPS_W_CASE(120) MIPS_W_CASE(128)
+#undef MIPS_W_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t maximus_keys_to_bounds(const uint32_t* keys, int64_t n, float* out, cudaStream_t s) {
+  keys_to_bounds_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(keys, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mips

@@ -5,7 +5,9 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <set>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "tc_topk.h"
@@ -105,6 +107,18 @@ struct mips_index_s {
   int64_t last_users = 0;
   int last_dtype = 0;
   int last_clusters = 0;
+  // views into the workspace of the last Maximus call (mips_get_buffer)
+  struct {
+    const void* assign = nullptr;
+    const void* cent = nullptr;
+    const void* cosb = nullptr;
+    const void* bounds = nullptr;
+    const void* lists = nullptr;
+    const void* visited = nullptr;
+    const void* user_perm = nullptr;
+    int64_t n_users = 0;
+    int C = 0;
+  } mx;
   // per-stage timing: ev[0] = call start, ev[1 + stage] = end of stage
   cudaEvent_t ev[kStages + 1] = {};
   bool stage_ran[kStages] = {};
@@ -153,6 +167,7 @@ int cap_for(int K) { return 4 * K + 96; }
 mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
                     double* out_score, cudaStream_t s) {
   const int f = idx->f;
+  idx->mx.C = 0;  // the workspace is reused: earlier Maximus views are gone
   // candidate pass: tcgen05 BF16 when the index has BF16 operands and the
   // tiling fits shared memory for this K, else the FP32 CUDA-core kernel
   TcParams p{};
@@ -218,6 +233,111 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
   idx->last_users = n_users;
   idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
+  return MIPS_OK;
+}
+
+// C distinct user ids from a counter-based stream (SplitMix64 of seed and
+// counter), Floyd's method: the k-means initial centroids.
+void draw_init_ids(int64_t n, int C, uint64_t seed, std::vector<int64_t>& out) {
+  auto mix = [](uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  out.clear();
+  std::set<int64_t> chosen;
+  uint64_t ctr = 0;
+  for (int64_t j = n - C; j < n; ++j) {
+    const int64_t t = (int64_t)(mix(seed ^ mix(++ctr)) % (uint64_t)(j + 1));
+    const int64_t pick = chosen.count(t) ? j : t;
+    chosen.insert(pick);
+    out.push_back(pick);
+  }
+}
+
+// Maximus (Sec. IV, Algorithm 1): k-means, theta_b + CBound, per-cluster
+// sort and user grouping, grouped walk, exact rescore.
+mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
+                        double* out_score, cudaStream_t s) {
+  const int f = idx->f;
+  const int64_t nI = idx->n_items;
+  const int C = (int)(idx->clusters < n_users ? idx->clusters : n_users);
+  const int cap = cap_for(K);
+  const int64_t CI = (int64_t)C * nI;
+  Arena& ws = idx->ws;
+  ws.reset();
+  size_t o_ids = ws.take(sizeof(int64_t) * C), o_cent = ws.take(sizeof(float) * C * f), o_hn2 = ws.take(sizeof(float) * C);
+  size_t o_assign = ws.take(sizeof(int32_t) * n_users), o_sums = ws.take(sizeof(unsigned long long) * C * f);
+  size_t o_cnt = ws.take(sizeof(unsigned) * C), o_amax = ws.take(16), o_scale = ws.take(16);
+  size_t o_cosb = ws.take(sizeof(uint32_t) * C), o_cosbf = ws.take(sizeof(float) * C);
+  size_t o_keys = ws.take(sizeof(uint32_t) * CI), o_vals = ws.take(sizeof(int32_t) * CI);
+  size_t o_keys2 = ws.take(sizeof(uint32_t) * CI), o_vals2 = ws.take(sizeof(int32_t) * CI);
+  size_t o_tmp = ws.take(radix_sort_temp_bytes(nI, C) > radix_sort_temp_bytes(n_users, 1)
+                             ? radix_sort_temp_bytes(nI, C)
+                             : radix_sort_temp_bytes(n_users, 1));
+  size_t o_bounds = ws.take(sizeof(float) * CI);
+  size_t o_uk = ws.take(sizeof(uint32_t) * n_users), o_ui = ws.take(sizeof(int32_t) * n_users);
+  size_t o_uk2 = ws.take(sizeof(uint32_t) * n_users), o_ui2 = ws.take(sizeof(int32_t) * n_users);
+  size_t o_ccnt = ws.take(sizeof(int) * C), o_off = ws.take(sizeof(int) * (C + 1)), o_toff = ws.take(sizeof(int) * (C + 1));
+  size_t o_wc = ws.take(16), o_vis = ws.take(sizeof(int32_t) * n_users);
+  size_t o_tau = ws.take(sizeof(float) * n_users), o_n = ws.take(sizeof(int) * n_users);
+  size_t o_pos = ws.take(sizeof(int32_t) * n_users * cap), o_ub = ws.take(sizeof(float) * n_users * cap);
+  size_t o_ovf = ws.take(sizeof(int32_t) * n_users), o_ovfc = ws.take(sizeof(int));
+  size_t o_work = ws.take(sizeof(uint32_t) * n_users * cap), o_workc = ws.take(sizeof(int));
+  size_t o_sc = ws.take(sizeof(double) * n_users * cap), o_tauf = ws.take(sizeof(float) * n_users);
+  MIPS_CUDA(ws.ensure(ws.used, s));
+
+  // k-means initial centroids: a seeded draw of C distinct users
+  std::vector<int64_t> ids;
+  draw_init_ids(n_users, C, idx->opt.seed, ids);
+  MIPS_CUDA(cudaMemcpyAsync(ws.at<int64_t>(o_ids), ids.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
+  mips_status st;
+  MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids), ws.at<float>(o_cent),
+                           ws.at<float>(o_hn2), ws.at<int32_t>(o_assign), ws.at<unsigned long long>(o_sums),
+                           ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax), ws.at<float>(o_scale), s, &idx->launches));
+  if ((st = end_stage(idx, ST_KMEANS, s)) != MIPS_OK) return st;
+  MIPS_CUDA(maximus_bounds(users, n_users, f, ws.at<int32_t>(o_assign), ws.at<float>(o_cent), C, idx->items,
+                           idx->item_nrm, nI, ws.at<uint32_t>(o_cosb), ws.at<uint32_t>(o_keys), ws.at<int32_t>(o_vals),
+                           ws.at<float>(o_cosbf), s, &idx->launches));
+  if ((st = end_stage(idx, ST_BOUNDS, s)) != MIPS_OK) return st;
+  // per-cluster lists: items by CBound, descending (stable: ties by position)
+  uint32_t* keys = ws.at<uint32_t>(o_keys);
+  int32_t* vals = ws.at<int32_t>(o_vals);
+  uint32_t* keys2 = ws.at<uint32_t>(o_keys2);
+  int32_t* vals2 = ws.at<int32_t>(o_vals2);
+  MIPS_CUDA(radix_sort_pairs(keys, vals, keys2, vals2, nI, C, 0, 32, ws.at<uint32_t>(o_tmp), s, &idx->launches));
+  MIPS_CUDA(maximus_keys_to_bounds(keys, CI, ws.at<float>(o_bounds), s));
+  idx->launches += 1;
+  int32_t* user_perm = nullptr;
+  MIPS_CUDA(maximus_group(ws.at<int32_t>(o_assign), n_users, C, ws.at<uint32_t>(o_uk), ws.at<int32_t>(o_ui),
+                          ws.at<uint32_t>(o_uk2), ws.at<int32_t>(o_ui2), ws.at<uint32_t>(o_tmp), ws.at<int>(o_ccnt),
+                          ws.at<int>(o_off), ws.at<int>(o_toff), &user_perm, s, &idx->launches));
+  if ((st = end_stage(idx, ST_SORT, s)) != MIPS_OK) return st;
+  SelectOut so{ws.at<float>(o_tau), ws.at<int>(o_n), ws.at<int32_t>(o_pos), ws.at<float>(o_ub), cap, 1, nullptr, 0,
+               ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc), ws.at<uint32_t>(o_work), ws.at<int>(o_workc),
+               ws.at<double>(o_sc), ws.at<float>(o_tauf)};
+  MIPS_CUDA(maximus_walk(users, f, idx->items, idx->item_nrm, nI, vals, ws.at<float>(o_bounds), user_perm,
+                         ws.at<int>(o_off), ws.at<int>(o_toff), C, K, so, ws.at<int32_t>(o_vis), ws.at<int>(o_wc),
+                         idx->stats_dev, idx->err_dev, idx->num_sms, s));
+  idx->launches += 1;
+  if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
+  MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
+                           idx->stats_dev, idx->err_dev, s));
+  idx->launches += 4;
+  if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
+  idx->mx.assign = ws.at<int32_t>(o_assign);
+  idx->mx.cent = ws.at<float>(o_cent);
+  idx->mx.cosb = ws.at<float>(o_cosbf);
+  idx->mx.bounds = ws.at<float>(o_bounds);
+  idx->mx.lists = vals;
+  idx->mx.visited = ws.at<int32_t>(o_vis);
+  idx->mx.user_perm = user_perm;
+  idx->mx.n_users = n_users;
+  idx->mx.C = C;
+  idx->last_users = n_users;
+  idx->last_clusters = C;
+  idx->last_dtype = MIPS_FP32;
   return MIPS_OK;
 }
 
@@ -355,8 +475,10 @@ mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t 
   g_err.clear();
   mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
   if (st != MIPS_OK) return st;
-  (void)stream;
-  return fail(MIPS_ERR_UNIMPLEMENTED, "Maximus path not built yet");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = begin_call(idx, s)) != MIPS_OK) return st;
+  if ((st = run_maximus(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s)) != MIPS_OK) return st;
+  return end_call(idx, s);
 }
 
 mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
@@ -468,8 +590,29 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
   } else if (!strcmp(name, "item_nrm")) {
     *dev_ptr = idx->item_nrm;
     *bytes = sizeof(float) * idx->n_items;
+  } else if (idx->mx.C > 0 && !strcmp(name, "assign")) {
+    *dev_ptr = idx->mx.assign;
+    *bytes = sizeof(int32_t) * idx->mx.n_users;
+  } else if (idx->mx.C > 0 && !strcmp(name, "centroids")) {
+    *dev_ptr = idx->mx.cent;
+    *bytes = sizeof(float) * (int64_t)idx->mx.C * idx->f;
+  } else if (idx->mx.C > 0 && !strcmp(name, "cos_b")) {
+    *dev_ptr = idx->mx.cosb;
+    *bytes = sizeof(float) * idx->mx.C;
+  } else if (idx->mx.C > 0 && !strcmp(name, "bound_sorted")) {
+    *dev_ptr = idx->mx.bounds;
+    *bytes = sizeof(float) * (int64_t)idx->mx.C * idx->n_items;
+  } else if (idx->mx.C > 0 && !strcmp(name, "list")) {
+    *dev_ptr = idx->mx.lists;
+    *bytes = sizeof(int32_t) * (int64_t)idx->mx.C * idx->n_items;
+  } else if (idx->mx.C > 0 && !strcmp(name, "visited")) {
+    *dev_ptr = idx->mx.visited;
+    *bytes = sizeof(int32_t) * idx->mx.n_users;
+  } else if (idx->mx.C > 0 && !strcmp(name, "user_perm")) {
+    *dev_ptr = idx->mx.user_perm;
+    *bytes = sizeof(int32_t) * idx->mx.n_users;
   } else {
-    return fail(MIPS_ERR_ARG, "unknown buffer name: %s", name);
+    return fail(MIPS_ERR_ARG, "unknown buffer name (or no Maximus call yet): %s", name);
   }
   return MIPS_OK;
 }

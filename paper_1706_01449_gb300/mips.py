@@ -260,7 +260,7 @@ def get_buffer(index: Index, name: str, dtype, shape):
         raise ValueError(f"buffer {name} holds {nbytes.value} bytes, shape asks for {count * esize}")
 
     class _View:
-        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (p.value, True),
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (p.value, False),
                                     "version": 3, "strides": None}
 
     return torch.as_tensor(_View(), device="cuda").clone()
