@@ -49,6 +49,9 @@ void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* er
 // role 0 = users (A operand), role 1 = items (B operand).
 void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void* out_bf16,
                        int64_t n_rows_out, float2* aux, int* err, cudaStream_t s);
+// dst rows[r] <- src row r, for [n][K] top-K outputs.
+void launch_scatter_topk(const int32_t* src_idx, const double* src_sc, const int32_t* rows, int64_t n, int K,
+                         int32_t* dst_idx, double* dst_sc, cudaStream_t s);
 // Gather rows of x by perm into out (out[r] = x[perm[r]]).
 void launch_gather_rows(const float* x, const int32_t* perm, int64_t n, int f, float* out, cudaStream_t s);
 

@@ -1,6 +1,7 @@
 // The C ABI of libmips (declared in include/mips.h): argument checks, the
 // index object, its workspace arena, and the dispatch of each call to its
 // kernels.  No C++ exception crosses the boundary.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -99,6 +100,7 @@ struct mips_index_s {
   int max_smem = 0;
   // per-call state
   Arena ws;
+  Arena ws_sel;  // the selector's own buffers (sample, rest, their outputs)
   int* err_dev = nullptr;
   DevStats* stats_dev = nullptr;
   cudaEvent_t done = nullptr;   // end of the last call (orders calls on different streams)
@@ -123,6 +125,8 @@ struct mips_index_s {
   cudaEvent_t ev[kStages + 1] = {};
   bool stage_ran[kStages] = {};
   int last_stage = -1;
+  int order[kStages] = {};  // stages in the order they ran in the last call
+  int n_order = 0;
   int launches = 0;
 };
 
@@ -140,6 +144,7 @@ mips_status begin_call(mips_index_t idx, cudaStream_t s) {
   MIPS_CUDA(cudaMemsetAsync(idx->stats_dev, 0, sizeof(DevStats), s));
   for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
   idx->last_stage = -1;
+  idx->n_order = 0;
   idx->launches = 0;
   MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
   return MIPS_OK;
@@ -148,6 +153,7 @@ mips_status begin_call(mips_index_t idx, cudaStream_t s) {
 // Mark the end of a stage (stages run in enum order within one call).
 mips_status end_stage(mips_index_t idx, Stage st, cudaStream_t s) {
   MIPS_CUDA(cudaEventRecord(idx->ev[1 + st], s));
+  if (!idx->stage_ran[st] && idx->n_order < kStages) idx->order[idx->n_order++] = st;
   idx->stage_ran[st] = true;
   idx->last_stage = st;
   return MIPS_OK;
@@ -341,6 +347,102 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   return MIPS_OK;
 }
 
+double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
+  float t = 0.f;
+  cudaEventElapsedTime(&t, a, b);
+  return t;
+}
+
+// Optimus (Sec. V): time a user sample on both paths, extrapolate, finish
+// the other users with the faster one, reuse the sample's results.
+mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
+                       double* out_score, cudaStream_t s, mips_select_report* rep) {
+  // sample size: the requested fraction, but at least two waves of user
+  // tiles on every SM (the hardware-effects floor, here the GPU's analogue
+  // of the L2-sized sample)
+  const int64_t floor_users = 2ll * idx->num_sms * 128;
+  int64_t ns = (int64_t)ceil(idx->opt.sample_frac * (double)n_users);
+  if (ns < floor_users) ns = floor_users;
+  if (ns > n_users) ns = n_users;
+  // seeded sample of distinct users, ascending; the rest, ascending
+  std::vector<int64_t> pick;
+  draw_init_ids(n_users, (int)ns, idx->opt.seed ^ 0x5EEDull, pick);
+  std::vector<char> in_sample((size_t)n_users, 0);
+  for (int64_t v : pick) in_sample[v] = 1;
+  std::vector<int32_t> sample, rest;
+  sample.reserve(ns);
+  rest.reserve(n_users - ns);
+  for (int64_t u = 0; u < n_users; ++u) (in_sample[u] ? sample : rest).push_back((int32_t)u);
+  const int64_t nr = n_users - ns;
+  const int f = idx->f;
+  Arena& w = idx->ws_sel;
+  w.reset();
+  size_t o_sid = w.take(4 * ns), o_rid = w.take(4 * (nr > 0 ? nr : 1));
+  size_t o_su = w.take(sizeof(float) * ns * f), o_ru = w.take(sizeof(float) * (nr > 0 ? nr : 1) * f);
+  size_t o_bi = w.take(4 * ns * K), o_bs = w.take(8 * ns * K), o_mi = w.take(4 * ns * K), o_ms = w.take(8 * ns * K);
+  size_t o_ri = w.take(4 * (nr > 0 ? nr : 1) * K), o_rs = w.take(8 * (nr > 0 ? nr : 1) * K);
+  MIPS_CUDA(w.ensure(w.used, s));
+  MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_sid), sample.data(), 4 * ns, cudaMemcpyHostToDevice, s));
+  if (nr > 0) MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_rid), rest.data(), 4 * nr, cudaMemcpyHostToDevice, s));
+  launch_gather_rows(users, w.at<int32_t>(o_sid), ns, f, w.at<float>(o_su), s);
+  if (nr > 0) launch_gather_rows(users, w.at<int32_t>(o_rid), nr, f, w.at<float>(o_ru), s);
+  MIPS_CUDA(cudaGetLastError());
+
+  cudaEvent_t e[3];
+  for (auto& x : e) MIPS_CUDA(cudaEventCreate(&x));
+  struct Guard {
+    cudaEvent_t* e;
+    ~Guard() {
+      for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+    }
+  } guard{e};
+  mips_status st;
+  // blocked multiply on the sample (M_I)
+  MIPS_CUDA(cudaEventRecord(e[0], s));
+  if ((st = run_bmm(idx, w.at<float>(o_su), ns, K, w.at<int32_t>(o_bi), w.at<double>(o_bs), s)) != MIPS_OK) return st;
+  MIPS_CUDA(cudaEventRecord(e[1], s));
+  // Maximus on the sample (C_I and Q_I); its stage times restart here
+  for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
+  idx->n_order = 0;
+  idx->last_stage = -1;
+  MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
+  if ((st = run_maximus(idx, w.at<float>(o_su), ns, K, w.at<int32_t>(o_mi), w.at<double>(o_ms), s)) != MIPS_OK)
+    return st;
+  MIPS_CUDA(cudaEventRecord(e[2], s));
+  MIPS_CUDA(cudaEventSynchronize(e[2]));
+  mips_stats mx;
+  if ((st = mips_get_stats(idx, &mx)) != MIPS_OK) return st;
+  const double t_bmm = elapsed_ms(e[0], e[1]) * 1e-3;
+  const double t_mx = elapsed_ms(e[1], e[2]) * 1e-3;
+  // construction: k-means work grows with the users, bounds and sort do not
+  const double c_i = (mx.ms_kmeans * (double)n_users / (double)ns + mx.ms_bounds + mx.ms_sort) * 1e-3;
+  const double q_i = (t_mx - (mx.ms_kmeans + mx.ms_bounds + mx.ms_sort) * 1e-3) / (double)ns;
+  const double m_i = t_bmm / (double)ns;
+  mips_select_report r{};
+  r.t_build = c_i;
+  r.q_user = q_i;
+  r.m_user = m_i;
+  r.sample_users = ns;
+  r.est_index = c_i + (double)n_users * q_i;
+  r.est_bmm = (double)n_users * m_i;
+  r.choice = r.est_index < r.est_bmm ? 1 : 0;
+  if (rep) *rep = r;
+  // the sample's results (both paths are exact and agree), then the rest
+  launch_scatter_topk(w.at<int32_t>(r.choice ? o_mi : o_bi), w.at<double>(r.choice ? o_ms : o_bs),
+                      w.at<int32_t>(o_sid), ns, K, out_idx, out_score, s);
+  if (nr > 0) {
+    if (r.choice == 1)
+      st = run_maximus(idx, w.at<float>(o_ru), nr, K, w.at<int32_t>(o_ri), w.at<double>(o_rs), s);
+    else
+      st = run_bmm(idx, w.at<float>(o_ru), nr, K, w.at<int32_t>(o_ri), w.at<double>(o_rs), s);
+    if (st != MIPS_OK) return st;
+    launch_scatter_topk(w.at<int32_t>(o_ri), w.at<double>(o_rs), w.at<int32_t>(o_rid), nr, K, out_idx, out_score, s);
+  }
+  MIPS_CUDA(cudaGetLastError());
+  idx->last_users = n_users;
+  return MIPS_OK;
+}
+
 mips_status check_call(mips_index_t idx, const void* users, int64_t n_users, int K, const void* oi,
                        const void* os) {
   if (!idx) return fail(MIPS_ERR_ARG, "null index");
@@ -487,9 +589,10 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
   g_err.clear();
   mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
   if (st != MIPS_OK) return st;
-  (void)stream;
-  (void)rep;
-  return fail(MIPS_ERR_UNIMPLEMENTED, "Optimus selector not built yet");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = begin_call(idx, s)) != MIPS_OK) return st;
+  if ((st = run_select(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s, rep)) != MIPS_OK) return st;
+  return end_call(idx, s);
 }
 
 mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_users, int K, int method,
@@ -561,8 +664,8 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out) {
   double ms[kStages] = {};
   cudaEvent_t prev = idx->ev[0];
   float t = 0.f;
-  for (int i = 0; i < kStages; ++i) {
-    if (!idx->stage_ran[i]) continue;
+  for (int q = 0; q < idx->n_order; ++q) {  // in the order the stages ran
+    const int i = idx->order[q];
     MIPS_CUDA(cudaEventElapsedTime(&t, prev, idx->ev[1 + i]));
     ms[i] = t;
     prev = idx->ev[1 + i];
@@ -621,6 +724,7 @@ void mips_free_index(mips_index_t idx) {
   if (!idx) return;
   if (idx->has_done) cudaEventSynchronize(idx->done);
   if (idx->ws.base) cudaFree(idx->ws.base);
+  if (idx->ws_sel.base) cudaFree(idx->ws_sel.base);
   cudaFree(idx->items);
   cudaFree(idx->perm);
   cudaFree(idx->item_nrm);

@@ -110,7 +110,24 @@ __global__ void gather_rows_kernel(const float* __restrict__ x, const int32_t* _
   out[t] = x[(int64_t)perm[r] * f + k];
 }
 
+__global__ void scatter_topk_kernel(const int32_t* __restrict__ src_idx, const double* __restrict__ src_sc,
+                                    const int32_t* __restrict__ rows, int64_t n, int K, int32_t* __restrict__ dst_idx,
+                                    double* __restrict__ dst_sc) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * K) return;
+  const int64_t r = t / K;
+  const int k = (int)(t - r * K);
+  dst_idx[(int64_t)rows[r] * K + k] = src_idx[t];
+  dst_sc[(int64_t)rows[r] * K + k] = src_sc[t];
+}
+
 }  // namespace
+
+void launch_scatter_topk(const int32_t* src_idx, const double* src_sc, const int32_t* rows, int64_t n, int K,
+                         int32_t* dst_idx, double* dst_sc, cudaStream_t s) {
+  if (n <= 0) return;
+  scatter_topk_kernel<<<(unsigned)((n * K + 255) / 256), 256, 0, s>>>(src_idx, src_sc, rows, n, K, dst_idx, dst_sc);
+}
 
 void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* err, cudaStream_t s) {
   if (n <= 0) return;
