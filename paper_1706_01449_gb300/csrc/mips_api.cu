@@ -235,7 +235,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   }
   MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, idx->n_items, K, so,
                            out_idx, out_score, idx->stats_dev, idx->err_dev, s));
-  idx->launches += 1;
+  idx->launches += 4;  // collect, dot, select, overflow
   if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
   idx->last_users = n_users;
   idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
