@@ -123,6 +123,17 @@ cudaError_t maximus_walk(const float* users, int f, const float* items, const fl
                          const int* tile_off, int C, int K, SelectOut o, int32_t* visited, int* work_counter,
                          DevStats* stats, int* err, int num_sms, cudaStream_t s);
 cudaError_t maximus_keys_to_bounds(const uint32_t* keys, int64_t n, float* out, cudaStream_t s);
+// tensor-core walk: operand layouts and pass-1 work list / pass-2 work list
+cudaError_t mx_tc_prepare(const int* counts, int C, const int32_t* user_perm, int64_t n_users, const int* offsets,
+                          int* pad_off, int32_t* row_user, int64_t n_rows_max, int32_t* user_row, const void* users_bf16,
+                          int fp, void* a_rows, const void* items_bf16, const float2* item_aux, const int32_t* lists,
+                          int64_t n_items, int64_t n_pad, void* b_rows, float2* aux_c, int32_t* pos_c, int t1,
+                          int* a_row1, int* b_row1, int* tb1, int* te1, int* n_work1, cudaStream_t s, int* launches);
+cudaError_t mx_tc_pass2(const int32_t* assign, const float2* user_aux, int64_t n_users, const float* bounds,
+                        int64_t n_items, int t1, SelectOut o, int K, const int32_t* user_row, int* work_end,
+                        int64_t max_work, const int* n_work1, const int* a_row1, const int* b_row1, int* a_row2,
+                        int* b_row2, int* tb2, int* te2, int* n_work2, int32_t* visited, DevStats* stats, cudaStream_t s,
+                        int* launches);
 
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);

@@ -277,8 +277,10 @@ __global__ void cluster_offsets_kernel(const int* __restrict__ counts, int C, in
 // by position with cp.async); before each tile every thread checks the stop
 // test of Algorithm 1 with the tile's leading bound (the largest bound of
 // everything not yet visited, the list being sorted):
-//     nhat_u * bound  <  tau_u   (strictly),
-// and the block stops when it holds for all of its users.
+//     max(nhat_u * bound, 0)  <  tau_u   (strictly)
+// (the clamp: a negative CBound times norm upper bounds is no upper bound
+// on a negative score), and the block stops when it holds for all of its
+// users.
 template <int FP>
 __global__ void __launch_bounds__(kThreads, 2)
     maximus_walk_kernel(const float* __restrict__ users, int f, const float* __restrict__ items,
@@ -363,8 +365,10 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int64_t t0 = t * kBlockItems;
       // stop test with the leading bound of this tile (K items must be seen first)
       if (!done && seen >= K) {
-        float bnd = nu * B[t0];
-        bnd += fabsf(bnd) * 9.5367432e-07f;  // rounded up whatever its sign (2^-20)
+        // a negative bound counts as 0: nhat_u, nhat_i exceed the true
+        // norms, which would make a negative product too small
+        float bnd = fmaxf(nu * B[t0], 0.f);
+        bnd += bnd * 9.5367432e-07f;  // rounded up (2^-20)
         if (bnd < st.tau) done = true;
       }
       cp_async_wait_all();
@@ -421,7 +425,207 @@ cudaError_t launch_walk_fp(const float* users, int f, const float* items, const 
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- tensor-core walk
+// Cluster-ordered A rows: each cluster's users start at a 128-aligned row
+// (pad_off), padding rows map to user -1.  One thread.
+__global__ void mx_pad_layout_kernel(const int* __restrict__ counts, int C, int* __restrict__ pad_off) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int o = 0;
+  for (int j = 0; j < C; ++j) {
+    pad_off[j] = o;
+    o += (counts[j] + kThreads - 1) / kThreads * kThreads;
+  }
+  pad_off[C] = o;
+}
+
+__device__ __forceinline__ int find_segment(const int* __restrict__ off, int C, int x) {  // last j: off[j] <= x
+  int lo = 0, hi = C - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (off[mid] <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// row_user[row] = user, user_row[user] = row, for every user (sorted rank r)
+__global__ void mx_row_map_kernel(const int32_t* __restrict__ user_perm, int64_t n_users, const int* __restrict__ offsets,
+                                  const int* __restrict__ pad_off, int C, int32_t* __restrict__ row_user,
+                                  int32_t* __restrict__ user_row) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_users) return;
+  const int j = find_segment(offsets, C, (int)r);
+  const int row = pad_off[j] + (int)(r - offsets[j]);
+  const int32_t u = user_perm[r];
+  row_user[row] = u;
+  user_row[u] = row;
+}
+
+// dst[r] = src[map[r]] (BF16 rows of fp elements), zero rows for map < 0;
+// 16-byte words.
+__global__ void mx_gather_bf16_kernel(const uint4* __restrict__ src, const int32_t* __restrict__ map, int64_t n_rows,
+                                      int words, uint4* __restrict__ dst) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_rows * words) return;
+  const int64_t r = t / words;
+  const int w = (int)(t - r * words);
+  const int32_t m = map[r];
+  dst[t] = m >= 0 ? src[(int64_t)m * words + w] : make_uint4(0, 0, 0, 0);
+}
+
+// Per-cluster item copies in list order, rows [j * n_pad, j * n_pad + n_pad):
+// BF16 operand rows, bound columns and positions (padding: zero / 0).
+__global__ void mx_items_by_cluster_kernel(const uint4* __restrict__ items_bf16, const float2* __restrict__ item_aux,
+                                           const int32_t* __restrict__ lists, int64_t n_items, int64_t n_pad, int C,
+                                           int words, uint4* __restrict__ b_rows, float2* __restrict__ aux_c,
+                                           int32_t* __restrict__ pos_c) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)C * n_pad * words) return;
+  const int64_t r = t / words;
+  const int w = (int)(t - r * words);
+  const int64_t j = r / n_pad, rank = r - j * n_pad;
+  if (rank < n_items) {
+    const int32_t pos = lists[j * n_items + rank];
+    b_rows[t] = items_bf16[(int64_t)pos * words + w];
+    if (w == 0) {
+      aux_c[r] = item_aux[pos];
+      pos_c[r] = pos;
+    }
+  } else {
+    b_rows[t] = make_uint4(0, 0, 0, 0);
+    if (w == 0) {
+      aux_c[r] = make_float2(0.f, 0.f);
+      pos_c[r] = 0;
+    }
+  }
+}
+
+// Pass-1 work list: every 128-row user tile against the first t1 item tiles
+// of its cluster's list.
+__global__ void mx_work1_kernel(const int* __restrict__ pad_off, int C, int64_t n_pad, int t1, int* __restrict__ a_row,
+                                int* __restrict__ b_row, int* __restrict__ tb, int* __restrict__ te,
+                                int* __restrict__ n_work) {
+  const int n = pad_off[C] / kThreads;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w == 0) *n_work = n;
+  if (w >= n) return;
+  const int j = find_segment(pad_off, C, w * kThreads);
+  a_row[w] = w * kThreads;
+  b_row[w] = (int)(j * n_pad);
+  tb[w] = 0;
+  te[w] = t1;
+}
+
+// Stop rank of every user after pass 1: the first list rank r >= r1 with
+// max(nhat_u * bound(r), 0) < tau_u (rounded up), tau_u the K-th
+// largest of the union of its two sub-lists' lower bounds (or their
+// thresholds); the work item of the user's tile must walk ceil(r / 256)
+// item tiles.  Users with no such rank walk the whole list.
+__global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux, int64_t n_users,
+                               const float* __restrict__ bounds, int64_t n_items, int r1, SelectOut o, int K,
+                               const int32_t* __restrict__ user_row, int* __restrict__ work_end) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_users) return;
+  const int64_t l0 = u * 2;
+  float tau = fmaxf(o.tau[l0], o.tau[l0 + 1]);
+  if (o.topl && o.topl_sorted) {
+    const float* a = o.topl + l0 * K;
+    const float* b = a + K;
+    int ia = 0, ib = 0;
+    float v = __int_as_float(0xff800000);
+    for (int r = 0; r < K; ++r) {
+      if (a[ia] >= b[ib]) v = a[ia++];
+      else v = b[ib++];
+    }
+    tau = fmaxf(tau, v);
+  }
+  const float nu = user_aux[u].y;
+  const float* B = bounds + (int64_t)assign[u] * n_items;
+  int64_t lo = r1 < n_items ? r1 : n_items, hi = n_items;  // first rank in [lo, hi) that stops; hi = none
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    float bnd = fmaxf(nu * B[mid], 0.f);  // negative bounds count as 0, as in the walk
+    bnd += bnd * 9.5367432e-07f;           // rounded up (2^-20)
+    if (bnd < tau) hi = mid;
+    else lo = mid + 1;
+  }
+  const int tiles = (int)((lo + 255) / 256);
+  atomicMax(&work_end[user_row[u] / kThreads], tiles);
+}
+
+// Pass-2 work list: the pass-1 items whose users need more item tiles.
+__global__ void mx_work2_kernel(const int* __restrict__ n_work1, const int* __restrict__ a_row1,
+                                const int* __restrict__ b_row1, const int* __restrict__ work_end, int t1,
+                                int* __restrict__ a_row2, int* __restrict__ b_row2, int* __restrict__ tb2,
+                                int* __restrict__ te2, int* __restrict__ n_work2, DevStats* stats) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= *n_work1) return;
+  const int end = work_end[w];
+  unsigned long long tiles = (unsigned long long)t1;
+  if (end > t1) {
+    const int q = atomicAdd(n_work2, 1);
+    a_row2[q] = a_row1[w];
+    b_row2[q] = b_row1[w];
+    tb2[q] = t1;
+    te2[q] = end;
+    tiles = end;
+  }
+  atomicAdd(&stats->blocks_walked, tiles);
+}
+
+// Items each user scored: the tiles its work item walked.
+__global__ void mx_visited_kernel(const int32_t* __restrict__ user_row, int64_t n_users, const int* __restrict__ work_end,
+                                  int t1, int64_t n_items, int32_t* __restrict__ visited,
+                                  unsigned long long* __restrict__ pairs) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_users) return;
+  const int end = max(t1, work_end[user_row[u] / kThreads]);
+  const int64_t v = min((int64_t)end * 256, n_items);
+  visited[u] = (int32_t)v;
+  atomicAdd(pairs, (unsigned long long)v);
+}
+
 }  // namespace
+
+cudaError_t mx_tc_prepare(const int* counts, int C, const int32_t* user_perm, int64_t n_users, const int* offsets,
+                          int* pad_off, int32_t* row_user, int64_t n_rows_max, int32_t* user_row, const void* users_bf16,
+                          int fp, void* a_rows, const void* items_bf16, const float2* item_aux, const int32_t* lists,
+                          int64_t n_items, int64_t n_pad, void* b_rows, float2* aux_c, int32_t* pos_c, int t1,
+                          int* a_row1, int* b_row1, int* tb1, int* te1, int* n_work1, cudaStream_t s, int* launches) {
+  const int words = fp * 2 / 16;
+  mx_pad_layout_kernel<<<1, 32, 0, s>>>(counts, C, pad_off);
+  cudaError_t e = cudaMemsetAsync(row_user, 0xff, sizeof(int32_t) * n_rows_max, s);
+  if (e != cudaSuccess) return e;
+  mx_row_map_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(user_perm, n_users, offsets, pad_off, C, row_user,
+                                                                      user_row);
+  mx_gather_bf16_kernel<<<(unsigned)((n_rows_max * words + 255) / 256), 256, 0, s>>>(
+      (const uint4*)users_bf16, row_user, n_rows_max, words, (uint4*)a_rows);
+  const int64_t tot = (int64_t)C * n_pad * words;
+  mx_items_by_cluster_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      (const uint4*)items_bf16, item_aux, lists, n_items, n_pad, C, words, (uint4*)b_rows, aux_c, pos_c);
+  const int max_work = (int)(n_rows_max / kThreads);
+  mx_work1_kernel<<<(max_work + 255) / 256, 256, 0, s>>>(pad_off, C, n_pad, t1, a_row1, b_row1, tb1, te1, n_work1);
+  *launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t mx_tc_pass2(const int32_t* assign, const float2* user_aux, int64_t n_users, const float* bounds,
+                        int64_t n_items, int t1, SelectOut o, int K, const int32_t* user_row, int* work_end,
+                        int64_t max_work, const int* n_work1, const int* a_row1, const int* b_row1, int* a_row2,
+                        int* b_row2, int* tb2, int* te2, int* n_work2, int32_t* visited, DevStats* stats, cudaStream_t s,
+                        int* launches) {
+  cudaError_t e = cudaMemsetAsync(work_end, 0, sizeof(int) * max_work, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n_work2, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  mx_stop_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, user_aux, n_users, bounds, n_items, t1 * 256,
+                                                                    o, K, user_row, work_end);
+  mx_work2_kernel<<<(unsigned)((max_work + 255) / 256), 256, 0, s>>>(n_work1, a_row1, b_row1, work_end, t1, a_row2,
+                                                                      b_row2, tb2, te2, n_work2, stats);
+  mx_visited_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(user_row, n_users, work_end, t1, n_items, visited,
+                                                                      &stats->pairs_scored);
+  *launches += 3;
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- host side
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,

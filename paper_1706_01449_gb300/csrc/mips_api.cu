@@ -271,6 +271,16 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int C = (int)(idx->clusters < n_users ? idx->clusters : n_users);
   const int cap = cap_for(K);
   const int64_t CI = (int64_t)C * nI;
+  // walk on tcgen05 when the index has BF16 operands and the tiling fits
+  TcParams p{};
+  p.n_users = n_users;
+  p.n_items = nI;
+  p.f = f;
+  p.fp = idx->fp;
+  p.K = K;
+  // (TMA row coordinates of the per-cluster item copies are 32-bit)
+  const bool use_tc = idx->opt.dtype == MIPS_BF16 && (int64_t)C * round_up(nI, 256) < (int64_t)INT32_MAX &&
+                      round_up(n_users, 128) + 128ll * C < (int64_t)INT32_MAX && tc_plan(p, idx->max_smem);
   Arena& ws = idx->ws;
   ws.reset();
   size_t o_ids = ws.take(sizeof(int64_t) * C), o_cent = ws.take(sizeof(float) * C * f), o_hn2 = ws.take(sizeof(float) * C);
@@ -288,10 +298,48 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_ccnt = ws.take(sizeof(int) * C), o_off = ws.take(sizeof(int) * (C + 1)), o_toff = ws.take(sizeof(int) * (C + 1));
   size_t o_wc = ws.take(16), o_vis = ws.take(sizeof(int32_t) * n_users);
   size_t o_tau = ws.take(sizeof(float) * n_users), o_n = ws.take(sizeof(int) * n_users);
-  size_t o_pos = ws.take(sizeof(int32_t) * n_users * cap), o_ub = ws.take(sizeof(float) * n_users * cap);
+  const int64_t cap1 = use_tc ? 0 : cap;  // the FP32 walk's single-list candidate buffers
+  size_t o_pos = ws.take(sizeof(int32_t) * n_users * cap1), o_ub = ws.take(sizeof(float) * n_users * cap1);
   size_t o_ovf = ws.take(sizeof(int32_t) * n_users), o_ovfc = ws.take(sizeof(int));
-  size_t o_work = ws.take(sizeof(uint32_t) * n_users * cap), o_workc = ws.take(sizeof(int));
-  size_t o_sc = ws.take(sizeof(double) * n_users * cap), o_tauf = ws.take(sizeof(float) * n_users);
+  size_t o_work = ws.take(sizeof(uint32_t) * n_users * cap1), o_workc = ws.take(sizeof(int));
+  size_t o_sc = ws.take(sizeof(double) * n_users * cap1), o_tauf = ws.take(sizeof(float) * n_users);
+  // tensor-core walk buffers: BF16 user rows grouped by cluster (each
+  // cluster padded to whole 128-row tiles), per-cluster BF16 item copies in
+  // bound order, two work lists, two-list select state
+  const int fp = idx->fp;
+  const int n_it = (int)((nI + 255) / 256);
+  const int blk = idx->opt.block_items > 0 ? idx->opt.block_items : 4096;
+  const int t1 = (int)((blk + 255) / 256) < n_it ? (int)((blk + 255) / 256) : n_it;
+  const int64_t n_rows_max = round_up(n_users, 128) + 128ll * C;
+  const int64_t max_work = n_rows_max / 128;
+  const int64_t n_pad = round_up(nI, 256);
+  const int cap2 = K <= kRegTopK ? 2 * K + 64 : 4 * K + 64;
+  const int64_t nl = n_users * 2;
+  size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
+         o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
+         o_topl = 0, o_work2 = 0, o_sc2 = 0;
+  if (use_tc) {
+    o_u16 = ws.take(sizeof(uint16_t) * n_users * fp);
+    o_uaux = ws.take(sizeof(float2) * n_users);
+    o_rowu = ws.take(sizeof(int32_t) * n_rows_max);
+    o_urow = ws.take(sizeof(int32_t) * n_users);
+    o_padoff = ws.take(sizeof(int) * (C + 1));
+    o_arows = ws.take(sizeof(uint16_t) * n_rows_max * fp);
+    o_brows = ws.take(sizeof(uint16_t) * C * n_pad * fp);
+    o_auxc = ws.take(sizeof(float2) * C * n_pad);
+    o_posc = ws.take(sizeof(int32_t) * C * n_pad);
+    o_w1 = ws.take(sizeof(int) * 4 * max_work);
+    o_w2 = ws.take(sizeof(int) * 4 * max_work);
+    o_nw = ws.take(16);
+    o_wend = ws.take(sizeof(int) * max_work);
+    o_tau2 = ws.take(sizeof(float) * nl);
+    o_n2 = ws.take(sizeof(int) * nl);
+    o_pos2 = ws.take(sizeof(int32_t) * nl * cap2);
+    o_ub2 = ws.take(sizeof(float) * nl * cap2);
+    o_topl = ws.take(sizeof(float) * nl * K);
+    o_work2 = ws.take(sizeof(uint32_t) * nl * cap2);
+    o_sc2 = ws.take(sizeof(double) * nl * cap2);
+  }
   MIPS_CUDA(ws.ensure(ws.used, s));
 
   // k-means initial centroids: a seeded draw of C distinct users
@@ -320,18 +368,62 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
                           ws.at<uint32_t>(o_uk2), ws.at<int32_t>(o_ui2), ws.at<uint32_t>(o_tmp), ws.at<int>(o_ccnt),
                           ws.at<int>(o_off), ws.at<int>(o_toff), &user_perm, s, &idx->launches));
   if ((st = end_stage(idx, ST_SORT, s)) != MIPS_OK) return st;
-  SelectOut so{ws.at<float>(o_tau), ws.at<int>(o_n), ws.at<int32_t>(o_pos), ws.at<float>(o_ub), cap, 1, nullptr, 0,
-               ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc), ws.at<uint32_t>(o_work), ws.at<int>(o_workc),
-               ws.at<double>(o_sc), ws.at<float>(o_tauf)};
-  MIPS_CUDA(maximus_walk(users, f, idx->items, idx->item_nrm, nI, vals, ws.at<float>(o_bounds), user_perm,
-                         ws.at<int>(o_off), ws.at<int>(o_toff), C, K, so, ws.at<int32_t>(o_vis), ws.at<int>(o_wc),
-                         idx->stats_dev, idx->err_dev, idx->num_sms, s));
-  idx->launches += 1;
-  if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
-  MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
-                           idx->stats_dev, idx->err_dev, s));
-  idx->launches += 4;
-  if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
+  if (!use_tc) {
+    // FP32 walk on CUDA cores, one candidate list per user
+    SelectOut so{ws.at<float>(o_tau), ws.at<int>(o_n), ws.at<int32_t>(o_pos), ws.at<float>(o_ub), cap, 1, nullptr, 0,
+                 ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc), ws.at<uint32_t>(o_work), ws.at<int>(o_workc),
+                 ws.at<double>(o_sc), ws.at<float>(o_tauf)};
+    MIPS_CUDA(maximus_walk(users, f, idx->items, idx->item_nrm, nI, vals, ws.at<float>(o_bounds), user_perm,
+                           ws.at<int>(o_off), ws.at<int>(o_toff), C, K, so, ws.at<int32_t>(o_vis), ws.at<int>(o_wc),
+                           idx->stats_dev, idx->err_dev, idx->num_sms, s));
+    idx->launches += 1;
+    if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
+    MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
+                             idx->stats_dev, idx->err_dev, s));
+    idx->launches += 4;
+  } else {
+    // tensor-core walk: cluster-ordered BF16 user rows, per-cluster BF16
+    // item copies in bound order; pass 1 = the first block of every list
+    // (the paper's item blocking), pass 2 = the rest each user tile needs
+    int* w1 = ws.at<int>(o_w1);
+    int* w2 = ws.at<int>(o_w2);
+    int* nw = ws.at<int>(o_nw);
+    launch_quant_bf16(users, n_users, f, fp, 0, ws.at<void>(o_u16), n_users, ws.at<float2>(o_uaux), idx->err_dev, s);
+    idx->launches += 1;
+    MIPS_CUDA(mx_tc_prepare(ws.at<int>(o_ccnt), C, user_perm, n_users, ws.at<int>(o_off), ws.at<int>(o_padoff),
+                            ws.at<int32_t>(o_rowu), n_rows_max, ws.at<int32_t>(o_urow), ws.at<void>(o_u16), fp,
+                            ws.at<void>(o_arows), idx->items_bf16, idx->item_aux, vals, nI, n_pad,
+                            ws.at<void>(o_brows), ws.at<float2>(o_auxc), ws.at<int32_t>(o_posc), t1, w1,
+                            w1 + max_work, w1 + 2 * max_work, w1 + 3 * max_work, nw, s, &idx->launches));
+    if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
+    CUtensorMap map_a, map_b;
+    if (!tc_make_map(&map_a, ws.at<void>(o_arows), n_rows_max, fp, p.row_bytes, tc_users_per_tile()) ||
+        !tc_make_map(&map_b, ws.at<void>(o_brows), C * n_pad, fp, p.row_bytes, tc_items_per_tile()))
+      return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Maximus operands");
+    SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
+                 ws.at<float>(o_topl), K <= kRegTopK ? 1 : 0, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
+                 ws.at<uint32_t>(o_work2), ws.at<int>(o_workc), ws.at<double>(o_sc2), ws.at<float>(o_tauf)};
+    p.n_users = n_users;
+    p.mode = 1;
+    p.work = TcWork{w1, w1 + max_work, w1 + 2 * max_work, w1 + 3 * max_work, nw, ws.at<int32_t>(o_rowu),
+                    ws.at<int32_t>(o_posc)};
+    const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), ws.at<float2>(o_auxc),
+                                     idx->stats_dev, idx->err_dev, grid, s));
+    MIPS_CUDA(mx_tc_pass2(ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), n_users, ws.at<float>(o_bounds), nI, t1, so,
+                          K, ws.at<int32_t>(o_urow), ws.at<int>(o_wend), max_work, nw, w1, w1 + max_work, w2,
+                          w2 + max_work, w2 + 2 * max_work, w2 + 3 * max_work, nw + 1, ws.at<int32_t>(o_vis),
+                          idx->stats_dev, s, &idx->launches));
+    p.work = TcWork{w2, w2 + max_work, w2 + 2 * max_work, w2 + 3 * max_work, nw + 1, ws.at<int32_t>(o_rowu),
+                    ws.at<int32_t>(o_posc)};
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), ws.at<float2>(o_auxc),
+                                     idx->stats_dev, idx->err_dev, grid, s));
+    idx->launches += 2;
+    if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
+    MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
+                             idx->stats_dev, idx->err_dev, s));
+    idx->launches += 4;
+  }
   idx->mx.assign = ws.at<int32_t>(o_assign);
   idx->mx.cent = ws.at<float>(o_cent);
   idx->mx.cosb = ws.at<float>(o_cosbf);
@@ -343,7 +435,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   idx->mx.C = C;
   idx->last_users = n_users;
   idx->last_clusters = C;
-  idx->last_dtype = MIPS_FP32;
+  idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
   return MIPS_OK;
 }
 

@@ -298,10 +298,10 @@ __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) 
 // over a user tile's first item tile, whose lower bounds are already in the
 // top-K) only the emission is done, so no item is counted twice.
 template <int KR>
-__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int32_t pos, const float2* aux_tile,
-                                         bool emit_only) {
+__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int col, const float2* aux_tile,
+                                         const int32_t* pos_tile, bool emit_only) {
   if (H < s.tau_eff) return;  // the threshold rose since the hit was queued
-  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux_tile[pos & (kHalfN - 1)]);
+  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux_tile[col]);
   if (L > s.tau_eff) {
     s.tau = topk_insert(s, c, L);
     if (s.tau > s.tau_eff) {
@@ -311,7 +311,7 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
   }
   if (H >= s.tau_eff) {
     if (s.n_cand < c.cap) {
-      c.cand_pos[s.n_cand] = pos;
+      c.cand_pos[s.n_cand] = pos_tile[col];
       c.cand_ub[s.n_cand] = H;
     }
     ++s.n_cand;
@@ -323,8 +323,9 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
 // the warp has a hit): this thread's hits are queued in shared memory, then
 // drained in order through one offer site.
 template <int KR>
-__device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const uint32_t* r, int32_t pos0, int valid,
-                                         const float2* aux_tile, unsigned long long& slow, bool emit_only) {
+__device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const uint32_t* r, int col0, int valid,
+                                         const float2* aux_tile, const int32_t* pos_tile, unsigned long long& slow,
+                                         bool emit_only) {
   const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
   const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
   const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
@@ -347,7 +348,7 @@ __device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const ui
             const float v = __uint_as_float(r[q]);
             if (v >= t && q < valid) {
               c.qh[n * kEpiThreads] = v;
-              c.qp[n * kEpiThreads] = pos0 + q;
+              c.qp[n * kEpiThreads] = col0 + q;
               ++n;
             }
           }
@@ -355,20 +356,23 @@ __device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const ui
       }
     }
     // one offer site for the queued hits (keeps the code small)
-    for (int t = 0; t < n; ++t) tc_offer(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, emit_only);
+    for (int t = 0; t < n; ++t)
+      tc_offer(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, pos_tile, emit_only);
   }
 }
 
 template <int KR>
-__device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t (&r)[64], int32_t pos0, int valid,
-                                         const float2* aux_tile, unsigned long long& slow, bool emit_only) {
+__device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t (&r)[64], int col0, int valid,
+                                         const float2* aux_tile, const int32_t* pos_tile, unsigned long long& slow,
+                                         bool emit_only) {
   if (valid < 64) {
 #pragma unroll
     for (int q = 0; q < 64; ++q)
       if (q >= valid) r[q] = 0xff800000u;  // -inf
   }
 #pragma unroll
-  for (int g = 0; g < 4; ++g) select16(s, c, r + 16 * g, pos0 + 16 * g, valid - 16 * g, aux_tile, slow, emit_only);
+  for (int g = 0; g < 4; ++g)
+    select16(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos_tile, slow, emit_only);
 }
 
 // First pass over a user tile's first item tile: every score's lower bound
@@ -400,6 +404,28 @@ __device__ __forceinline__ void seed64(TcUser<KR>& s, const TcSel& c, const uint
   }
 }
 
+struct WorkItem {
+  int a_row;   // first A row of the user tile
+  int b_row;   // B row of list rank 0
+  int tb, te;  // item tiles [tb, te)
+};
+
+__device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it) {
+  WorkItem w;
+  if (p.mode == 0) {
+    w.a_row = wi * kTileM;
+    w.b_row = 0;
+    w.tb = 0;
+    w.te = n_it;
+  } else {
+    w.a_row = p.work.a_row[wi];
+    w.b_row = p.work.b_row[wi];
+    w.tb = p.work.t_begin[wi];
+    w.te = p.work.t_end[wi];
+  }
+  return w;
+}
+
 struct Smem {
   uint64_t b_full[kMaxStages];
   uint64_t b_empty[kMaxStages];
@@ -424,7 +450,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   unsigned char* b_tiles = a_tiles + (size_t)p.kc * a_chunk;                  // [S][KC][b_chunk]
   float* heap_base = (float*)(b_tiles + (size_t)p.stages * p.kc * b_chunk);   // [K][256] (KR = 0)
   float2* aux_base = (float2*)(heap_base + (KR > 0 ? 0 : (size_t)p.K * kEpiThreads));  // [8 warps][128]
-  float* qh_base = (float*)(aux_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
+  int32_t* posb_base = (int32_t*)(aux_base + (size_t)kEpiWarps * kHalfN);      // [8 warps][128]
+  float* qh_base = (float*)(posb_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
   int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
   unsigned long long* tau_sh = (unsigned long long*)(qp_base + (size_t)kQueue * kEpiThreads);  // [256]
   int* seed_sh = (int*)(tau_sh + kEpiThreads);                                                // [2][256]
@@ -433,8 +460,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ctl->abort_flag;
-  const int n_ut = (int)((p.n_users + kTileM - 1) / kTileM);
   const int n_it = (int)((p.n_items + kTileN - 1) / kTileN);
+  const int n_work = p.mode == 0 ? (int)((p.n_users + kTileM - 1) / kTileM) : *p.work.n_work;
   constexpr uint32_t kTmemCols = 2 * kTileN;  // two accumulators
 
   if (threadIdx.x == 0) {
@@ -479,19 +506,21 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       int lt = 0;
       bool ok = true;
       const uint32_t b_bytes = p.kc * b_chunk;
-      for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
+      for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+        const WorkItem wk = get_work(p, wi, n_it);
         if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
         if (!ok) break;
         mbar_expect_tx(&ctl->a_full, p.kc * a_chunk);
         for (int c = 0; c < p.kc; ++c)
-          tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, ut * kTileM, &ctl->a_full);
-        for (int j = 0; j < n_it; ++j, ++g) {
+          tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full);
+        for (int j = wk.tb; j < wk.te; ++j, ++g) {
           if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
           if (!ok) break;
           mbar_expect_tx(&ctl->b_full[st], b_bytes);
           unsigned char* dst = b_tiles + (size_t)st * b_bytes;
           for (int c = 0; c < p.kc; ++c)
-            tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, j * kTileN, &ctl->b_full[st]);
+            tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, wk.b_row + j * kTileN,
+                        &ctl->b_full[st]);
           if (++st == p.stages) {
             st = 0;
             ph ^= 1u;
@@ -529,11 +558,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       uint32_t aph = 0;  // accumulator pass parity
       int lt = 0;
       bool ok = true;
-      for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
+      for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+        const WorkItem wk = get_work(p, wi, n_it);
         ok = mbar_wait(&ctl->a_full, lt & 1, abort_flag, err);
         if (!ok) break;
         tc_fence_after();
-        for (int j = 0; j < n_it; ++j, ++g) {
+        for (int j = wk.tb; j < wk.te; ++j, ++g) {
           ok = mbar_wait(&ctl->b_full[st], ph, abort_flag, err);
           if (ok && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, abort_flag, err);
           if (!ok) break;
@@ -586,20 +616,35 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     long long g = 0;
     bool ok = true;
     unsigned long long emitted = 0, slow = 0;
-    // this warp's copy of the bound columns of its 128 items of the current
-    // tile, prefetched one tile ahead into registers (4 entries per lane)
+    // this warp's copy of the bound columns and item positions of its 128
+    // items of the current tile, prefetched one tile ahead into registers
+    // (4 entries per lane); the tile after the last of a work item is the
+    // first of the CTA's next work item
     float2* aux_tile = aux_base + (size_t)e * kHalfN;
+    int32_t* pos_tile = posb_base + (size_t)e * kHalfN;
     float2 pre[4];
+    int32_t prep[4];
+    auto prefetch = [&](int64_t brow0) {  // B row of this warp's first column
 #pragma unroll
-    for (int t = 0; t < 4; ++t) pre[t] = item_aux[c2 * kHalfN + lane * 4 + t];
-    int lt = 0;  // user tiles done by this CTA
-    for (int ut = blockIdx.x; ut < n_ut && ok; ut += gridDim.x, ++lt) {
-      const int64_t u = (int64_t)ut * kTileM + row;
-      const bool active = u < p.n_users;
+      for (int t = 0; t < 4; ++t) {
+        const int64_t br = brow0 + lane * 4 + t;
+        pre[t] = item_aux[br];
+        prep[t] = p.mode == 0 ? (int32_t)br : p.work.item_pos[br];
+      }
+    };
+    if (blockIdx.x < n_work) {
+      const WorkItem w0 = get_work(p, blockIdx.x, n_it);
+      prefetch((int64_t)w0.b_row + (int64_t)w0.tb * kTileN + c2 * kHalfN);
+    }
+    int lt = 0;  // work items done by this CTA
+    for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+      const WorkItem wk = get_work(p, wi, n_it);
+      const int64_t u = p.mode == 0 ? (int64_t)wk.a_row + row : (int64_t)p.work.row_user[wk.a_row + row];
+      const bool active = u >= 0 && u < p.n_users;
       s.tau = active ? kNegInf : __int_as_float(0x7f800000);  // inactive: never a hit
       s.tau_eff = s.tau;
       s.n_cand = 0;
-      s.ut = ut;
+      s.ut = wi;
       s.beta_u = 0.f;
       s.nhat_u = 0.f;
       const int64_t list = (active ? u : 0) * 2 + c2;
@@ -610,32 +655,53 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const float2 ua = user_aux[u];
         s.beta_u = ua.x;
         s.nhat_u = ua.y;
+        if (wk.tb > 0) {  // continue a walk: restore the select state
+          s.n_cand = o.n_cand[list];
+          const float* src = o.topl + list * (int64_t)p.K;
+          if constexpr (KR > 0) {
+#pragma unroll
+            for (int i = 0; i < KR; ++i) s.d[i] = i < p.K ? src[i] : kNegInf;
+            s.tau = s.d[0];
+#pragma unroll
+            for (int i = 0; i < KR; ++i) s.tau = (i < p.K) ? s.d[i] : s.tau;
+          } else {
+            for (int i = 0; i < p.K; ++i) c.heap[i * kEpiThreads] = src[i];
+            s.tau = c.heap[0];
+          }
+          s.tau_eff = fmaxf(s.tau, o.tau[list]);
+          tc_publish(s, c);
+        }
       }
-      for (int j = 0; j < n_it; ++j, ++g) {
+      for (int j = wk.tb; j < wk.te; ++j, ++g) {
         const int b = (int)(g & 1);
         ok = mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), abort_flag, err);
         // lanes leave together: the tcgen05.ld below needs the whole warp
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) break;
         tc_fence_after();
-        __syncwarp();  // the previous tile's offers are done with aux_tile
+        __syncwarp();  // the previous tile's offers are done with aux_tile / pos_tile
 #pragma unroll
-        for (int t = 0; t < 4; ++t) aux_tile[lane * 4 + t] = pre[t];
-        __syncwarp();
-        {
-          const int jn = (j + 1 < n_it) ? j + 1 : 0;  // next tile (wraps to the next user tile)
-#pragma unroll
-          for (int t = 0; t < 4; ++t) pre[t] = item_aux[(int64_t)jn * kTileN + c2 * kHalfN + lane * 4 + t];
+        for (int t = 0; t < 4; ++t) {
+          aux_tile[lane * 4 + t] = pre[t];
+          pos_tile[lane * 4 + t] = prep[t];
         }
-        {  // the partner's threshold, if it is for this user tile
+        __syncwarp();
+        if (j + 1 < wk.te) {
+          prefetch((int64_t)wk.b_row + (int64_t)(j + 1) * kTileN + c2 * kHalfN);
+        } else if (wi + (int)gridDim.x < n_work) {
+          const WorkItem wn = get_work(p, wi + gridDim.x, n_it);
+          prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
+        }
+        {  // the partner's threshold, if it is for this work item
           const unsigned long long pt = *c.tau_partner;
-          if ((int)(pt >> 32) == ut) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
+          if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
         }
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
-        const int32_t pos0 = j * kTileN + c2 * kHalfN;
-        const int valid = (int)min((int64_t)kHalfN, p.n_items - (int64_t)pos0);
+        const int64_t rank0 = (int64_t)j * kTileN + c2 * kHalfN;  // list rank of this thread's first column
+        const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         uint32_t r[64];
-        if (j == 0) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
+        const bool first = j == 0;
+        if (first) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
           // (inactive lanes hold tau = +inf and insert nothing)
           tmem_ld64(taddr, r);
           seed64(s, c, r, 0, valid, aux_tile);
@@ -644,14 +710,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if (active) {
             s.tau_eff = s.tau;
             tc_publish(s, c);
-            if constexpr (KR > 0) seed_merge(s, c, ut, lt & 1);
+            if constexpr (KR > 0) seed_merge(s, c, wi, lt & 1);
           }
         }
-        const bool emit_only = j == 0;
         tmem_ld64(taddr, r);
-        select64(s, c, r, pos0, valid, aux_tile, slow, emit_only);
+        select64(s, c, r, 0, valid, aux_tile, pos_tile, slow, first);
         tmem_ld64(taddr + 64, r);
-        select64(s, c, r, pos0 + 64, valid - 64, aux_tile, slow, emit_only);
+        select64(s, c, r, 64, valid - 64, aux_tile, pos_tile, slow, first);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->acc_empty[b]);
@@ -693,7 +758,7 @@ size_t tc_smem_bytes(const TcParams& p) {
   const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = (size_t)kTileN * p.row_bytes;
   const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
   return 1024 + (size_t)p.kc * a_chunk + (size_t)p.stages * p.kc * b_chunk + heap +
-         sizeof(float2) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
+         (sizeof(float2) + sizeof(int32_t)) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
          (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
 }

@@ -9,6 +9,22 @@ namespace mips {
 constexpr int kMaxStages = 8;
 constexpr int kRegTopK = 16;  // K up to this keeps its top-K in registers
 
+// Work list for the kernel's second mode (Maximus walk): work item w scores
+// the 128 users at A rows [a_row[w], a_row[w] + 128) against the item tiles
+// t in [t_begin[w], t_end[w]) of the list whose rank 0 is B row b_row[w].
+// Without a work list (mode 0, the blocked multiply) work item w is user tile
+// w against every item tile, and A and B rows are user ids and item
+// positions themselves.
+struct TcWork {
+  const int* a_row;
+  const int* b_row;
+  const int* t_begin;
+  const int* t_end;
+  const int* n_work;        // device count of work items
+  const int32_t* row_user;  // A row -> user id, -1 for padding rows
+  const int32_t* item_pos;  // B row -> item position
+};
+
 struct TcParams {
   int64_t n_users, n_items;
   int f, fp, K;
@@ -17,7 +33,9 @@ struct TcParams {
   int row_elems;  // BF16 elements of one chunk row
   int swizzle;    // tcgen05 descriptor layout code: 6 = 32B, 4 = 64B, 2 = 128B
   int stages;     // item-tile ring depth
-  float g;        // accumulation-error factor used by prep.cu for this fp
+  float g;
+  int mode;       // 0: blocked multiply, 1: work list
+  TcWork work;        // accumulation-error factor used by prep.cu for this fp
 };
 
 // Operand row length (BF16 elements) for dimension f: f + 2 bound columns,

@@ -31,8 +31,9 @@ def clustered(n_users, n_items, f, seed, n_dirs=16, noise=0.2, item_norm=(0.0, 0
     return U, I
 
 
-def run_maximus(U, I, K, C, dtype="fp32", iters=3, seed=0):
-    index = mips.build_index(torch.from_numpy(I).cuda(), clusters=C, dtype=dtype, kmeans_iters=iters, seed=seed)
+def run_maximus(U, I, K, C, dtype="fp32", iters=3, seed=0, block_items=0):
+    index = mips.build_index(torch.from_numpy(I).cuda(), clusters=C, dtype=dtype, kmeans_iters=iters, seed=seed,
+                             block_items=block_items)
     idx, sc = mips.topk_maximus(index, torch.from_numpy(U).cuda(), K)
     mips.sync(index)
     st = mips.get_stats(index)
@@ -53,10 +54,14 @@ def run_maximus(U, I, K, C, dtype="fp32", iters=3, seed=0):
     return idx.cpu().numpy(), sc.cpu().numpy(), st, bufs, bmm_idx.cpu().numpy(), bmm_sc.cpu().numpy()
 
 
+@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 0), ("bf16", 256)])
 @pytest.mark.parametrize("C,K", [(8, 10), (16, 1), (4, 50)])
-def test_maximus_exact_and_bounds(C, K):
+def test_maximus_exact_and_bounds(C, K, dtype, block):
+    """bf16 runs the tensor-core walk: pass 1 over the first block of every
+    list (4096 items, or one 256-item tile), pass 2 over the rest."""
     U, I = clustered(3000, 2000, 16, seed=C + K)
-    idx, sc, st, b, bidx, bsc = run_maximus(U, I, K, C)
+    idx, sc, st, b, bidx, bsc = run_maximus(U, I, K, C, dtype=dtype, block_items=block)
+    assert st["dtype"] == (1 if dtype == "bf16" else 0)
     ref = oracle.topk(U, I, K)
     check_against_oracle(U, I, K, idx, sc, ref=ref)
     assert (idx == bidx).all() and (sc == bsc).all()
@@ -89,9 +94,10 @@ def test_maximus_exact_and_bounds(C, K):
     assert st["pairs_scored"] == b["visited"].sum()
 
 
-def test_maximus_prunes_on_clustered_users():
+@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 512)])
+def test_maximus_prunes_on_clustered_users(dtype, block):
     U, I = clustered(4000, 6000, 12, seed=11, n_dirs=8, noise=0.1)
-    idx, sc, st, b, _, _ = run_maximus(U, I, 5, 8)
+    idx, sc, st, b, _, _ = run_maximus(U, I, 5, 8, dtype=dtype, block_items=block)
     check_against_oracle(U, I, 5, idx, sc)
     assert b["visited"].mean() < 0.5 * I.shape[0]
 
