@@ -315,7 +315,10 @@ def main():
         return
 
     peaks, peak_src = load_peaks()
-    flops = 2.0 * f * nU * nI
+    # algorithmic work of the scoring kernel: every (user, item) pair it
+    # scores; the Maximus walk scores only the pairs its bounds leave
+    walked = args.method == "maximus" or (args.method == "select" and stats["ms_walk"] > 0 and not stats["ms_score"])
+    flops = 2.0 * f * (stats["pairs_scored"] if walked else nU * nI)
     kms = statistics.mean(score_ms)
     if dtype == "bf16":
         bound, peak, unit = "tensor", peaks["bf16_tflops"], "TFLOP/s"

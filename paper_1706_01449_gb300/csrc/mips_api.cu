@@ -424,6 +424,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
                              idx->stats_dev, idx->err_dev, s));
     idx->launches += 4;
   }
+  if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
   idx->mx.assign = ws.at<int32_t>(o_assign);
   idx->mx.cent = ws.at<float>(o_cent);
   idx->mx.cosb = ws.at<float>(o_cosbf);

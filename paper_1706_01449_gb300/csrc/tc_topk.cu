@@ -296,10 +296,12 @@ __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) 
 // then the candidate emission.  Lower bounds at or below the current filter
 // threshold cannot raise it and are not kept.  With emit_only (second pass
 // over a user tile's first item tile, whose lower bounds are already in the
-// top-K) only the emission is done, so no item is counted twice.
-template <int KR>
+// top-K) only the emission is done, so no item is counted twice.  The
+// item's position is pos0 + col, or pos_tile[col] for a walk of a
+// cluster's sorted list (MX).
+template <int KR, bool MX>
 __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int col, const float2* aux_tile,
-                                         const int32_t* pos_tile, bool emit_only) {
+                                         int32_t pos0, const int32_t* pos_tile, bool emit_only) {
   if (H < s.tau_eff) return;  // the threshold rose since the hit was queued
   const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux_tile[col]);
   if (L > s.tau_eff) {
@@ -311,7 +313,7 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
   }
   if (H >= s.tau_eff) {
     if (s.n_cand < c.cap) {
-      c.cand_pos[s.n_cand] = pos_tile[col];
+      c.cand_pos[s.n_cand] = MX ? pos_tile[col] : pos0 + col;
       c.cand_ub[s.n_cand] = H;
     }
     ++s.n_cand;
@@ -322,10 +324,10 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
 // Fast path: one maximum over the 16 and a compare.  Slow path (any lane of
 // the warp has a hit): this thread's hits are queued in shared memory, then
 // drained in order through one offer site.
-template <int KR>
+template <int KR, bool MX>
 __device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const uint32_t* r, int col0, int valid,
-                                         const float2* aux_tile, const int32_t* pos_tile, unsigned long long& slow,
-                                         bool emit_only) {
+                                         const float2* aux_tile, int32_t pos0, const int32_t* pos_tile,
+                                         unsigned long long& slow, bool emit_only) {
   const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
   const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
   const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
@@ -357,14 +359,14 @@ __device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const ui
     }
     // one offer site for the queued hits (keeps the code small)
     for (int t = 0; t < n; ++t)
-      tc_offer(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, pos_tile, emit_only);
+      tc_offer<KR, MX>(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, pos0, pos_tile, emit_only);
   }
 }
 
-template <int KR>
+template <int KR, bool MX>
 __device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t (&r)[64], int col0, int valid,
-                                         const float2* aux_tile, const int32_t* pos_tile, unsigned long long& slow,
-                                         bool emit_only) {
+                                         const float2* aux_tile, int32_t pos0, const int32_t* pos_tile,
+                                         unsigned long long& slow, bool emit_only) {
   if (valid < 64) {
 #pragma unroll
     for (int q = 0; q < 64; ++q)
@@ -372,7 +374,7 @@ __device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t
   }
 #pragma unroll
   for (int g = 0; g < 4; ++g)
-    select16(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos_tile, slow, emit_only);
+    select16<KR, MX>(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos0, pos_tile, slow, emit_only);
 }
 
 // First pass over a user tile's first item tile: every score's lower bound
@@ -410,9 +412,10 @@ struct WorkItem {
   int tb, te;  // item tiles [tb, te)
 };
 
+template <bool MX>
 __device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it) {
   WorkItem w;
-  if (p.mode == 0) {
+  if constexpr (!MX) {
     w.a_row = wi * kTileM;
     w.b_row = 0;
     w.tb = 0;
@@ -436,7 +439,9 @@ struct Smem {
   int abort_flag;
 };
 
-template <int KR>
+// MX: work items from p.work (Maximus walk of per-cluster sorted lists);
+// otherwise every user tile against every item tile (blocked multiply).
+template <int KR, bool MX>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     tc_score_select_kernel(const __grid_constant__ CUtensorMap map_users, const __grid_constant__ CUtensorMap map_items,
                            TcParams p, SelectOut o, const float2* __restrict__ user_aux,
@@ -461,7 +466,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ctl->abort_flag;
   const int n_it = (int)((p.n_items + kTileN - 1) / kTileN);
-  const int n_work = p.mode == 0 ? (int)((p.n_users + kTileM - 1) / kTileM) : *p.work.n_work;
+  const int n_work = MX ? *p.work.n_work : (int)((p.n_users + kTileM - 1) / kTileM);
   constexpr uint32_t kTmemCols = 2 * kTileN;  // two accumulators
 
   if (threadIdx.x == 0) {
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       bool ok = true;
       const uint32_t b_bytes = p.kc * b_chunk;
       for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
-        const WorkItem wk = get_work(p, wi, n_it);
+        const WorkItem wk = get_work<MX>(p, wi, n_it);
         if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
         if (!ok) break;
         mbar_expect_tx(&ctl->a_full, p.kc * a_chunk);
@@ -559,7 +564,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       int lt = 0;
       bool ok = true;
       for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
-        const WorkItem wk = get_work(p, wi, n_it);
+        const WorkItem wk = get_work<MX>(p, wi, n_it);
         ok = mbar_wait(&ctl->a_full, lt & 1, abort_flag, err);
         if (!ok) break;
         tc_fence_after();
@@ -629,17 +634,17 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       for (int t = 0; t < 4; ++t) {
         const int64_t br = brow0 + lane * 4 + t;
         pre[t] = item_aux[br];
-        prep[t] = p.mode == 0 ? (int32_t)br : p.work.item_pos[br];
+        if constexpr (MX) prep[t] = p.work.item_pos[br];
       }
     };
     if (blockIdx.x < n_work) {
-      const WorkItem w0 = get_work(p, blockIdx.x, n_it);
+      const WorkItem w0 = get_work<MX>(p, blockIdx.x, n_it);
       prefetch((int64_t)w0.b_row + (int64_t)w0.tb * kTileN + c2 * kHalfN);
     }
     int lt = 0;  // work items done by this CTA
     for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
-      const WorkItem wk = get_work(p, wi, n_it);
-      const int64_t u = p.mode == 0 ? (int64_t)wk.a_row + row : (int64_t)p.work.row_user[wk.a_row + row];
+      const WorkItem wk = get_work<MX>(p, wi, n_it);
+      const int64_t u = MX ? (int64_t)p.work.row_user[wk.a_row + row] : (int64_t)wk.a_row + row;
       const bool active = u >= 0 && u < p.n_users;
       s.tau = active ? kNegInf : __int_as_float(0x7f800000);  // inactive: never a hit
       s.tau_eff = s.tau;
@@ -683,21 +688,25 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
           aux_tile[lane * 4 + t] = pre[t];
-          pos_tile[lane * 4 + t] = prep[t];
+          if constexpr (MX) pos_tile[lane * 4 + t] = prep[t];
         }
         __syncwarp();
-        if (j + 1 < wk.te) {
-          prefetch((int64_t)wk.b_row + (int64_t)(j + 1) * kTileN + c2 * kHalfN);
-        } else if (wi + (int)gridDim.x < n_work) {
-          const WorkItem wn = get_work(p, wi + gridDim.x, n_it);
-          prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
+        if constexpr (MX) {
+          if (j + 1 < wk.te) {
+            prefetch((int64_t)wk.b_row + (int64_t)(j + 1) * kTileN + c2 * kHalfN);
+          } else if (wi + (int)gridDim.x < n_work) {
+            const WorkItem wn = get_work<MX>(p, wi + gridDim.x, n_it);
+            prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
+          }
+        } else {  // next tile (wraps to the first of the next user tile)
+          prefetch((int64_t)((j + 1 < n_it) ? j + 1 : 0) * kTileN + c2 * kHalfN);
         }
         {  // the partner's threshold, if it is for this work item
           const unsigned long long pt = *c.tau_partner;
           if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
         }
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
-        const int64_t rank0 = (int64_t)j * kTileN + c2 * kHalfN;  // list rank of this thread's first column
+        const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         uint32_t r[64];
         const bool first = j == 0;
@@ -714,9 +723,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           }
         }
         tmem_ld64(taddr, r);
-        select64(s, c, r, 0, valid, aux_tile, pos_tile, slow, first);
+        select64<KR, MX>(s, c, r, 0, valid, aux_tile, rank0, pos_tile, slow, first);
         tmem_ld64(taddr + 64, r);
-        select64(s, c, r, 64, valid - 64, aux_tile, pos_tile, slow, first);
+        select64<KR, MX>(s, c, r, 64, valid - 64, aux_tile, rank0, pos_tile, slow, first);
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->acc_empty[b]);
@@ -766,6 +775,22 @@ size_t tc_smem_bytes(const TcParams& p) {
 int tc_users_per_tile() { return kTileM; }
 int tc_items_per_tile() { return kTileN; }
 
+namespace {
+
+template <int KR, bool MX>
+cudaError_t launch_variant(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p, SelectOut o,
+                           const float2* user_aux, const float2* item_aux, DevStats* stats, int* err, int grid,
+                           size_t smem, cudaStream_t s) {
+  cudaError_t e =
+      cudaFuncSetAttribute(tc_score_select_kernel<KR, MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tc_score_select_kernel<KR, MX><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux,
+                                                                 stats, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p,
                                    SelectOut o, const float2* user_aux, const float2* item_aux, DevStats* stats,
                                    int* err, int grid, cudaStream_t s) {
@@ -776,19 +801,12 @@ cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorM
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
-  cudaError_t e;
-  if (p.K <= kRegTopK) {
-    e = cudaFuncSetAttribute(tc_score_select_kernel<kRegTopK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_score_select_kernel<kRegTopK><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux,
-                                                                     stats, err);
-  } else {
-    e = cudaFuncSetAttribute(tc_score_select_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    tc_score_select_kernel<0><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux, stats,
-                                                              err);
-  }
-  return cudaGetLastError();
+  const bool mx = p.mode != 0;
+  if (p.K <= kRegTopK)
+    return mx ? launch_variant<kRegTopK, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
+              : launch_variant<kRegTopK, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s);
+  return mx ? launch_variant<0, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
+            : launch_variant<0, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s);
 }
 
 }  // namespace mips
