@@ -124,16 +124,43 @@ cudaError_t maximus_walk(const float* users, int f, const float* items, const fl
                          DevStats* stats, int* err, int num_sms, cudaStream_t s);
 cudaError_t maximus_keys_to_bounds(const uint32_t* keys, int64_t n, float* out, cudaStream_t s);
 // tensor-core walk: operand layouts and pass-1 work list / pass-2 work list
-cudaError_t mx_tc_prepare(const int* counts, int C, const int32_t* user_perm, int64_t n_users, const int* offsets,
-                          int* pad_off, int32_t* row_user, int64_t n_rows_max, int32_t* user_row, const void* users_bf16,
-                          int fp, void* a_rows, const void* items_bf16, const float2* item_aux, const int32_t* lists,
-                          int64_t n_items, int64_t n_pad, void* b_rows, float2* aux_c, int32_t* pos_c, int t1,
-                          int* a_row1, int* b_row1, int* tb1, int* te1, int* n_work1, cudaStream_t s, int* launches);
-cudaError_t mx_tc_pass2(const int32_t* assign, const float2* user_aux, int64_t n_users, const float* bounds,
-                        int64_t n_items, int t1, SelectOut o, int K, const int32_t* user_row, int* work_end,
-                        int64_t max_work, const int* n_work1, const int* a_row1, const int* b_row1, int* a_row2,
-                        int* b_row2, int* tb2, int* te2, int* n_work2, int32_t* visited, DevStats* stats, cudaStream_t s,
-                        int* launches);
+// Tensor-core Maximus walk: layout and buffers (device pointers into the
+// library's workspace).  A rows: users grouped by cluster, each cluster
+// starting at a 128-aligned row; B rows: each cluster's item list copied in
+// bound order, n_pad rows per cluster.
+struct MxTc {
+  int C = 0, fp = 0, t1 = 0, n_it = 0;
+  int64_t n_users = 0, n_items = 0, n_pad = 0, n_rows_max = 0, max_work = 0;
+  const int* counts = nullptr;       // [C] users per cluster
+  const int* offsets = nullptr;      // [C + 1] first sorted rank of each cluster
+  int* pad_off = nullptr;            // [C + 1] first A row of each cluster
+  int32_t* row_user = nullptr;       // [n_rows_max] user of each A row, -1 = padding
+  int32_t* user_row = nullptr;       // [n_users]
+  const void* users_bf16 = nullptr;  // [n_users][fp] in user order
+  void* a_rows = nullptr;            // [n_rows_max][fp]
+  void* b_rows = nullptr;            // [C * n_pad][fp]
+  float2* aux_c = nullptr;           // [C * n_pad] bound columns of the B rows
+  int32_t* pos_c = nullptr;          // [C * n_pad] item positions of the B rows
+  int* w1 = nullptr;                 // [4][max_work] a_row, b_row, t_begin, t_end (pass 1)
+  int* w2 = nullptr;                 // [4][max_work] (pass 2, longest first)
+  int* n_work = nullptr;             // [2] work items of pass 1, pass 2
+  int* work_end = nullptr;           // [max_work] item tiles each A tile walks
+  int32_t* ustop = nullptr;          // [n_users] item tiles each user needs
+  uint32_t* ukeys[2] = {};           // [n_users] user regroup sort
+  int32_t* uvals[2] = {};
+  uint32_t* wkeys[2] = {};           // [max_work] pass-2 work sort
+  int32_t* wvals[2] = {};
+  uint32_t* temp = nullptr;          // radix sort scratch for max(n_users, max_work) keys
+};
+// Whether the regroup sort key (cluster, item tiles) fits 32 bits.
+bool mx_tc_regroup_fits(int C, int64_t n_items);
+// A rows, B rows, pass-1 work list.
+cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_bf16, const float2* item_aux,
+                          const int32_t* lists, cudaStream_t s, int* launches);
+// After pass 1: each user's stop tile, users regrouped by it within their
+// cluster (new A rows, *user_perm), the pass-2 work list, visited counts.
+cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, const float* bounds, SelectOut o, int K,
+                        int32_t** user_perm, int32_t* visited, DevStats* stats, cudaStream_t s, int* launches);
 
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);

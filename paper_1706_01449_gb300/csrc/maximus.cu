@@ -516,14 +516,17 @@ __global__ void mx_work1_kernel(const int* __restrict__ pad_off, int C, int64_t 
   te[w] = t1;
 }
 
-// Stop rank of every user after pass 1: the first list rank r >= r1 with
-// max(nhat_u * bound(r), 0) < tau_u (rounded up), tau_u the K-th
-// largest of the union of its two sub-lists' lower bounds (or their
-// thresholds); the work item of the user's tile must walk ceil(r / 256)
-// item tiles.  Users with no such rank walk the whole list.
+// Item tiles every user needs after pass 1: ceil(r / 256) for the first list
+// rank r >= r1 with max(nhat_u * bound(r), 0) < tau_u (rounded up), tau_u
+// the K-th largest of the union of its two sub-lists' lower bounds (or
+// their thresholds).  The list being sorted, no later item can reach tau_u
+// either.  Users with no such rank need the whole list.  The sort key puts
+// the users of a cluster in order of that need:
+//   key = cluster << tile_bits | tiles.
 __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux, int64_t n_users,
                                const float* __restrict__ bounds, int64_t n_items, int r1, SelectOut o, int K,
-                               const int32_t* __restrict__ user_row, int* __restrict__ work_end) {
+                               int tile_bits, int32_t* __restrict__ ustop, uint32_t* __restrict__ keys,
+                               int32_t* __restrict__ vals) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n_users) return;
   const int64_t l0 = u * 2;
@@ -540,7 +543,8 @@ __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2*
     tau = fmaxf(tau, v);
   }
   const float nu = user_aux[u].y;
-  const float* B = bounds + (int64_t)assign[u] * n_items;
+  const int j = assign[u];
+  const float* B = bounds + (int64_t)j * n_items;
   int64_t lo = r1 < n_items ? r1 : n_items, hi = n_items;  // first rank in [lo, hi) that stops; hi = none
   while (lo < hi) {
     const int64_t mid = (lo + hi) / 2;
@@ -550,27 +554,45 @@ __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2*
     else lo = mid + 1;
   }
   const int tiles = (int)((lo + 255) / 256);
-  atomicMax(&work_end[user_row[u] / kThreads], tiles);
+  ustop[u] = tiles;
+  keys[u] = ((uint32_t)j << tile_bits) | (uint32_t)tiles;
+  vals[u] = (int32_t)u;
 }
 
-// Pass-2 work list: the pass-1 items whose users need more item tiles.
-__global__ void mx_work2_kernel(const int* __restrict__ n_work1, const int* __restrict__ a_row1,
-                                const int* __restrict__ b_row1, const int* __restrict__ work_end, int t1,
-                                int* __restrict__ a_row2, int* __restrict__ b_row2, int* __restrict__ tb2,
-                                int* __restrict__ te2, int* __restrict__ n_work2, DevStats* stats) {
+// work_end[tile] = max item tiles over the users of the A tile.
+__global__ void mx_tile_end_kernel(const int32_t* __restrict__ ustop, const int32_t* __restrict__ user_row,
+                                   int64_t n_users, int* __restrict__ work_end) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_users) return;
+  atomicMax(&work_end[user_row[u] / kThreads], ustop[u]);
+}
+
+// Sort keys of the pass-2 work list: A tiles that need more than t1 item
+// tiles, longest first (key n_it - length); the rest sort last (key n_it).
+__global__ void mx_work2_keys_kernel(const int* __restrict__ n_work1, const int* __restrict__ work_end, int64_t max_work,
+                                     int t1, int n_it, uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
+                                     int* __restrict__ n_work2, DevStats* stats) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= *n_work1) return;
-  const int end = work_end[w];
-  unsigned long long tiles = (unsigned long long)t1;
-  if (end > t1) {
-    const int q = atomicAdd(n_work2, 1);
-    a_row2[q] = a_row1[w];
-    b_row2[q] = b_row1[w];
-    tb2[q] = t1;
-    te2[q] = end;
-    tiles = end;
-  }
-  atomicAdd(&stats->blocks_walked, tiles);
+  if (w >= max_work) return;
+  const bool real = w < *n_work1;
+  const int end = real ? work_end[w] : 0;
+  keys[w] = (uint32_t)(end > t1 ? n_it - (end - t1) : n_it);
+  vals[w] = w;
+  if (end > t1) atomicAdd(n_work2, 1);
+  if (real) atomicAdd(&stats->blocks_walked, (unsigned long long)(end > t1 ? end : t1));
+}
+
+__global__ void mx_work2_kernel(const int* __restrict__ n_work2, const int32_t* __restrict__ order,
+                                const int* __restrict__ a_row1, const int* __restrict__ b_row1,
+                                const int* __restrict__ work_end, int t1, int* __restrict__ a_row2,
+                                int* __restrict__ b_row2, int* __restrict__ tb2, int* __restrict__ te2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *n_work2) return;
+  const int w = order[q];
+  a_row2[q] = a_row1[w];
+  b_row2[q] = b_row1[w];
+  tb2[q] = t1;
+  te2[q] = work_end[w];
 }
 
 // Items each user scored: the tiles its work item walked.
@@ -585,45 +607,76 @@ __global__ void mx_visited_kernel(const int32_t* __restrict__ user_row, int64_t 
   atomicAdd(pairs, (unsigned long long)v);
 }
 
+int bits_for(int64_t x) {  // bits to hold 0..x
+  int b = 0;
+  while (b < 62 && (int64_t(1) << b) <= x) ++b;
+  return b;
+}
+
 }  // namespace
 
-cudaError_t mx_tc_prepare(const int* counts, int C, const int32_t* user_perm, int64_t n_users, const int* offsets,
-                          int* pad_off, int32_t* row_user, int64_t n_rows_max, int32_t* user_row, const void* users_bf16,
-                          int fp, void* a_rows, const void* items_bf16, const float2* item_aux, const int32_t* lists,
-                          int64_t n_items, int64_t n_pad, void* b_rows, float2* aux_c, int32_t* pos_c, int t1,
-                          int* a_row1, int* b_row1, int* tb1, int* te1, int* n_work1, cudaStream_t s, int* launches) {
-  const int words = fp * 2 / 16;
-  mx_pad_layout_kernel<<<1, 32, 0, s>>>(counts, C, pad_off);
-  cudaError_t e = cudaMemsetAsync(row_user, 0xff, sizeof(int32_t) * n_rows_max, s);
+bool mx_tc_regroup_fits(int C, int64_t n_items) {
+  return bits_for(C - 1) + bits_for((n_items + 255) / 256) <= 32;
+}
+
+cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_bf16, const float2* item_aux,
+                          const int32_t* lists, cudaStream_t s, int* launches) {
+  const int words = m.fp * 2 / 16;
+  mx_pad_layout_kernel<<<1, 32, 0, s>>>(m.counts, m.C, m.pad_off);
+  cudaError_t e = cudaMemsetAsync(m.row_user, 0xff, sizeof(int32_t) * m.n_rows_max, s);
   if (e != cudaSuccess) return e;
-  mx_row_map_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(user_perm, n_users, offsets, pad_off, C, row_user,
-                                                                      user_row);
-  mx_gather_bf16_kernel<<<(unsigned)((n_rows_max * words + 255) / 256), 256, 0, s>>>(
-      (const uint4*)users_bf16, row_user, n_rows_max, words, (uint4*)a_rows);
-  const int64_t tot = (int64_t)C * n_pad * words;
+  mx_row_map_kernel<<<(unsigned)((m.n_users + 255) / 256), 256, 0, s>>>(user_perm, m.n_users, m.offsets, m.pad_off, m.C,
+                                                                        m.row_user, m.user_row);
+  mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * words + 255) / 256), 256, 0, s>>>(
+      (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, words, (uint4*)m.a_rows);
+  const int64_t tot = (int64_t)m.C * m.n_pad * words;
   mx_items_by_cluster_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      (const uint4*)items_bf16, item_aux, lists, n_items, n_pad, C, words, (uint4*)b_rows, aux_c, pos_c);
-  const int max_work = (int)(n_rows_max / kThreads);
-  mx_work1_kernel<<<(max_work + 255) / 256, 256, 0, s>>>(pad_off, C, n_pad, t1, a_row1, b_row1, tb1, te1, n_work1);
+      (const uint4*)items_bf16, item_aux, lists, m.n_items, m.n_pad, m.C, words, (uint4*)m.b_rows, m.aux_c, m.pos_c);
+  const int64_t mw = m.max_work;
+  mx_work1_kernel<<<(unsigned)((mw + 255) / 256), 256, 0, s>>>(m.pad_off, m.C, m.n_pad, m.t1, m.w1, m.w1 + mw,
+                                                                m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work);
   *launches += 5;
   return cudaGetLastError();
 }
 
-cudaError_t mx_tc_pass2(const int32_t* assign, const float2* user_aux, int64_t n_users, const float* bounds,
-                        int64_t n_items, int t1, SelectOut o, int K, const int32_t* user_row, int* work_end,
-                        int64_t max_work, const int* n_work1, const int* a_row1, const int* b_row1, int* a_row2,
-                        int* b_row2, int* tb2, int* te2, int* n_work2, int32_t* visited, DevStats* stats, cudaStream_t s,
-                        int* launches) {
-  cudaError_t e = cudaMemsetAsync(work_end, 0, sizeof(int) * max_work, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(n_work2, 0, sizeof(int), s);
+cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, const float* bounds, SelectOut o, int K,
+                        int32_t** user_perm, int32_t* visited, DevStats* stats, cudaStream_t s, int* launches) {
+  const int64_t mw = m.max_work, nU = m.n_users;
+  const unsigned ub = (unsigned)((nU + 255) / 256), wb = (unsigned)((mw + 255) / 256);
+  const int tile_bits = bits_for(m.n_it);
+  const int key_bits = bits_for(m.C - 1) + tile_bits;
+  cudaError_t e = cudaMemsetAsync(m.work_end, 0, sizeof(int) * mw, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.n_work + 1, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  mx_stop_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, user_aux, n_users, bounds, n_items, t1 * 256,
-                                                                    o, K, user_row, work_end);
-  mx_work2_kernel<<<(unsigned)((max_work + 255) / 256), 256, 0, s>>>(n_work1, a_row1, b_row1, work_end, t1, a_row2,
-                                                                      b_row2, tb2, te2, n_work2, stats);
-  mx_visited_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(user_row, n_users, work_end, t1, n_items, visited,
-                                                                      &stats->pairs_scored);
-  *launches += 3;
+  mx_stop_kernel<<<ub, 256, 0, s>>>(assign, user_aux, nU, bounds, m.n_items, m.t1 * 256, o, K, tile_bits, m.ustop,
+                                    m.ukeys[0], m.uvals[0]);
+  *launches += 1;
+  // regroup: the users of each cluster in order of the item tiles they
+  // need, so that each A tile's walk is close to its users' own need
+  uint32_t* k0 = m.ukeys[0];
+  int32_t* v0 = m.uvals[0];
+  uint32_t* k1 = m.ukeys[1];
+  int32_t* v1 = m.uvals[1];
+  e = radix_sort_pairs(k0, v0, k1, v1, nU, 1, 0, key_bits, m.temp, s, launches);
+  if (e != cudaSuccess) return e;
+  *user_perm = v0;
+  mx_row_map_kernel<<<ub, 256, 0, s>>>(v0, nU, m.offsets, m.pad_off, m.C, m.row_user, m.user_row);
+  mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * (m.fp / 8) + 255) / 256), 256, 0, s>>>(
+      (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, m.fp / 8, (uint4*)m.a_rows);
+  mx_tile_end_kernel<<<ub, 256, 0, s>>>(m.ustop, m.user_row, nU, m.work_end);
+  mx_work2_keys_kernel<<<wb, 256, 0, s>>>(m.n_work, m.work_end, mw, m.t1, m.n_it, m.wkeys[0], m.wvals[0], m.n_work + 1,
+                                          stats);
+  *launches += 4;
+  uint32_t* wk0 = m.wkeys[0];
+  int32_t* wv0 = m.wvals[0];
+  uint32_t* wk1 = m.wkeys[1];
+  int32_t* wv1 = m.wvals[1];
+  e = radix_sort_pairs(wk0, wv0, wk1, wv1, mw, 1, 0, tile_bits, m.temp, s, launches);
+  if (e != cudaSuccess) return e;
+  mx_work2_kernel<<<wb, 256, 0, s>>>(m.n_work + 1, wv0, m.w1, m.w1 + mw, m.work_end, m.t1, m.w2, m.w2 + mw,
+                                     m.w2 + 2 * mw, m.w2 + 3 * mw);
+  mx_visited_kernel<<<ub, 256, 0, s>>>(m.user_row, nU, m.work_end, m.t1, m.n_items, visited, &stats->pairs_scored);
+  *launches += 2;
   return cudaGetLastError();
 }
 

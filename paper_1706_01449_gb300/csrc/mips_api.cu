@@ -280,7 +280,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   p.K = K;
   // (TMA row coordinates of the per-cluster item copies are 32-bit)
   const bool use_tc = idx->opt.dtype == MIPS_BF16 && (int64_t)C * round_up(nI, 256) < (int64_t)INT32_MAX &&
-                      round_up(n_users, 128) + 128ll * C < (int64_t)INT32_MAX && tc_plan(p, idx->max_smem);
+                      round_up(n_users, 128) + 128ll * C < (int64_t)INT32_MAX && mx_tc_regroup_fits(C, nI) &&
+                      tc_plan(p, idx->max_smem);
   Arena& ws = idx->ws;
   ws.reset();
   size_t o_ids = ws.take(sizeof(int64_t) * C), o_cent = ws.take(sizeof(float) * C * f), o_hn2 = ws.take(sizeof(float) * C);
@@ -289,9 +290,12 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_cosb = ws.take(sizeof(uint32_t) * C), o_cosbf = ws.take(sizeof(float) * C);
   size_t o_keys = ws.take(sizeof(uint32_t) * CI), o_vals = ws.take(sizeof(int32_t) * CI);
   size_t o_keys2 = ws.take(sizeof(uint32_t) * CI), o_vals2 = ws.take(sizeof(int32_t) * CI);
-  size_t o_tmp = ws.take(radix_sort_temp_bytes(nI, C) > radix_sort_temp_bytes(n_users, 1)
-                             ? radix_sort_temp_bytes(nI, C)
-                             : radix_sort_temp_bytes(n_users, 1));
+  const int64_t n_rows_max = round_up(n_users, 128) + 128ll * C;  // A rows of the tensor-core walk
+  const int64_t max_work = n_rows_max / 128;
+  size_t tmp_bytes = radix_sort_temp_bytes(nI, C);
+  if (radix_sort_temp_bytes(n_users, 1) > tmp_bytes) tmp_bytes = radix_sort_temp_bytes(n_users, 1);
+  if (radix_sort_temp_bytes(max_work, 1) > tmp_bytes) tmp_bytes = radix_sort_temp_bytes(max_work, 1);
+  size_t o_tmp = ws.take(tmp_bytes);
   size_t o_bounds = ws.take(sizeof(float) * CI);
   size_t o_uk = ws.take(sizeof(uint32_t) * n_users), o_ui = ws.take(sizeof(int32_t) * n_users);
   size_t o_uk2 = ws.take(sizeof(uint32_t) * n_users), o_ui2 = ws.take(sizeof(int32_t) * n_users);
@@ -310,14 +314,12 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int n_it = (int)((nI + 255) / 256);
   const int blk = idx->opt.block_items > 0 ? idx->opt.block_items : 4096;
   const int t1 = (int)((blk + 255) / 256) < n_it ? (int)((blk + 255) / 256) : n_it;
-  const int64_t n_rows_max = round_up(n_users, 128) + 128ll * C;
-  const int64_t max_work = n_rows_max / 128;
   const int64_t n_pad = round_up(nI, 256);
   const int cap2 = K <= kRegTopK ? 2 * K + 64 : 4 * K + 64;
   const int64_t nl = n_users * 2;
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
-         o_topl = 0, o_work2 = 0, o_sc2 = 0;
+         o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0;
   if (use_tc) {
     o_u16 = ws.take(sizeof(uint16_t) * n_users * fp);
     o_uaux = ws.take(sizeof(float2) * n_users);
@@ -339,6 +341,11 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     o_topl = ws.take(sizeof(float) * nl * K);
     o_work2 = ws.take(sizeof(uint32_t) * nl * cap2);
     o_sc2 = ws.take(sizeof(double) * nl * cap2);
+    o_ustop = ws.take(sizeof(int32_t) * n_users);
+    o_wk0 = ws.take(sizeof(uint32_t) * max_work);
+    o_wk1 = ws.take(sizeof(uint32_t) * max_work);
+    o_wv0 = ws.take(sizeof(int32_t) * max_work);
+    o_wv1 = ws.take(sizeof(int32_t) * max_work);
   }
   MIPS_CUDA(ws.ensure(ws.used, s));
 
@@ -385,39 +392,63 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     // tensor-core walk: cluster-ordered BF16 user rows, per-cluster BF16
     // item copies in bound order; pass 1 = the first block of every list
     // (the paper's item blocking), pass 2 = the rest each user tile needs
-    int* w1 = ws.at<int>(o_w1);
-    int* w2 = ws.at<int>(o_w2);
-    int* nw = ws.at<int>(o_nw);
+    MxTc m;
+    m.C = C;
+    m.fp = fp;
+    m.t1 = t1;
+    m.n_it = n_it;
+    m.n_users = n_users;
+    m.n_items = nI;
+    m.n_pad = n_pad;
+    m.n_rows_max = n_rows_max;
+    m.max_work = max_work;
+    m.counts = ws.at<int>(o_ccnt);
+    m.offsets = ws.at<int>(o_off);
+    m.pad_off = ws.at<int>(o_padoff);
+    m.row_user = ws.at<int32_t>(o_rowu);
+    m.user_row = ws.at<int32_t>(o_urow);
+    m.users_bf16 = ws.at<void>(o_u16);
+    m.a_rows = ws.at<void>(o_arows);
+    m.b_rows = ws.at<void>(o_brows);
+    m.aux_c = ws.at<float2>(o_auxc);
+    m.pos_c = ws.at<int32_t>(o_posc);
+    m.w1 = ws.at<int>(o_w1);
+    m.w2 = ws.at<int>(o_w2);
+    m.n_work = ws.at<int>(o_nw);
+    m.work_end = ws.at<int>(o_wend);
+    m.ustop = ws.at<int32_t>(o_ustop);
+    m.ukeys[0] = ws.at<uint32_t>(o_uk);  // the user-group sort is done with these
+    m.ukeys[1] = ws.at<uint32_t>(o_uk2);
+    m.uvals[0] = ws.at<int32_t>(o_ui);
+    m.uvals[1] = ws.at<int32_t>(o_ui2);
+    m.wkeys[0] = ws.at<uint32_t>(o_wk0);
+    m.wkeys[1] = ws.at<uint32_t>(o_wk1);
+    m.wvals[0] = ws.at<int32_t>(o_wv0);
+    m.wvals[1] = ws.at<int32_t>(o_wv1);
+    m.temp = ws.at<uint32_t>(o_tmp);
     launch_quant_bf16(users, n_users, f, fp, 0, ws.at<void>(o_u16), n_users, ws.at<float2>(o_uaux), idx->err_dev, s);
     idx->launches += 1;
-    MIPS_CUDA(mx_tc_prepare(ws.at<int>(o_ccnt), C, user_perm, n_users, ws.at<int>(o_off), ws.at<int>(o_padoff),
-                            ws.at<int32_t>(o_rowu), n_rows_max, ws.at<int32_t>(o_urow), ws.at<void>(o_u16), fp,
-                            ws.at<void>(o_arows), idx->items_bf16, idx->item_aux, vals, nI, n_pad,
-                            ws.at<void>(o_brows), ws.at<float2>(o_auxc), ws.at<int32_t>(o_posc), t1, w1,
-                            w1 + max_work, w1 + 2 * max_work, w1 + 3 * max_work, nw, s, &idx->launches));
+    MIPS_CUDA(mx_tc_prepare(m, user_perm, idx->items_bf16, idx->item_aux, vals, s, &idx->launches));
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
     CUtensorMap map_a, map_b;
-    if (!tc_make_map(&map_a, ws.at<void>(o_arows), n_rows_max, fp, p.row_bytes, tc_users_per_tile()) ||
-        !tc_make_map(&map_b, ws.at<void>(o_brows), C * n_pad, fp, p.row_bytes, tc_items_per_tile()))
+    if (!tc_make_map(&map_a, m.a_rows, n_rows_max, fp, p.row_bytes, tc_users_per_tile()) ||
+        !tc_make_map(&map_b, m.b_rows, C * n_pad, fp, p.row_bytes, tc_items_per_tile()))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Maximus operands");
     SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
                  ws.at<float>(o_topl), K <= kRegTopK ? 1 : 0, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
                  ws.at<uint32_t>(o_work2), ws.at<int>(o_workc), ws.at<double>(o_sc2), ws.at<float>(o_tauf)};
     p.n_users = n_users;
     p.mode = 1;
-    p.work = TcWork{w1, w1 + max_work, w1 + 2 * max_work, w1 + 3 * max_work, nw, ws.at<int32_t>(o_rowu),
-                    ws.at<int32_t>(o_posc)};
+    const int64_t mw = max_work;
+    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
-    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), ws.at<float2>(o_auxc),
-                                     idx->stats_dev, idx->err_dev, grid, s));
-    MIPS_CUDA(mx_tc_pass2(ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), n_users, ws.at<float>(o_bounds), nI, t1, so,
-                          K, ws.at<int32_t>(o_urow), ws.at<int>(o_wend), max_work, nw, w1, w1 + max_work, w2,
-                          w2 + max_work, w2 + 2 * max_work, w2 + 3 * max_work, nw + 1, ws.at<int32_t>(o_vis),
-                          idx->stats_dev, s, &idx->launches));
-    p.work = TcWork{w2, w2 + max_work, w2 + 2 * max_work, w2 + 3 * max_work, nw + 1, ws.at<int32_t>(o_rowu),
-                    ws.at<int32_t>(o_posc)};
-    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), ws.at<float2>(o_auxc),
-                                     idx->stats_dev, idx->err_dev, grid, s));
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), m.aux_c, idx->stats_dev,
+                                     idx->err_dev, grid, s));
+    MIPS_CUDA(mx_tc_pass2(m, ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), ws.at<float>(o_bounds), so, K,
+                          &user_perm, ws.at<int32_t>(o_vis), idx->stats_dev, s, &idx->launches));
+    p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c};
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), m.aux_c, idx->stats_dev,
+                                     idx->err_dev, grid, s));
     idx->launches += 2;
     if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
