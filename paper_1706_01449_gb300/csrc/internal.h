@@ -146,6 +146,10 @@ struct MxTc {
   int* n_work = nullptr;             // [2] work items of pass 1, pass 2
   int* work_end = nullptr;           // [max_work] item tiles each A tile walks
   int32_t* ustop = nullptr;          // [n_users] item tiles each user needs
+  int* cl_end = nullptr;             // [C] item tiles any member of the cluster needs
+  const void* items_bf16 = nullptr;  // set by mx_tc_prepare: the sources of the list copies
+  const float2* item_aux = nullptr;
+  const int32_t* lists = nullptr;
   uint32_t* ukeys[2] = {};           // [n_users] user regroup sort
   int32_t* uvals[2] = {};
   uint32_t* wkeys[2] = {};           // [max_work] pass-2 work sort
@@ -154,11 +158,12 @@ struct MxTc {
 };
 // Whether the regroup sort key (cluster, item tiles) fits 32 bits.
 bool mx_tc_regroup_fits(int C, int64_t n_items);
-// A rows, B rows, pass-1 work list.
+// A rows, the B rows pass 1 reads, pass-1 work list.
 cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_bf16, const float2* item_aux,
                           const int32_t* lists, cudaStream_t s, int* launches);
-// After pass 1: each user's stop tile, users regrouped by it within their
-// cluster (new A rows, *user_perm), the pass-2 work list, visited counts.
+// After pass 1: each user's stop tile, the B rows pass 2 reads, users
+// regrouped by stop tile within their cluster (new A rows, *user_perm), the
+// pass-2 work list, visited counts.
 cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, const float* bounds, SelectOut o, int K,
                         int32_t** user_perm, int32_t* visited, DevStats* stats, cudaStream_t s, int* launches);
 

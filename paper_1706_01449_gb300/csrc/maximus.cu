@@ -15,6 +15,7 @@
 //     x y + sqrt((1 - x)(1 + x)) sqrt((1 - y)(1 + y))   (= cos(theta_ic - theta_b)),
 //     g rounded up; g increases with x and decreases with y on x < y, so
 //     the outward inputs give an upper bound.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -182,23 +183,17 @@ __global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, in
 
 // CBound of every (cluster, item): key = float_desc_key(bound) (sorts
 // descending), value = item position.  [C][n_items], cluster-major.
-__global__ void cbound_kernel(const float* __restrict__ cent, int C, int f, const float* __restrict__ items,
-                              const float* __restrict__ item_nrm, int64_t n_items, const uint32_t* __restrict__ cosb_ord,
-                              uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)C * n_items) return;
-  const int j = (int)(t / n_items);
-  const int64_t i = t - (int64_t)j * n_items;
-  const float* cr = cent + (int64_t)j * f;
-  const float* ir = items + i * f;
-  float d = 0.f, sc = 0.f, si = 0.f;
-  for (int k = 0; k < f; ++k) {
-    d = __fmaf_rn(cr[k], ir[k], d);
-    sc = __fmaf_rn(cr[k], cr[k], sc);
-    si = __fmaf_rn(ir[k], ir[k], si);
-  }
-  const float ni = item_nrm[i];  // upper bound of ||i||
-  const float y = ord2f(cosb_ord[j]);
+// One block: 128 items (one per thread, staged in shared memory as
+// [f][129] to keep the banks apart) against a chunk of 32 centroids
+// ([f][32], read four at a time); every dot product, item norm and
+// centroid norm is summed sequentially over k with FMA.
+constexpr int kCbItems = 128, kCbChunk = 32;
+
+__host__ __device__ __forceinline__ size_t cb_items_floats(int f) {  // rounded to 4 floats (float4 reads after it)
+  return ((size_t)f * (kCbItems + 1) + 3) & ~(size_t)3;
+}
+
+__device__ __forceinline__ float cbound_value(float d, float sc, float si, float ni, float y, int f) {
   float g;
   if (si == 0.f) {
     g = 0.f;  // zero item: bound 0 = its score
@@ -216,10 +211,65 @@ __global__ void cbound_kernel(const float* __restrict__ cent, int C, int f, cons
     }
   }
   // bound = ||i|| g: ni is an upper bound of ||i||, and ||i|| >= ni (1 - (2f + 4) 2^-23)
-  const float bound = g >= 0.f ? ni * g * (1.f + 2.3841858e-07f)
-                               : ni * (1.f - (float)(2 * f + 4) * 1.1920929e-07f) * g * (1.f - 2.3841858e-07f);
-  keys[t] = float_desc_key(bound);
-  vals[t] = (int32_t)i;
+  return g >= 0.f ? ni * g * (1.f + 2.3841858e-07f)
+                  : ni * (1.f - (float)(2 * f + 4) * 1.1920929e-07f) * g * (1.f - 2.3841858e-07f);
+}
+
+__global__ void __launch_bounds__(kCbItems)
+    cbound_kernel(const float* __restrict__ cent, int C, int f, const float* __restrict__ items,
+                  const float* __restrict__ item_nrm, int64_t n_items, const uint32_t* __restrict__ cosb_ord,
+                  uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  extern __shared__ __align__(16) float cb_smem[];
+  float* it = cb_smem;                                  // [f][kCbItems + 1]
+  float* ct = it + cb_items_floats(f);                  // [f][kCbChunk], 16-byte aligned
+  float* cn2 = ct + (size_t)f * kCbChunk;               // [kCbChunk]
+  const int t = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kCbItems;
+  const int j0 = blockIdx.y * kCbChunk;
+  const int rows = (int)min((int64_t)kCbItems, n_items - i0);
+  const int nc = min(kCbChunk, C - j0);
+  for (int e = t; e < kCbItems * f; e += kCbItems) {
+    const int r = e / f, k = e - r * f;
+    it[k * (kCbItems + 1) + r] = r < rows ? items[(i0 + r) * f + k] : 0.f;
+  }
+  for (int e = t; e < kCbChunk * f; e += kCbItems) {
+    const int jj = e / f, k = e - jj * f;
+    ct[k * kCbChunk + jj] = jj < nc ? cent[(int64_t)(j0 + jj) * f + k] : 0.f;
+  }
+  __syncthreads();
+  if (t < kCbChunk) {
+    float sc = 0.f;
+    for (int k = 0; k < f; ++k) sc = __fmaf_rn(ct[k * kCbChunk + t], ct[k * kCbChunk + t], sc);
+    cn2[t] = sc;
+  }
+  float si = 0.f;
+  for (int k = 0; k < f; ++k) si = __fmaf_rn(it[k * (kCbItems + 1) + t], it[k * (kCbItems + 1) + t], si);
+  __syncthreads();
+  if (t >= rows) return;
+  const int64_t i = i0 + t;
+  const float ni = item_nrm[i];
+  for (int jj = 0; jj < nc; jj += 4) {
+    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+    for (int k = 0; k < f; ++k) {
+      const float v = it[k * (kCbItems + 1) + t];
+      const float4 c4 = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj);
+      d0 = __fmaf_rn(c4.x, v, d0);
+      d1 = __fmaf_rn(c4.y, v, d1);
+      d2 = __fmaf_rn(c4.z, v, d2);
+      d3 = __fmaf_rn(c4.w, v, d3);
+    }
+    const float d[4] = {d0, d1, d2, d3};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (jj + q < nc) {
+        const int j = j0 + jj + q;
+        const float y = ord2f(cosb_ord[j]);
+        const int64_t o = (int64_t)j * n_items + i;
+        keys[o] = float_desc_key(cbound_value(d[q], cn2[jj + q], si, ni, y, f));
+        vals[o] = (int32_t)i;
+      }
+    }
+  }
 }
 
 __global__ void cosb_init_kernel(uint32_t* __restrict__ cosb_ord, int C) {
@@ -473,29 +523,37 @@ __global__ void mx_gather_bf16_kernel(const uint4* __restrict__ src, const int32
   dst[t] = m >= 0 ? src[(int64_t)m * words + w] : make_uint4(0, 0, 0, 0);
 }
 
-// Per-cluster item copies in list order, rows [j * n_pad, j * n_pad + n_pad):
-// BF16 operand rows, bound columns and positions (padding: zero / 0).
+// Per-cluster item copies in list order (cluster j = blockIdx.y at rows
+// j * n_pad + rank): BF16 operand rows, bound columns and positions for the
+// list ranks [256 t_begin, 256 t_end_j), t_end_j = cl_end[j] (or t_end),
+// capped at n_pad; ranks past the list are zero rows.  Only the ranks a walk
+// reaches are copied.
 __global__ void mx_items_by_cluster_kernel(const uint4* __restrict__ items_bf16, const float2* __restrict__ item_aux,
-                                           const int32_t* __restrict__ lists, int64_t n_items, int64_t n_pad, int C,
-                                           int words, uint4* __restrict__ b_rows, float2* __restrict__ aux_c,
+                                           const int32_t* __restrict__ lists, int64_t n_items, int64_t n_pad, int words,
+                                           int t_begin, int t_end, const int* __restrict__ cl_end,
+                                           uint4* __restrict__ b_rows, float2* __restrict__ aux_c,
                                            int32_t* __restrict__ pos_c) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)C * n_pad * words) return;
-  const int64_t r = t / words;
-  const int w = (int)(t - r * words);
-  const int64_t j = r / n_pad, rank = r - j * n_pad;
-  if (rank < n_items) {
-    const int32_t pos = lists[j * n_items + rank];
-    b_rows[t] = items_bf16[(int64_t)pos * words + w];
-    if (w == 0) {
-      aux_c[r] = item_aux[pos];
-      pos_c[r] = pos;
-    }
-  } else {
-    b_rows[t] = make_uint4(0, 0, 0, 0);
-    if (w == 0) {
-      aux_c[r] = make_float2(0.f, 0.f);
-      pos_c[r] = 0;
+  const int64_t j = blockIdx.y;
+  const int64_t r0 = (int64_t)t_begin * 256;
+  const int64_t r1 = min(n_pad, (int64_t)(cl_end ? cl_end[j] : t_end) * 256);
+  const int64_t n = (r1 - r0) * words;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rank = r0 + e / words;
+    const int w = (int)(e % words);
+    const int64_t r = j * n_pad + rank;
+    if (rank < n_items) {
+      const int32_t pos = lists[j * n_items + rank];
+      b_rows[r * words + w] = items_bf16[(int64_t)pos * words + w];
+      if (w == 0) {
+        aux_c[r] = item_aux[pos];
+        pos_c[r] = pos;
+      }
+    } else {
+      b_rows[r * words + w] = make_uint4(0, 0, 0, 0);
+      if (w == 0) {
+        aux_c[r] = make_float2(0.f, 0.f);
+        pos_c[r] = 0;
+      }
     }
   }
 }
@@ -525,8 +583,8 @@ __global__ void mx_work1_kernel(const int* __restrict__ pad_off, int C, int64_t 
 //   key = cluster << tile_bits | tiles.
 __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux, int64_t n_users,
                                const float* __restrict__ bounds, int64_t n_items, int r1, SelectOut o, int K,
-                               int tile_bits, int32_t* __restrict__ ustop, uint32_t* __restrict__ keys,
-                               int32_t* __restrict__ vals) {
+                               int tile_bits, int32_t* __restrict__ ustop, int* __restrict__ cl_end,
+                               uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= n_users) return;
   const int64_t l0 = u * 2;
@@ -555,6 +613,7 @@ __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2*
   }
   const int tiles = (int)((lo + 255) / 256);
   ustop[u] = tiles;
+  atomicMax(&cl_end[j], tiles);
   keys[u] = ((uint32_t)j << tile_bits) | (uint32_t)tiles;
   vals[u] = (int32_t)u;
 }
@@ -607,6 +666,10 @@ __global__ void mx_visited_kernel(const int32_t* __restrict__ user_row, int64_t 
   atomicAdd(pairs, (unsigned long long)v);
 }
 
+unsigned copy_blocks(int C) {  // blocks per cluster of the list copies: about 64 per SM in all
+  return (unsigned)std::max(1, 152 * 64 / std::max(C, 1));
+}
+
 int bits_for(int64_t x) {  // bits to hold 0..x
   int b = 0;
   while (b < 62 && (int64_t(1) << b) <= x) ++b;
@@ -621,6 +684,9 @@ bool mx_tc_regroup_fits(int C, int64_t n_items) {
 
 cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_bf16, const float2* item_aux,
                           const int32_t* lists, cudaStream_t s, int* launches) {
+  m.items_bf16 = items_bf16;
+  m.item_aux = item_aux;
+  m.lists = lists;
   const int words = m.fp * 2 / 16;
   mx_pad_layout_kernel<<<1, 32, 0, s>>>(m.counts, m.C, m.pad_off);
   cudaError_t e = cudaMemsetAsync(m.row_user, 0xff, sizeof(int32_t) * m.n_rows_max, s);
@@ -629,9 +695,9 @@ cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_b
                                                                         m.row_user, m.user_row);
   mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * words + 255) / 256), 256, 0, s>>>(
       (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, words, (uint4*)m.a_rows);
-  const int64_t tot = (int64_t)m.C * m.n_pad * words;
-  mx_items_by_cluster_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-      (const uint4*)items_bf16, item_aux, lists, m.n_items, m.n_pad, m.C, words, (uint4*)m.b_rows, m.aux_c, m.pos_c);
+  const dim3 cgrid(copy_blocks(m.C), (unsigned)m.C);
+  mx_items_by_cluster_kernel<<<cgrid, 256, 0, s>>>((const uint4*)items_bf16, item_aux, lists, m.n_items, m.n_pad, words,
+                                                   0, m.t1, nullptr, (uint4*)m.b_rows, m.aux_c, m.pos_c);
   const int64_t mw = m.max_work;
   mx_work1_kernel<<<(unsigned)((mw + 255) / 256), 256, 0, s>>>(m.pad_off, m.C, m.n_pad, m.t1, m.w1, m.w1 + mw,
                                                                 m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work);
@@ -647,10 +713,15 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   const int key_bits = bits_for(m.C - 1) + tile_bits;
   cudaError_t e = cudaMemsetAsync(m.work_end, 0, sizeof(int) * mw, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.n_work + 1, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m.cl_end, 0, sizeof(int) * m.C, s);
   if (e != cudaSuccess) return e;
   mx_stop_kernel<<<ub, 256, 0, s>>>(assign, user_aux, nU, bounds, m.n_items, m.t1 * 256, o, K, tile_bits, m.ustop,
-                                    m.ukeys[0], m.uvals[0]);
-  *launches += 1;
+                                    m.cl_end, m.ukeys[0], m.uvals[0]);
+  // the rest of each cluster's list that some member still needs
+  const dim3 cgrid(copy_blocks(m.C), (unsigned)m.C);
+  mx_items_by_cluster_kernel<<<cgrid, 256, 0, s>>>((const uint4*)m.items_bf16, m.item_aux, m.lists, m.n_items, m.n_pad,
+                                                   m.fp / 8, m.t1, 0, m.cl_end, (uint4*)m.b_rows, m.aux_c, m.pos_c);
+  *launches += 2;
   // regroup: the users of each cluster in order of the item tiles they
   // need, so that each A tile's walk is close to its users' own need
   uint32_t* k0 = m.ukeys[0];
@@ -723,8 +794,11 @@ cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int
                            uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches) {
   cosb_init_kernel<<<(C + 127) / 128, 128, 0, s>>>(cosb_ord, C);
   cosb_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, cent, cosb_ord);
-  const int64_t n = (int64_t)C * n_items;
-  cbound_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(cent, C, f, items, item_nrm, n_items, cosb_ord, keys, vals);
+  const size_t smem = sizeof(float) * (cb_items_floats(f) + (size_t)f * kCbChunk + kCbChunk);
+  cudaError_t e = cudaFuncSetAttribute(cbound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((n_items + kCbItems - 1) / kCbItems), (unsigned)((C + kCbChunk - 1) / kCbChunk));
+  cbound_kernel<<<grid, kCbItems, smem, s>>>(cent, C, f, items, item_nrm, n_items, cosb_ord, keys, vals);
   cosb_to_float_kernel<<<(C + 127) / 128, 128, 0, s>>>(cosb_ord, C, cosb_f);
   *launches += 4;
   return cudaGetLastError();

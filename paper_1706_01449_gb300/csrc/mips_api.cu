@@ -319,7 +319,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int64_t nl = n_users * 2;
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
-         o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0;
+         o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0, o_clend = 0;
   if (use_tc) {
     o_u16 = ws.take(sizeof(uint16_t) * n_users * fp);
     o_uaux = ws.take(sizeof(float2) * n_users);
@@ -342,6 +342,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     o_work2 = ws.take(sizeof(uint32_t) * nl * cap2);
     o_sc2 = ws.take(sizeof(double) * nl * cap2);
     o_ustop = ws.take(sizeof(int32_t) * n_users);
+    o_clend = ws.take(sizeof(int) * C);
     o_wk0 = ws.take(sizeof(uint32_t) * max_work);
     o_wk1 = ws.take(sizeof(uint32_t) * max_work);
     o_wv0 = ws.take(sizeof(int32_t) * max_work);
@@ -417,6 +418,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     m.n_work = ws.at<int>(o_nw);
     m.work_end = ws.at<int>(o_wend);
     m.ustop = ws.at<int32_t>(o_ustop);
+    m.cl_end = ws.at<int>(o_clend);
     m.ukeys[0] = ws.at<uint32_t>(o_uk);  // the user-group sort is done with these
     m.ukeys[1] = ws.at<uint32_t>(o_uk2);
     m.uvals[0] = ws.at<int32_t>(o_ui);
