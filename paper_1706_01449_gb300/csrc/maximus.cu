@@ -140,6 +140,39 @@ __global__ void kmeans_accum_kernel(const float* __restrict__ users, int64_t n_u
   if (k == 0) atomicAdd(&counts[j], 1u);
 }
 
+// The same sums for the clusters [j0, j0 + cc) of this block's chunk
+// (blockIdx.y), partial sums of a grid-stride share of the users kept in
+// shared memory, then one global add per (cluster, dimension) and block.
+// Integer sums: the same result as kmeans_accum_kernel in any order.
+__global__ void kmeans_accum_smem_kernel(const float* __restrict__ users, int64_t n_users, int f,
+                                         const int32_t* __restrict__ assign, int C, int cc,
+                                         const float* __restrict__ scale, unsigned long long* __restrict__ sums,
+                                         unsigned int* __restrict__ counts) {
+  extern __shared__ unsigned long long km_acc[];        // [cc][f]
+  unsigned int* km_cnt = (unsigned int*)(km_acc + (size_t)cc * f);  // [cc]
+  const int j0 = blockIdx.y * cc;
+  const int nc = min(cc, C - j0);
+  for (int e = threadIdx.x; e < nc * f; e += blockDim.x) km_acc[e] = 0ull;
+  for (int e = threadIdx.x; e < nc; e += blockDim.x) km_cnt[e] = 0u;
+  __syncthreads();
+  const float sc = scale[0];
+  const int64_t total = n_users * f;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = t / f;
+    const int k = (int)(t - u * f);
+    const int j = assign[u] - j0;
+    if (j >= 0 && j < nc) {
+      atomicAdd(&km_acc[j * f + k], (unsigned long long)__float2ll_rn(users[t] * sc));
+      if (k == 0) atomicAdd(&km_cnt[j], 1u);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nc * f; e += blockDim.x)
+    if (km_acc[e]) atomicAdd(&sums[(int64_t)j0 * f + e], km_acc[e]);
+  for (int e = threadIdx.x; e < nc; e += blockDim.x)
+    if (km_cnt[e]) atomicAdd(&counts[j0 + e], km_cnt[e]);
+}
+
 // Update step, part 2: mean of the members; an empty cluster keeps its centroid.
 __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ sums, const unsigned int* __restrict__ counts,
                                     int C, int f, const float* __restrict__ scale, float* __restrict__ cent) {
@@ -298,9 +331,22 @@ __global__ void iota_u32_kernel(const int32_t* __restrict__ assign, int64_t n, u
   ids[t] = (int32_t)t;
 }
 
-__global__ void cluster_count_kernel(const int32_t* __restrict__ assign, int64_t n, int* __restrict__ counts) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) atomicAdd(&counts[assign[t]], 1);
+// counts[j] += members of cluster j: a shared-memory histogram per block
+// when C fits (use_smem), else global atomics.
+__global__ void cluster_count_kernel(const int32_t* __restrict__ assign, int64_t n, int C, int use_smem,
+                                     int* __restrict__ counts) {
+  extern __shared__ int cc_hist[];
+  if (use_smem) {
+    for (int j = threadIdx.x; j < C; j += blockDim.x) cc_hist[j] = 0;
+    __syncthreads();
+  }
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(use_smem ? &cc_hist[assign[t]] : &counts[assign[t]], 1);
+  if (use_smem) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < C; j += blockDim.x)
+      if (cc_hist[j]) atomicAdd(&counts[j], cc_hist[j]);
+  }
 }
 
 // offsets[j] = users before cluster j; tile_off[j] = walk tiles before j
@@ -581,12 +627,11 @@ __global__ void mx_work1_kernel(const int* __restrict__ pad_off, int C, int64_t 
 // either.  Users with no such rank need the whole list.  The sort key puts
 // the users of a cluster in order of that need:
 //   key = cluster << tile_bits | tiles.
-__global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux, int64_t n_users,
-                               const float* __restrict__ bounds, int64_t n_items, int r1, SelectOut o, int K,
-                               int tile_bits, int32_t* __restrict__ ustop, int* __restrict__ cl_end,
-                               uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n_users) return;
+__device__ __forceinline__ void mx_stop_user(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux,
+                                             const float* __restrict__ bounds, int64_t n_items, int r1, const SelectOut& o,
+                                             int K, int tile_bits, int64_t u, int32_t* __restrict__ ustop,
+                                             int* cl_max,  // shared or global per-cluster maxima
+                                             uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
   const int64_t l0 = u * 2;
   float tau = fmaxf(o.tau[l0], o.tau[l0 + 1]);
   if (o.topl && o.topl_sorted) {
@@ -613,9 +658,28 @@ __global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2*
   }
   const int tiles = (int)((lo + 255) / 256);
   ustop[u] = tiles;
-  atomicMax(&cl_end[j], tiles);
+  atomicMax(&cl_max[j], tiles);
   keys[u] = ((uint32_t)j << tile_bits) | (uint32_t)tiles;
   vals[u] = (int32_t)u;
+}
+
+__global__ void mx_stop_kernel(const int32_t* __restrict__ assign, const float2* __restrict__ user_aux, int64_t n_users,
+                               const float* __restrict__ bounds, int64_t n_items, int r1, SelectOut o, int K,
+                               int tile_bits, int C, int use_smem, int32_t* __restrict__ ustop,
+                               int* __restrict__ cl_end, uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+  extern __shared__ int st_clmax[];  // [C] per-block maxima (use_smem)
+  if (use_smem) {
+    for (int j = threadIdx.x; j < C; j += blockDim.x) st_clmax[j] = 0;
+    __syncthreads();
+  }
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u < n_users) mx_stop_user(assign, user_aux, bounds, n_items, r1, o, K, tile_bits, u, ustop,
+                                use_smem ? st_clmax : cl_end, keys, vals);
+  if (use_smem) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < C; j += blockDim.x)
+      if (st_clmax[j]) atomicMax(&cl_end[j], st_clmax[j]);
+  }
 }
 
 // work_end[tile] = max item tiles over the users of the A tile.
@@ -626,16 +690,20 @@ __global__ void mx_tile_end_kernel(const int32_t* __restrict__ ustop, const int3
   atomicMax(&work_end[user_row[u] / kThreads], ustop[u]);
 }
 
-// Sort keys of the pass-2 work list: A tiles that need more than t1 item
-// tiles, longest first (key n_it - length); the rest sort last (key n_it).
-__global__ void mx_work2_keys_kernel(const int* __restrict__ n_work1, const int* __restrict__ work_end, int64_t max_work,
-                                     int t1, int n_it, uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
+// Sort keys of the pass-2 work list: the A tiles that need more than t1
+// item tiles, by cluster and within a cluster longest first
+// (key = cluster << tile_bits | n_it - length), so that the CTAs running at
+// one time read the same cluster's list through L2; the rest sort last.
+__global__ void mx_work2_keys_kernel(const int* __restrict__ n_work1, const int* __restrict__ work_end,
+                                     const int* __restrict__ b_row1, int64_t n_pad, int64_t max_work, int t1, int n_it,
+                                     int tile_bits, uint32_t* __restrict__ keys, int32_t* __restrict__ vals,
                                      int* __restrict__ n_work2, DevStats* stats) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= max_work) return;
   const bool real = w < *n_work1;
   const int end = real ? work_end[w] : 0;
-  keys[w] = (uint32_t)(end > t1 ? n_it - (end - t1) : n_it);
+  const uint32_t j = real ? (uint32_t)(b_row1[w] / n_pad) : 0u;
+  keys[w] = end > t1 ? (j << tile_bits) | (uint32_t)(n_it - (end - t1)) : 0xffffffffu;
   vals[w] = w;
   if (end > t1) atomicAdd(n_work2, 1);
   if (real) atomicAdd(&stats->blocks_walked, (unsigned long long)(end > t1 ? end : t1));
@@ -659,11 +727,15 @@ __global__ void mx_visited_kernel(const int32_t* __restrict__ user_row, int64_t 
                                   int t1, int64_t n_items, int32_t* __restrict__ visited,
                                   unsigned long long* __restrict__ pairs) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n_users) return;
-  const int end = max(t1, work_end[user_row[u] / kThreads]);
-  const int64_t v = min((int64_t)end * 256, n_items);
-  visited[u] = (int32_t)v;
-  atomicAdd(pairs, (unsigned long long)v);
+  unsigned long long v = 0;
+  if (u < n_users) {
+    const int end = max(t1, work_end[user_row[u] / kThreads]);
+    v = (unsigned long long)min((int64_t)end * 256, n_items);
+    visited[u] = (int32_t)v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(pairs, v);
 }
 
 unsigned copy_blocks(int C) {  // blocks per cluster of the list copies: about 64 per SM in all
@@ -715,8 +787,10 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   if (e == cudaSuccess) e = cudaMemsetAsync(m.n_work + 1, 0, sizeof(int), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(m.cl_end, 0, sizeof(int) * m.C, s);
   if (e != cudaSuccess) return e;
-  mx_stop_kernel<<<ub, 256, 0, s>>>(assign, user_aux, nU, bounds, m.n_items, m.t1 * 256, o, K, tile_bits, m.ustop,
-                                    m.cl_end, m.ukeys[0], m.uvals[0]);
+  const int st_smem = m.C <= 8192;
+  mx_stop_kernel<<<ub, 256, st_smem ? sizeof(int) * m.C : 0, s>>>(assign, user_aux, nU, bounds, m.n_items, m.t1 * 256,
+                                                                   o, K, tile_bits, m.C, st_smem, m.ustop, m.cl_end,
+                                                                   m.ukeys[0], m.uvals[0]);
   // the rest of each cluster's list that some member still needs
   const dim3 cgrid(copy_blocks(m.C), (unsigned)m.C);
   mx_items_by_cluster_kernel<<<cgrid, 256, 0, s>>>((const uint4*)m.items_bf16, m.item_aux, m.lists, m.n_items, m.n_pad,
@@ -735,14 +809,14 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * (m.fp / 8) + 255) / 256), 256, 0, s>>>(
       (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, m.fp / 8, (uint4*)m.a_rows);
   mx_tile_end_kernel<<<ub, 256, 0, s>>>(m.ustop, m.user_row, nU, m.work_end);
-  mx_work2_keys_kernel<<<wb, 256, 0, s>>>(m.n_work, m.work_end, mw, m.t1, m.n_it, m.wkeys[0], m.wvals[0], m.n_work + 1,
-                                          stats);
+  mx_work2_keys_kernel<<<wb, 256, 0, s>>>(m.n_work, m.work_end, m.w1 + mw, m.n_pad, mw, m.t1, m.n_it, tile_bits,
+                                          m.wkeys[0], m.wvals[0], m.n_work + 1, stats);
   *launches += 4;
   uint32_t* wk0 = m.wkeys[0];
   int32_t* wv0 = m.wvals[0];
   uint32_t* wk1 = m.wkeys[1];
   int32_t* wv1 = m.wvals[1];
-  e = radix_sort_pairs(wk0, wv0, wk1, wv1, mw, 1, 0, tile_bits, m.temp, s, launches);
+  e = radix_sort_pairs(wk0, wv0, wk1, wv1, mw, 1, 0, 32, m.temp, s, launches);
   if (e != cudaSuccess) return e;
   mx_work2_kernel<<<wb, 256, 0, s>>>(m.n_work + 1, wv0, m.w1, m.w1 + mw, m.work_end, m.t1, m.w2, m.w2 + mw,
                                      m.w2 + 2 * mw, m.w2 + 3 * mw);
@@ -781,8 +855,17 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
     e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * C * f, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned int) * C, s);
     if (e != cudaSuccess) return e;
-    kmeans_accum_kernel<<<(unsigned)((n_users * f + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, C, scale, sums,
-                                                                            counts);
+    if ((size_t)C * f * 8 + (size_t)C * 4 <= 96 * 1024) {
+      // all partial sums fit one block's shared memory
+      const size_t smem = (size_t)C * f * 8 + (size_t)C * 4;
+      e = cudaFuncSetAttribute(kmeans_accum_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users * f + 255) / 256, 152 * 8));
+      kmeans_accum_smem_kernel<<<dim3(bx, 1), 256, smem, s>>>(users, n_users, f, assign, C, C, scale, sums, counts);
+    } else {  // many clusters: the global adds spread over C * f addresses
+      kmeans_accum_kernel<<<(unsigned)((n_users * f + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, C, scale,
+                                                                              sums, counts);
+    }
     kmeans_update_kernel<<<(C * f + 255) / 256, 256, 0, s>>>(sums, counts, C, f, scale, cent);
     *launches += 4;
   }
@@ -810,7 +893,11 @@ cudaError_t maximus_group(const int32_t* assign, int64_t n_users, int C, uint32_
   iota_u32_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, n_users, keys, ids);
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * C, s);
   if (e != cudaSuccess) return e;
-  cluster_count_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(assign, n_users, counts);
+  {
+    const int use_smem = C <= 8192;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, 152 * 4));
+    cluster_count_kernel<<<blocks, 256, use_smem ? sizeof(int) * C : 0, s>>>(assign, n_users, C, use_smem, counts);
+  }
   cluster_offsets_kernel<<<1, 32, 0, s>>>(counts, C, offsets, tile_off);
   *launches += 3;
   int bits = 8;
