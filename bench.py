@@ -343,6 +343,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(U, I, K)
 
+    tiles = (stats["blocks_walked"] if walked else ((nU + 127) // 128) * ((nI + 255) // 256))
     line = {
         "metric": "exact top-K users/sec", "value": value, "unit": "users/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -361,8 +362,9 @@ def main():
                                                        "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
         "candidates_per_user": stats["cand_emitted"] / nU, "rescored_per_user": stats["cand_rescored"] / nU,
         "users_overflow": stats["users_overflow"], "users_fp64": stats["users_fp64"],
-        "select_slow_chunk_frac": (stats["select_slow"] / (((nU + 255) // 256) * 8 * ((nI + 127) // 128) * 8)
-                                   if dtype == "bf16" else None),
+        # per warp and 16-score chunk of the tiles the score kernel processed
+        # (128 users x 256 items each)
+        "select_slow_chunk_frac": (stats["select_slow"] / (tiles * 8 * 8) if dtype == "bf16" and tiles else None),
     }
     print(json.dumps(line), flush=True)
     index.close()
