@@ -27,6 +27,9 @@ struct DevStats {
   unsigned long long pad;
 };
 
+// Maximus lists are sorted by this many leading bits of the bound key.
+constexpr int kListKeyBits = 16;
+
 // Unsigned key whose ascending order is the float's DESCENDING order.
 __host__ __device__ inline uint32_t float_desc_key(float x) {
 #ifdef __CUDA_ARCH__

@@ -315,11 +315,16 @@ __global__ void cosb_to_float_kernel(const uint32_t* __restrict__ cosb_ord, int 
   if (j < C) out[j] = ord2f(cosb_ord[j]);
 }
 
-// sorted key -> bound value (float_desc_key is invertible)
+// sorted key -> bound of the list rank.  The lists are sorted by the key's
+// top 16 bits only (kListKeyBits), so each rank gets the largest bound its
+// 16-bit bucket can hold: the key with the low bits cleared (keys ascend
+// as bounds descend).  The result is non-increasing along the list and at
+// least the bound of every item at that rank or later.
 __global__ void keys_to_bounds_kernel(const uint32_t* __restrict__ keys, int64_t n, float* __restrict__ out) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
-  out[t] = ord2f(~keys[t]);
+  constexpr uint32_t mask = ~((1u << (32 - kListKeyBits)) - 1u);
+  out[t] = ord2f(~(keys[t] & mask));
 }
 
 // ---------------------------------------------------------------- grouping

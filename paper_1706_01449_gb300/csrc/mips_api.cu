@@ -363,12 +363,13 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
                            idx->item_nrm, nI, ws.at<uint32_t>(o_cosb), ws.at<uint32_t>(o_keys), ws.at<int32_t>(o_vals),
                            ws.at<float>(o_cosbf), s, &idx->launches));
   if ((st = end_stage(idx, ST_BOUNDS, s)) != MIPS_OK) return st;
-  // per-cluster lists: items by CBound, descending (stable: ties by position)
+  // per-cluster lists: items by CBound (its key's leading kListKeyBits bits), descending, stable
   uint32_t* keys = ws.at<uint32_t>(o_keys);
   int32_t* vals = ws.at<int32_t>(o_vals);
   uint32_t* keys2 = ws.at<uint32_t>(o_keys2);
   int32_t* vals2 = ws.at<int32_t>(o_vals2);
-  MIPS_CUDA(radix_sort_pairs(keys, vals, keys2, vals2, nI, C, 0, 32, ws.at<uint32_t>(o_tmp), s, &idx->launches));
+  MIPS_CUDA(radix_sort_pairs(keys, vals, keys2, vals2, nI, C, 32 - kListKeyBits, 32, ws.at<uint32_t>(o_tmp), s,
+                             &idx->launches));
   MIPS_CUDA(maximus_keys_to_bounds(keys, CI, ws.at<float>(o_bounds), s));
   idx->launches += 1;
   int32_t* user_perm = nullptr;
