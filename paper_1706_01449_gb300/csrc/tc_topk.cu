@@ -802,11 +802,15 @@ cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorM
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
   const bool mx = p.mode != 0;
-  if (p.K <= kRegTopK)
-    return mx ? launch_variant<kRegTopK, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
-              : launch_variant<kRegTopK, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s);
-  return mx ? launch_variant<0, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
-            : launch_variant<0, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s);
+  // register top-K sized to K: the insertion cost grows with the array
+#define MIPS_TC_LAUNCH(KR)                                                                                        \
+  return mx ? launch_variant<KR, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s) \
+            : launch_variant<KR, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
+  if (p.K == 1) MIPS_TC_LAUNCH(1);
+  if (p.K <= 10) MIPS_TC_LAUNCH(10);
+  if (p.K <= kRegTopK) MIPS_TC_LAUNCH(kRegTopK);
+  MIPS_TC_LAUNCH(0);
+#undef MIPS_TC_LAUNCH
 }
 
 }  // namespace mips
