@@ -377,31 +377,53 @@ __device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t
     select16<KR, MX>(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos0, pos_tile, slow, emit_only);
 }
 
-// First pass over a user tile's first item tile: every score's lower bound
-// goes through the top-K (nothing is emitted), so the threshold starts the
-// scan near its final value instead of at -inf.  The columns are the items
-// of largest norm (the index stores items by norm, descending).
+// First pass over a user tile's first item tile (the items of largest norm:
+// the index stores items by norm, descending), so that the threshold starts
+// the scan near its final value instead of at -inf; nothing is emitted.
+// K = 1: the 64 scores form 8 groups of 8 and each group's largest lower
+// bound goes to the top-1 -- branch-free, and the result is the exact
+// maximum.  K > 1: every lower bound above the threshold is queued, then
+// inserted (group maxima would be cheaper but give a lower threshold,
+// which measured slower overall on large catalogues).
 template <int KR>
 __device__ __forceinline__ void seed64(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[64], int col0, int valid,
                                        const float2* aux_tile) {
+  if constexpr (KR == 1) {
 #pragma unroll
-  for (int g = 0; g < 4; ++g) {
-    // lower bounds above the current threshold are queued, then inserted
-    int n = 0;
+    for (int g = 0; g < 8; ++g) {
+      float m = kNegInf;
 #pragma unroll
-    for (int q = 16 * g; q < 16 * g + 16; ++q) {
-      const float H = __uint_as_float(r[q]);
-      if (H > s.tau && q < valid) {  // L <= H: nothing at or below tau can enter
-        const float L = tc_lower(s, c, H, aux_tile[col0 + q]);
-        if (L > s.tau) {
-          c.qh[n * kEpiThreads] = L;
-          ++n;
+      for (int q = 8 * g; q < 8 * g + 8; ++q) {
+        const float L = tc_lower(s, c, __uint_as_float(r[q]), aux_tile[col0 + q]);
+        m = fmaxf(m, q < valid ? L : kNegInf);
+      }
+      c.qh[g * kEpiThreads] = m;
+    }
+    // inserted from shared memory in a rolled loop (keeps the registers down)
+#pragma unroll 1
+    for (int g = 0; g < 8; ++g) {
+      const float m = c.qh[g * kEpiThreads];
+      if (m > s.tau) s.tau = topk_insert(s, c, m);
+    }
+  } else {
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      int n = 0;
+#pragma unroll
+      for (int q = 16 * g; q < 16 * g + 16; ++q) {
+        const float H = __uint_as_float(r[q]);
+        if (H > s.tau && q < valid) {  // L <= H: nothing at or below tau can enter
+          const float L = tc_lower(s, c, H, aux_tile[col0 + q]);
+          if (L > s.tau) {
+            c.qh[n * kEpiThreads] = L;
+            ++n;
+          }
         }
       }
-    }
-    for (int t = 0; t < n; ++t) {
-      const float L = c.qh[t * kEpiThreads];
-      if (L > s.tau) s.tau = topk_insert(s, c, L);
+      for (int t = 0; t < n; ++t) {
+        const float L = c.qh[t * kEpiThreads];
+        if (L > s.tau) s.tau = topk_insert(s, c, L);
+      }
     }
   }
 }
