@@ -134,6 +134,24 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
                         mips_select_report* rep);
 
 /*
+ * mips_topk (method 0) or mips_topk_maximus (method 1) through a CUDA
+ * graph: the first call with a given (method, users_dev, n_users, K,
+ * out_idx_dev, out_score_dev) runs the plain call and then captures the
+ * same call into a graph held by the index; later calls with the same
+ * arguments replay it with one cudaGraphLaunch on `stream` (the inputs
+ * are read afresh, so new user values at the same address give new
+ * results).  A graph is dropped once the index's workspace is reallocated
+ * by a larger call; the index keeps at most 8.  The legacy default stream
+ * (NULL) cannot be captured: the call then runs plain.  Same result
+ * semantics, ownership and errors as mips_topk; method outside {0, 1}:
+ * MIPS_ERR_ARG.  No counterpart in the paper (one grouped launch per pass
+ * and the whole call in one graph are GPU forms of its batching).
+ */
+mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                            int method, int32_t* out_idx_dev, double* out_score_dev,
+                            void* stream);
+
+/*
  * Host-memory variant of mips_topk (method 0) / mips_topk_maximus
  * (method 1) / mips_select (method 2): copies users_host to the device,
  * runs the method and copies the results back, all on `stream`, then

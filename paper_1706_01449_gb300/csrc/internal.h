@@ -159,6 +159,9 @@ struct MxTc {
   int32_t* wvals[2] = {};
   uint32_t* temp = nullptr;          // radix sort scratch for max(n_users, max_work) keys
 };
+// k-means initial centroid ids: C distinct users of n (seeded Floyd draw on
+// the device; chosen_bits: scratch of (n + 31) / 32 words).
+cudaError_t draw_init_ids(int64_t n, int C, uint64_t seed, uint32_t* chosen_bits, int64_t* ids, cudaStream_t s);
 // Whether the regroup sort key (cluster, item tiles) fits 32 bits.
 bool mx_tc_regroup_fits(int C, int64_t n_items);
 // A rows, the B rows pass 1 reads, pass-1 work list.

@@ -830,6 +830,42 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   return cudaGetLastError();
 }
 
+// k-means initial centroids: C distinct users drawn by Floyd's algorithm
+// from SplitMix64 over a counter keyed by the seed (one thread; `chosen` is
+// a zeroed bitmap of n bits).  For j = n - C .. n - 1: t = draw mod (j + 1);
+// take t, or j if t was taken before.
+namespace {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void draw_init_ids_kernel(int64_t n, int C, uint64_t seed, uint32_t* __restrict__ chosen,
+                                     int64_t* __restrict__ ids) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint64_t ctr = 0;
+  int k = 0;
+  for (int64_t j = n - C; j < n; ++j, ++k) {
+    const int64_t t = (int64_t)(splitmix64(seed ^ splitmix64(++ctr)) % (uint64_t)(j + 1));
+    const bool taken = (chosen[t >> 5] >> (t & 31)) & 1u;
+    const int64_t pick = taken ? j : t;
+    chosen[pick >> 5] |= 1u << (pick & 31);
+    ids[k] = pick;
+  }
+}
+
+}  // namespace
+
+cudaError_t draw_init_ids(int64_t n, int C, uint64_t seed, uint32_t* chosen_bits, int64_t* ids, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(chosen_bits, 0, sizeof(uint32_t) * ((n + 31) / 32), s);
+  if (e != cudaSuccess) return e;
+  draw_init_ids_kernel<<<1, 32, 0, s>>>(n, C, seed, chosen_bits, ids);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host side
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,

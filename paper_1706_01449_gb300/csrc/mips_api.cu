@@ -47,6 +47,7 @@ struct Arena {
   char* base = nullptr;
   size_t cap = 0;
   size_t used = 0;
+  uint64_t gen = 0;  // bumped on every reallocation (captured graphs hold the old base)
 
   void reset() { used = 0; }
   size_t take(size_t bytes) {
@@ -66,6 +67,7 @@ struct Arena {
     cudaError_t e = cudaMallocAsync((void**)&base, want, s);
     if (e != cudaSuccess) return e;
     cap = want;
+    ++gen;
     return cudaSuccess;
   }
   template <typename T>
@@ -128,6 +130,24 @@ struct mips_index_s {
   int order[kStages] = {};  // stages in the order they ran in the last call
   int n_order = 0;
   int launches = 0;
+  // captured calls (mips_topk_graph): replayed while the arguments and the
+  // workspace are the same
+  bool capturing = false;
+  struct Graph {
+    int method = 0;
+    const float* users = nullptr;
+    int64_t n_users = 0;
+    int K = 0;
+    int32_t* out_idx = nullptr;
+    double* out_score = nullptr;
+    uint64_t ws_gen = 0;
+    cudaGraphExec_t exec = nullptr;
+    // host bookkeeping of the captured call, restored on replay
+    bool stage_ran[kStages] = {};
+    int order[kStages] = {};
+    int n_order = 0, last_stage = -1, launches = 0, clusters = 0, dtype = 0;
+  };
+  std::vector<Graph> graphs;
 };
 
 namespace {
@@ -139,20 +159,27 @@ mips_status check_device(mips_index_t idx) {
   return MIPS_OK;
 }
 
+// Stage events; inside a stream capture they become event-record nodes of
+// the graph, so a replay times its stages too.
+cudaError_t record(mips_index_t idx, cudaEvent_t ev, cudaStream_t s) {
+  return idx->capturing ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal) : cudaEventRecord(ev, s);
+}
+
 mips_status begin_call(mips_index_t idx, cudaStream_t s) {
-  if (idx->has_done) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
+  // (a captured call is ordered after the previous one at launch time)
+  if (idx->has_done && !idx->capturing) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
   MIPS_CUDA(cudaMemsetAsync(idx->stats_dev, 0, sizeof(DevStats), s));
   for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
   idx->last_stage = -1;
   idx->n_order = 0;
   idx->launches = 0;
-  MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
+  MIPS_CUDA(record(idx, idx->ev[0], s));
   return MIPS_OK;
 }
 
 // Mark the end of a stage (stages run in enum order within one call).
 mips_status end_stage(mips_index_t idx, Stage st, cudaStream_t s) {
-  MIPS_CUDA(cudaEventRecord(idx->ev[1 + st], s));
+  MIPS_CUDA(record(idx, idx->ev[1 + st], s));
   if (!idx->stage_ran[st] && idx->n_order < kStages) idx->order[idx->n_order++] = st;
   idx->stage_ran[st] = true;
   idx->last_stage = st;
@@ -244,7 +271,9 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
 
 // C distinct user ids from a counter-based stream (SplitMix64 of seed and
 // counter), Floyd's method: the k-means initial centroids.
-void draw_init_ids(int64_t n, int C, uint64_t seed, std::vector<int64_t>& out) {
+// C distinct values of [0, n): Floyd's algorithm over SplitMix64 draws of a
+// counter keyed by the seed (the selector's user sample).
+void draw_distinct_host(int64_t n, int64_t C, uint64_t seed, std::vector<int64_t>& out) {
   auto mix = [](uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -285,6 +314,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   Arena& ws = idx->ws;
   ws.reset();
   size_t o_ids = ws.take(sizeof(int64_t) * C), o_cent = ws.take(sizeof(float) * C * f), o_hn2 = ws.take(sizeof(float) * C);
+  size_t o_bits = ws.take(sizeof(uint32_t) * ((n_users + 31) / 32));
   size_t o_assign = ws.take(sizeof(int32_t) * n_users), o_sums = ws.take(sizeof(unsigned long long) * C * f);
   size_t o_cnt = ws.take(sizeof(unsigned) * C), o_amax = ws.take(16), o_scale = ws.take(16);
   size_t o_cosb = ws.take(sizeof(uint32_t) * C), o_cosbf = ws.take(sizeof(float) * C);
@@ -350,10 +380,10 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   }
   MIPS_CUDA(ws.ensure(ws.used, s));
 
-  // k-means initial centroids: a seeded draw of C distinct users
-  std::vector<int64_t> ids;
-  draw_init_ids(n_users, C, idx->opt.seed, ids);
-  MIPS_CUDA(cudaMemcpyAsync(ws.at<int64_t>(o_ids), ids.data(), sizeof(int64_t) * C, cudaMemcpyHostToDevice, s));
+  // k-means initial centroids: a seeded draw of C distinct users (on the
+  // device, so that a captured call holds no host data)
+  MIPS_CUDA(draw_init_ids(n_users, C, idx->opt.seed, ws.at<uint32_t>(o_bits), ws.at<int64_t>(o_ids), s));
+  idx->launches += 1;
   mips_status st;
   MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids), ws.at<float>(o_cent),
                            ws.at<float>(o_hn2), ws.at<int32_t>(o_assign), ws.at<unsigned long long>(o_sums),
@@ -493,7 +523,7 @@ mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, in
   if (ns > n_users) ns = n_users;
   // seeded sample of distinct users, ascending; the rest, ascending
   std::vector<int64_t> pick;
-  draw_init_ids(n_users, (int)ns, idx->opt.seed ^ 0x5EEDull, pick);
+  draw_distinct_host(n_users, ns, idx->opt.seed ^ 0x5EEDull, pick);
   std::vector<char> in_sample((size_t)n_users, 0);
   for (int64_t v : pick) in_sample[v] = 1;
   std::vector<int32_t> sample, rest;
@@ -722,6 +752,93 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
   return end_call(idx, s);
 }
 
+mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_users, int K, int method,
+                            int32_t* out_idx_dev, double* out_score_dev, void* stream) {
+  g_err.clear();
+  mips_status st = check_call(idx, users_dev, n_users, K, out_idx_dev, out_score_dev);
+  if (st != MIPS_OK) return st;
+  if (method != 0 && method != 1) return fail(MIPS_ERR_ARG, "method must be 0 (blocked multiply) or 1 (Maximus)");
+  cudaStream_t s = (cudaStream_t)stream;
+  auto plain = [&]() {
+    return method == 0 ? mips_topk(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, stream)
+                       : mips_topk_maximus(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, stream);
+  };
+  if (s == nullptr) return plain();  // the legacy default stream cannot be captured
+  for (auto& g : idx->graphs) {
+    if (g.method != method || g.users != users_dev || g.n_users != n_users || g.K != K || g.out_idx != out_idx_dev ||
+        g.out_score != out_score_dev || g.ws_gen != idx->ws.gen)
+      continue;
+    if (idx->has_done) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
+    MIPS_CUDA(cudaGraphLaunch(g.exec, s));
+    for (int i = 0; i < kStages; ++i) {
+      idx->stage_ran[i] = g.stage_ran[i];
+      idx->order[i] = g.order[i];
+    }
+    idx->n_order = g.n_order;
+    idx->last_stage = g.last_stage;
+    idx->launches = g.launches;
+    idx->last_users = n_users;
+    idx->last_clusters = g.clusters;
+    idx->last_dtype = g.dtype;
+    return end_call(idx, s);
+  }
+  // first time for these arguments: a plain call (it also sizes the
+  // workspace), then the same call captured (not run) for later replays
+  if ((st = plain()) != MIPS_OK) return st;
+  const uint64_t gen = idx->ws.gen;
+  MIPS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  idx->capturing = true;
+  st = begin_call(idx, s);
+  if (st == MIPS_OK)
+    st = method == 0 ? run_bmm(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s)
+                     : run_maximus(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s);
+  idx->capturing = false;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (st != MIPS_OK || ec != cudaSuccess || idx->ws.gen != gen) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (st != MIPS_OK) return st;
+    if (ec != cudaSuccess) return cuda_fail(ec, "stream capture of the call");
+    return MIPS_OK;  // the workspace moved during capture: stay uncaptured
+  }
+  mips_index_s::Graph g;
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return cuda_fail(ei, "graph instantiation");
+  g.method = method;
+  g.users = users_dev;
+  g.n_users = n_users;
+  g.K = K;
+  g.out_idx = out_idx_dev;
+  g.out_score = out_score_dev;
+  g.ws_gen = gen;
+  for (int i = 0; i < kStages; ++i) {
+    g.stage_ran[i] = idx->stage_ran[i];
+    g.order[i] = idx->order[i];
+  }
+  g.n_order = idx->n_order;
+  g.last_stage = idx->last_stage;
+  g.launches = idx->launches;
+  g.clusters = idx->last_clusters;
+  g.dtype = idx->last_dtype;
+  // keep a few; drop those the workspace has outgrown first
+  for (size_t i = 0; i < idx->graphs.size();) {
+    if (idx->graphs[i].ws_gen != idx->ws.gen) {
+      cudaGraphExecDestroy(idx->graphs[i].exec);
+      idx->graphs.erase(idx->graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+  if (idx->graphs.size() >= 8) {
+    cudaGraphExecDestroy(idx->graphs.front().exec);
+    idx->graphs.erase(idx->graphs.begin());
+  }
+  idx->graphs.push_back(g);
+  return MIPS_OK;
+}
+
 mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_users, int K, int method,
                            int32_t* out_idx_host, double* out_score_host, void* stream) {
   g_err.clear();
@@ -850,6 +967,7 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
 void mips_free_index(mips_index_t idx) {
   if (!idx) return;
   if (idx->has_done) cudaEventSynchronize(idx->done);
+  for (auto& g : idx->graphs) cudaGraphExecDestroy(g.exec);
   if (idx->ws.base) cudaFree(idx->ws.base);
   if (idx->ws_sel.base) cudaFree(idx->ws_sel.base);
   cudaFree(idx->items);

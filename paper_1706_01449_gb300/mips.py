@@ -27,7 +27,7 @@ METHODS = {"bmm": 0, "maximus": 1, "select": 2}
 # every symbol include/mips.h declares
 EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_maximus",
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
-           "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc")
+           "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph")
 
 
 class MipsError(RuntimeError):
@@ -90,6 +90,8 @@ def load():
     lib.mips_select.restype = st
     lib.mips_topk_host.argtypes = [P, P, i64, i32, i32, P, P, P]
     lib.mips_topk_host.restype = st
+    lib.mips_topk_graph.argtypes = [P, P, i64, i32, i32, P, P, P]
+    lib.mips_topk_graph.restype = st
     lib.mips_sync.argtypes = [P, P]
     lib.mips_sync.restype = st
     lib.mips_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -202,6 +204,20 @@ def topk(index: Index, users, K: int, out_idx=None, out_score=None, stream=None)
 def topk_maximus(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
     """Maximus (mips_topk_maximus).  Asynchronous on the stream."""
     return _run(load().mips_topk_maximus, index, users, K, out_idx, out_score, stream)
+
+
+def topk_graph(index: Index, users, K: int, method: str = "bmm", out_idx=None, out_score=None, stream=None):
+    """mips_topk_graph: the blocked multiply ("bmm") or Maximus ("maximus")
+    captured into a CUDA graph on the first call with these buffers and
+    replayed afterwards.  Asynchronous on the stream."""
+    lib = load()
+    users = _dev_f32(users, "users")
+    out_idx, out_score = _outputs(users.shape[0], K, out_idx, out_score, users.device)
+    m = {"bmm": 0, "maximus": 1}[method]
+    _check(lib.mips_topk_graph(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0], K, m,
+                               ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
+                               _stream_ptr(stream)))
+    return out_idx, out_score
 
 
 def select(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
