@@ -3,10 +3,13 @@
 One step = one mips_topk call (the whole hot path: user quantisation,
 fused score + select, exact rescore) over all users of the workload, with
 users and items already resident in HBM.  Prints ONE JSON line (rank 0).
+The blocked multiply and Maximus steps go through mips_topk_graph on a
+created stream (the call is captured into a CUDA graph in the warm-up and
+replayed); --no-graph runs the plain calls.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|fp32]
                     [--method bmm|maximus|select] [--f 50] [--k 10]
-                    [--impl ours|reference]
+                    [--impl ours|reference] [--no-graph]
 
 Under torchrun (N > 1) every rank runs the same workload on its own users
 (seed = rank) with no collective on the data path: weak scaling; the time
@@ -48,6 +51,7 @@ def parse():
                    help="use only the first N users (profiling captures; not the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="plain calls instead of captured graphs")
     return p.parse_args()
 
 
@@ -243,13 +247,17 @@ def main():
     out_idx = torch.empty((nU, K), dtype=torch.int32, device=dev)
     out_sc = torch.empty((nU, K), dtype=torch.float64, device=dev)
     fn = {"bmm": mips.topk, "maximus": mips.topk_maximus}.get(args.method)
-    stream = torch.cuda.current_stream()
+    use_graph = args.method != "select" and not args.no_graph
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)  # torch work (flush, events) and the calls share it
 
     def step():
         if args.method == "select":
-            mips.select(index, U_d, K, out_idx, out_sc)
+            mips.select(index, U_d, K, out_idx, out_sc, stream=stream)
+        elif use_graph:
+            mips.topk_graph(index, U_d, K, args.method, out_idx, out_sc, stream=stream)
         else:
-            fn(index, U_d, K, out_idx, out_sc)
+            fn(index, U_d, K, out_idx, out_sc, stream=stream)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
@@ -352,6 +360,7 @@ def main():
         "config": {"workload": f"{args.workload} f={f} K={K}" + (f" first {nU} users" if args.users else ""),
                    "n_users": nU, "n_items": nI, "f": f, "K": K,
                    "method": args.method, "candidate_pass": dtype, "rescore": "compensated fp32 + fp64 tie check",
+                   "launch": "cuda graph replay" if use_graph else "plain calls",
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
