@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="plain calls instead of captured graphs")
+    p.add_argument("--autotune", action="store_true",
+                   help="Maximus / selector: pick |C| and B with mips_autotune before the warm-up (timed separately)")
     return p.parse_args()
 
 
@@ -259,6 +261,11 @@ def main():
         else:
             fn(index, U_d, K, out_idx, out_sc, stream=stream)
 
+    tune = None
+    if args.autotune and args.method != "bmm":
+        tune = mips.autotune(index, U_d, K, stream=stream)
+        tune = {"clusters": tune["clusters"], "block_items": tune["block_items"],
+                "sample_users": tune["sample_users"], "seconds": tune["t_tune"], "candidates": len(tune["tried"])}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -361,6 +368,8 @@ def main():
                    "n_users": nU, "n_items": nI, "f": f, "K": K,
                    "method": args.method, "candidate_pass": dtype, "rescore": "compensated fp32 + fp64 tie check",
                    "launch": "cuda graph replay" if use_graph else "plain calls",
+                   **({"clusters": stats["clusters"]} if args.method != "bmm" else {}),
+                   **({"autotune": tune} if tune else {}),
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -133,6 +133,33 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
                         int32_t* out_idx_dev, double* out_score_dev, void* stream,
                         mips_select_report* rep);
 
+/* Result of mips_autotune. */
+typedef struct {
+  int clusters;            /* chosen |C|, now the index's */
+  int block_items;         /* chosen item block B, now the index's */
+  int64_t sample_users;    /* users in the timed sample */
+  int n_tried;             /* candidates timed (at most 32) */
+  int tried_clusters[32];  /* |C| of candidate t (for all n_users) */
+  int tried_block[32];     /* B of candidate t */
+  double tried_est[32];    /* predicted seconds of candidate t for all n_users */
+  double t_tune;           /* seconds spent tuning (wall clock) */
+} mips_tune_report;
+
+/*
+ * Autotuner for Maximus: picks the cluster count |C| and the item block B
+ * (Sec. IV-A, IV-D) for these users by timing Maximus on a seeded user
+ * sample (n_users / 8 users, at least two waves of 128-user tiles per SM)
+ * for |C| in {16, ..., 1024} (at most n_users / 32) and B in {1024, 4096,
+ * 16384}.  The sample runs with |C| scaled by sample / n_users, so that it
+ * has the full run's users per cluster; the prediction for all users
+ * scales the sample's k-means and per-user stages by n_users / sample and
+ * k-means and the (cluster, item) bound and sort stages by the |C| ratio.
+ * The best pair becomes the index's (later Maximus calls use it).
+ * Synchronises the stream; rep may be NULL.  Errors as mips_topk.
+ */
+mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
+                          void* stream, mips_tune_report* rep);
+
 /*
  * mips_topk (method 0) or mips_topk_maximus (method 1) through a CUDA
  * graph: the first call with a given (method, users_dev, n_users, K,

@@ -1,6 +1,8 @@
 // The C ABI of libmips (declared in include/mips.h): argument checks, the
 // index object, its workspace arena, and the dispatch of each call to its
 // kernels.  No C++ exception crosses the boundary.
+#include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -750,6 +752,91 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
   if ((st = begin_call(idx, s)) != MIPS_OK) return st;
   if ((st = run_select(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s, rep)) != MIPS_OK) return st;
   return end_call(idx, s);
+}
+
+mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_users, int K, void* stream,
+                          mips_tune_report* rep) {
+  g_err.clear();
+  // (the outputs are the tuner's own buffers)
+  mips_status st = check_call(idx, users_dev, n_users, K, users_dev, users_dev);
+  if (st != MIPS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  // sample: n / 8 users, at least two waves of 128-user tiles on every SM
+  int64_t ns = n_users / 8;
+  if (ns < 2ll * idx->num_sms * 128) ns = 2ll * idx->num_sms * 128;
+  if (ns > n_users) ns = n_users;
+  std::vector<int64_t> pick;
+  draw_distinct_host(n_users, ns, idx->opt.seed ^ 0x7E57ull, pick);
+  std::sort(pick.begin(), pick.end());
+  std::vector<int32_t> sample(pick.begin(), pick.end());
+  const int f = idx->f;
+  Arena& w = idx->ws_sel;
+  w.reset();
+  size_t o_sid = w.take(4 * ns), o_su = w.take(sizeof(float) * ns * f);
+  size_t o_oi = w.take(4 * ns * K), o_os = w.take(8 * ns * K);
+  MIPS_CUDA(w.ensure(w.used, s));
+  MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_sid), sample.data(), 4 * ns, cudaMemcpyHostToDevice, s));
+  launch_gather_rows(users_dev, w.at<int32_t>(o_sid), ns, f, w.at<float>(o_su), s);
+  MIPS_CUDA(cudaGetLastError());
+  const int saved_c = idx->clusters, saved_b = idx->opt.block_items;
+  const double scale = (double)ns / (double)n_users;
+  struct Cand { int C, B; double est; };
+  std::vector<Cand> tried;
+  for (int C = 16; C <= 1024 && C <= n_users / 32; C *= 2) {
+    int Cs = (int)llround(C * scale);
+    if (Cs < 1) Cs = 1;
+    for (int B : {1024, 4096, 16384}) {
+      idx->clusters = Cs;
+      idx->opt.block_items = B;
+      double ms[kStages] = {};
+      for (int rep_i = 0; rep_i < 2 && st == MIPS_OK; ++rep_i) {  // the first run sizes the workspace
+        st = begin_call(idx, s);
+        if (st == MIPS_OK) st = run_maximus(idx, w.at<float>(o_su), ns, K, w.at<int32_t>(o_oi), w.at<double>(o_os), s);
+        if (st == MIPS_OK) st = end_call(idx, s);
+      }
+      if (st == MIPS_OK) st = mips_sync(idx, stream);
+      if (st != MIPS_OK) {
+        idx->clusters = saved_c;
+        idx->opt.block_items = saved_b;
+        return st;
+      }
+      cudaEvent_t prev = idx->ev[0];
+      float t = 0.f;
+      for (int q = 0; q < idx->n_order; ++q) {
+        const int i = idx->order[q];
+        MIPS_CUDA(cudaEventElapsedTime(&t, prev, idx->ev[1 + i]));
+        ms[i] = t;
+        prev = idx->ev[1 + i];
+      }
+      const double cr = (double)C / (double)Cs;
+      const double est_ms = (ms[ST_BOUNDS] + ms[ST_SORT]) * cr + ms[ST_KMEANS] * cr / scale +
+                            (ms[ST_PREP] + ms[ST_WALK] + ms[ST_RESCORE]) / scale;
+      tried.push_back({C, B, est_ms / 1e3});
+    }
+  }
+  Cand best{saved_c, saved_b, 0.0};
+  if (!tried.empty()) {
+    best = tried[0];
+    for (const Cand& c : tried)
+      if (c.est < best.est) best = c;
+  }
+  idx->clusters = best.C;
+  idx->opt.block_items = best.B;
+  if (rep) {
+    memset(rep, 0, sizeof(*rep));
+    rep->clusters = best.C;
+    rep->block_items = best.B;
+    rep->sample_users = ns;
+    rep->n_tried = (int)(tried.size() < 32 ? tried.size() : 32);
+    for (int i = 0; i < rep->n_tried; ++i) {
+      rep->tried_clusters[i] = tried[i].C;
+      rep->tried_block[i] = tried[i].B;
+      rep->tried_est[i] = tried[i].est;
+    }
+    rep->t_tune = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return MIPS_OK;
 }
 
 mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_users, int K, int method,

@@ -27,7 +27,8 @@ METHODS = {"bmm": 0, "maximus": 1, "select": 2}
 # every symbol include/mips.h declares
 EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_maximus",
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
-           "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph")
+           "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph",
+           "mips_autotune")
 
 
 class MipsError(RuntimeError):
@@ -48,6 +49,12 @@ class SelectReport(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("clusters", ctypes.c_int), ("block_items", ctypes.c_int), ("sample_users", ctypes.c_int64),
+                ("n_tried", ctypes.c_int), ("tried_clusters", ctypes.c_int * 32), ("tried_block", ctypes.c_int * 32),
+                ("tried_est", ctypes.c_double * 32), ("t_tune", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +99,8 @@ def load():
     lib.mips_topk_host.restype = st
     lib.mips_topk_graph.argtypes = [P, P, i64, i32, i32, P, P, P]
     lib.mips_topk_graph.restype = st
+    lib.mips_autotune.argtypes = [P, P, i64, i32, P, ctypes.POINTER(TuneReport)]
+    lib.mips_autotune.restype = st
     lib.mips_sync.argtypes = [P, P]
     lib.mips_sync.restype = st
     lib.mips_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -218,6 +227,20 @@ def topk_graph(index: Index, users, K: int, method: str = "bmm", out_idx=None, o
                                ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
                                _stream_ptr(stream)))
     return out_idx, out_score
+
+
+def autotune(index: Index, users, K: int, stream=None) -> dict:
+    """mips_autotune: choose |C| and B for Maximus on a user sample; the
+    choice becomes the index's.  Returns the report as a dict."""
+    lib = load()
+    users = _dev_f32(users, "users")
+    rep = TuneReport()
+    _check(lib.mips_autotune(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0], K,
+                             _stream_ptr(stream), ctypes.byref(rep)))
+    n = rep.n_tried
+    return {"clusters": rep.clusters, "block_items": rep.block_items, "sample_users": rep.sample_users,
+            "t_tune": rep.t_tune,
+            "tried": [(rep.tried_clusters[i], rep.tried_block[i], rep.tried_est[i]) for i in range(n)]}
 
 
 def select(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):

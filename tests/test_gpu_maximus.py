@@ -140,3 +140,23 @@ def test_maximus_kdd_shape_sampled():
     assert (idx == bidx).all()
     rows = synth.distinct_ids(U.shape[0], 256, 0, synth.S_SAMPLE)
     check_against_oracle(U, I, 10, idx, sc, rows=rows)
+
+
+def test_autotune_picks_a_tried_candidate_and_stays_exact():
+    """mips_autotune times Maximus on a user sample for |C| x B candidates;
+    its choice becomes the index's and the results stay exact."""
+    U, I = clustered(20000, 3000, 12, seed=21, n_dirs=16, noise=0.15)
+    index = mips.build_index(torch.from_numpy(I).cuda(), clusters=8, dtype="bf16")
+    Ud = torch.from_numpy(U).cuda()
+    rep = mips.autotune(index, Ud, 10)
+    assert rep["tried"], rep
+    cs = {c for c, _, _ in rep["tried"]}
+    assert max(cs) <= U.shape[0] // 32 and min(cs) >= 16
+    best = min(rep["tried"], key=lambda t: t[2])
+    assert (rep["clusters"], rep["block_items"]) == (best[0], best[1])
+    assert all(e > 0 for _, _, e in rep["tried"])
+    idx, sc = mips.topk_maximus(index, Ud, 10)
+    mips.sync(index)
+    assert mips.get_stats(index)["clusters"] == rep["clusters"]
+    check_against_oracle(U, I, 10, idx.cpu().numpy(), sc.cpu().numpy())
+    index.close()
