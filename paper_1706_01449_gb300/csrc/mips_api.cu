@@ -99,7 +99,8 @@ struct mips_index_s {
   void* items_bf16 = nullptr;  // [n_items_pad][fp]
   float2* item_aux = nullptr;  // {nhat_i, alpha_i}
   int64_t n_items_pad = 0;
-  CUtensorMap map_items;       // TMA map over items_bf16
+  CUtensorMap map_items;       // TMA maps over items_bf16: full chunks, tail chunk
+  CUtensorMap map_items_tail;
   int num_sms = 0;
   int max_smem = 0;
   // per-call state
@@ -252,12 +253,13 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     MIPS_CUDA(cudaGetLastError());
     idx->launches += 1;
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
-    CUtensorMap map_users;
-    if (!tc_make_map(&map_users, ub16, n_users, idx->fp, p.row_bytes, tc_users_per_tile()))
+    CUtensorMap map_users, map_users_tail;
+    if (!tc_make_maps(&map_users, &map_users_tail, ub16, n_users, p, tc_users_per_tile()))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the user operand");
     const int64_t n_ut = (n_users + tc_users_per_tile() - 1) / tc_users_per_tile();
     const int grid = (int)(n_ut < idx->num_sms ? n_ut : idx->num_sms);
-    MIPS_CUDA(launch_tc_score_select(&map_users, &idx->map_items, p, so, uaux, idx->item_aux, idx->stats_dev,
+    MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &idx->map_items, &idx->map_items_tail, p, so, uaux,
+                                     idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
     idx->launches += 1;
     if ((st = end_stage(idx, ST_SCORE, s)) != MIPS_OK) return st;
@@ -465,9 +467,9 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     idx->launches += 1;
     MIPS_CUDA(mx_tc_prepare(m, user_perm, idx->items_bf16, idx->item_aux, vals, s, &idx->launches));
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
-    CUtensorMap map_a, map_b;
-    if (!tc_make_map(&map_a, m.a_rows, n_rows_max, fp, p.row_bytes, tc_users_per_tile()) ||
-        !tc_make_map(&map_b, m.b_rows, C * n_pad, fp, p.row_bytes, tc_items_per_tile()))
+    CUtensorMap map_a, map_at, map_b, map_bt;
+    if (!tc_make_maps(&map_a, &map_at, m.a_rows, n_rows_max, p, tc_users_per_tile()) ||
+        !tc_make_maps(&map_b, &map_bt, m.b_rows, C * n_pad, p, tc_items_per_tile()))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Maximus operands");
     SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
                  ws.at<float>(o_topl), K <= kRegTopK ? 1 : 0, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
@@ -477,12 +479,14 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     const int64_t mw = max_work;
     p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
-    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), m.aux_c, idx->stats_dev,
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
+                                     idx->stats_dev,
                                      idx->err_dev, grid, s));
     MIPS_CUDA(mx_tc_pass2(m, ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), ws.at<float>(o_bounds), so, K,
                           &user_perm, ws.at<int32_t>(o_vis), idx->stats_dev, s, &idx->launches));
     p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c};
-    MIPS_CUDA(launch_tc_score_select(&map_a, &map_b, p, so, ws.at<float2>(o_uaux), m.aux_c, idx->stats_dev,
+    MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
+                                     idx->stats_dev,
                                      idx->err_dev, grid, s));
     idx->launches += 2;
     if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
@@ -708,7 +712,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
     p.f = f;
     p.K = 1;
     tc_plan(p, idx->max_smem);  // chunking only; calls whose tiling does not fit use the FP32 pass
-    if (!tc_make_map(&idx->map_items, idx->items_bf16, idx->n_items_pad, idx->fp, p.row_bytes, tc_items_per_tile()))
+    if (!tc_make_maps(&idx->map_items, &idx->map_items_tail, idx->items_bf16, idx->n_items_pad, p, tc_items_per_tile()))
       return bail(fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the item operand"));
   }
   BUILD_CUDA(cudaStreamSynchronize(s));

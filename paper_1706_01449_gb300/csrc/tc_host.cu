@@ -10,6 +10,8 @@ bool tc_plan(TcParams& p, int max_smem) {
   p.row_elems = p.row_bytes / 2;
   p.kc = p.fp / p.row_elems;
   p.swizzle = p.row_bytes == 32 ? 6 : (p.row_bytes == 64 ? 4 : 2);
+  p.tail_bytes = (p.fp - p.kc * p.row_elems) * 2;  // 0, 32 or 64 (tc_row_len)
+  p.tail_swizzle = p.tail_bytes == 32 ? 6 : 4;
   p.g = (float)(p.fp + 4) * 9.5367432e-07f + (float)p.f * 8.8817842e-16f;
   p.stages = 2;
   for (int st = kMaxStages; st >= 2; --st) {
@@ -37,6 +39,16 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 }  // namespace
+
+bool tc_make_maps(CUtensorMap* map, CUtensorMap* tail, const void* base, int64_t rows, const TcParams& p,
+                  int box_rows) {
+  if (!tc_make_map(map, base, rows, p.fp, p.row_bytes, box_rows)) return false;
+  if (p.tail_bytes == 0) {
+    *tail = *map;
+    return true;
+  }
+  return tc_make_map(tail, base, rows, p.fp, p.tail_bytes, box_rows);
+}
 
 bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows) {
   EncodeTiledFn enc = encode_fn();

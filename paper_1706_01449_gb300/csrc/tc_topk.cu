@@ -465,7 +465,8 @@ struct Smem {
 // otherwise every user tile against every item tile (blocked multiply).
 template <int KR, bool MX>
 __global__ void __launch_bounds__(kWarps * 32, 1)
-    tc_score_select_kernel(const __grid_constant__ CUtensorMap map_users, const __grid_constant__ CUtensorMap map_items,
+    tc_score_select_kernel(const __grid_constant__ CUtensorMap map_users, const __grid_constant__ CUtensorMap map_users_t,
+                           const __grid_constant__ CUtensorMap map_items, const __grid_constant__ CUtensorMap map_items_t,
                            TcParams p, SelectOut o, const float2* __restrict__ user_aux,
                            const float2* __restrict__ item_aux, DevStats* stats, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -473,9 +474,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_chunk = kTileM * p.row_bytes;  // one K chunk of the user tile
   const uint32_t b_chunk = kTileN * p.row_bytes;  // one K chunk of an item tile
-  unsigned char* a_tiles = base;                                              // [KC][a_chunk]
-  unsigned char* b_tiles = a_tiles + (size_t)p.kc * a_chunk;                  // [S][KC][b_chunk]
-  float* heap_base = (float*)(b_tiles + (size_t)p.stages * p.kc * b_chunk);   // [K][256] (KR = 0)
+  const uint32_t a_bytes = p.kc * a_chunk + kTileM * p.tail_bytes;  // user tile (full chunks, then the tail)
+  const uint32_t b_bytes = p.kc * b_chunk + kTileN * p.tail_bytes;  // one ring stage
+  unsigned char* a_tiles = base;                                              // [KC][a_chunk] + tail
+  unsigned char* b_tiles = a_tiles + a_bytes;                                 // [S]([KC][b_chunk] + tail)
+  float* heap_base = (float*)(b_tiles + (size_t)p.stages * b_bytes);          // [K][256] (KR = 0)
   float2* aux_base = (float2*)(heap_base + (KR > 0 ? 0 : (size_t)p.K * kEpiThreads));  // [8 warps][128]
   int32_t* posb_base = (int32_t*)(aux_base + (size_t)kEpiWarps * kHalfN);      // [8 warps][128]
   float* qh_base = (float*)(posb_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
@@ -527,19 +530,21 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_users)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_items)) : "memory");
+      const int tail_x = p.kc * p.row_elems;  // element column of the tail chunk
       long long g = 0;  // item tiles issued so far
       int st = 0;        // ring stage of tile g
       uint32_t ph = 0;   // ring pass parity of tile g
       int lt = 0;
       bool ok = true;
-      const uint32_t b_bytes = p.kc * b_chunk;
       for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
         const WorkItem wk = get_work<MX>(p, wi, n_it);
         if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
         if (!ok) break;
-        mbar_expect_tx(&ctl->a_full, p.kc * a_chunk);
+        mbar_expect_tx(&ctl->a_full, a_bytes);
         for (int c = 0; c < p.kc; ++c)
           tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full);
+        if (p.tail_bytes)
+          tma_load_2d(a_tiles + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full);
         for (int j = wk.tb; j < wk.te; ++j, ++g) {
           if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
           if (!ok) break;
@@ -548,6 +553,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           for (int c = 0; c < p.kc; ++c)
             tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, wk.b_row + j * kTileN,
                         &ctl->b_full[st]);
+          if (p.tail_bytes)
+            tma_load_2d(dst + (size_t)p.kc * b_chunk, &map_items_t, tail_x, wk.b_row + j * kTileN, &ctl->b_full[st]);
           if (++st == p.stages) {
             st = 0;
             ph ^= 1u;
@@ -577,7 +584,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       const uint64_t a_desc0 = smem_desc(smem_u32(a_tiles), sbo, p.swizzle);
       const uint64_t b_desc0 = smem_desc(smem_u32(b_tiles), sbo, p.swizzle);
       const uint32_t a16 = a_chunk >> 4, b16 = b_chunk >> 4;
-      const uint32_t stage16 = (p.kc * b_chunk) >> 4;
+      const uint32_t stage16 = b_bytes >> 4;
+      // the tail chunk: its own swizzle and row stride
+      const uint32_t tsbo = 8 * p.tail_bytes;
+      const int tsteps = p.tail_bytes / 32;
+      const uint64_t a_tdesc = smem_desc(smem_u32(a_tiles + (size_t)p.kc * a_chunk), tsbo, p.tail_swizzle);
+      const uint64_t b_tdesc0 = smem_desc(smem_u32(b_tiles + (size_t)p.kc * b_chunk), tsbo, p.tail_swizzle);
       long long g = 0;
       int st = 0;
       uint32_t ph = 0;   // ring pass parity
@@ -603,6 +615,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             for (int k = 0; k < ksteps; ++k)
               mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (c | k) != 0);
           }
+          const uint64_t btd = b_tdesc0 + (uint64_t)(st * stage16);
+          for (int k = 0; k < tsteps; ++k)
+            mma_bf16(d, a_tdesc + (uint64_t)(2 * k), btd + (uint64_t)(2 * k), idesc, 1u);
           mma_commit(&ctl->b_empty[st]);
           mma_commit(&ctl->acc_full[b]);
           if (++st == p.stages) {
@@ -788,7 +803,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 size_t tc_smem_bytes(const TcParams& p) {
   const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = (size_t)kTileN * p.row_bytes;
   const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
-  return 1024 + (size_t)p.kc * a_chunk + (size_t)p.stages * p.kc * b_chunk + heap +
+  const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
+  const size_t b_bytes = (size_t)p.kc * b_chunk + (size_t)kTileN * p.tail_bytes;
+  return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +
          (sizeof(float2) + sizeof(int32_t)) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
          (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
@@ -800,20 +817,21 @@ int tc_items_per_tile() { return kTileN; }
 namespace {
 
 template <int KR, bool MX>
-cudaError_t launch_variant(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p, SelectOut o,
-                           const float2* user_aux, const float2* item_aux, DevStats* stats, int* err, int grid,
-                           size_t smem, cudaStream_t s) {
+cudaError_t launch_variant(const CUtensorMap* mu, const CUtensorMap* mut, const CUtensorMap* mi, const CUtensorMap* mit,
+                           const TcParams& p, SelectOut o, const float2* user_aux, const float2* item_aux,
+                           DevStats* stats, int* err, int grid, size_t smem, cudaStream_t s) {
   cudaError_t e =
       cudaFuncSetAttribute(tc_score_select_kernel<KR, MX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tc_score_select_kernel<KR, MX><<<grid, kWarps * 32, smem, s>>>(*map_users, *map_items, p, o, user_aux, item_aux,
+  tc_score_select_kernel<KR, MX><<<grid, kWarps * 32, smem, s>>>(*mu, *mut, *mi, *mit, p, o, user_aux, item_aux,
                                                                  stats, err);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p,
+cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_users_tail,
+                                   const CUtensorMap* map_items, const CUtensorMap* map_items_tail, const TcParams& p,
                                    SelectOut o, const float2* user_aux, const float2* item_aux, DevStats* stats,
                                    int* err, int grid, cudaStream_t s) {
   // at least half the SM's shared memory: one CTA per SM, so no two CTAs
@@ -825,9 +843,11 @@ cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorM
   if (smem < (size_t)max_smem / 2 + 1024) smem = (size_t)max_smem / 2 + 1024;
   const bool mx = p.mode != 0;
   // register top-K sized to K: the insertion cost grows with the array
-#define MIPS_TC_LAUNCH(KR)                                                                                        \
-  return mx ? launch_variant<KR, true>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s) \
-            : launch_variant<KR, false>(map_users, map_items, p, o, user_aux, item_aux, stats, err, grid, smem, s)
+#define MIPS_TC_LAUNCH(KR)                                                                                       \
+  return mx ? launch_variant<KR, true>(map_users, map_users_tail, map_items, map_items_tail, p, o, user_aux,   \
+                                       item_aux, stats, err, grid, smem, s)                                    \
+            : launch_variant<KR, false>(map_users, map_users_tail, map_items, map_items_tail, p, o, user_aux,  \
+                                        item_aux, stats, err, grid, smem, s)
   if (p.K == 1) MIPS_TC_LAUNCH(1);
   if (p.K <= 10) MIPS_TC_LAUNCH(10);
   if (p.K <= kRegTopK) MIPS_TC_LAUNCH(kRegTopK);

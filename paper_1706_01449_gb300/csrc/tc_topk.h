@@ -28,10 +28,12 @@ struct TcWork {
 struct TcParams {
   int64_t n_users, n_items;
   int f, fp, K;
-  int kc;         // K chunks per operand row (fp / row_elems)
-  int row_bytes;  // bytes of one chunk row: 32, 64 or 128 (= swizzle span)
-  int row_elems;  // BF16 elements of one chunk row
+  int kc;         // full K chunks per operand row
+  int row_bytes;  // bytes of one full chunk row: 32, 64 or 128 (= swizzle span)
+  int row_elems;  // BF16 elements of one full chunk row
   int swizzle;    // tcgen05 descriptor layout code: 6 = 32B, 4 = 64B, 2 = 128B
+  int tail_bytes;    // a last, narrower chunk after kc 128-byte ones: 0, 32 or 64 bytes
+  int tail_swizzle;  // its layout code (6 or 4)
   int stages;     // item-tile ring depth
   float g;
   int mode;       // 0: blocked multiply, 1: work list
@@ -39,12 +41,18 @@ struct TcParams {
 };
 
 // Operand row length (BF16 elements) for dimension f: f + 2 bound columns,
-// padded to 16, 32 or a multiple of 64 (one swizzle span per chunk).
+// padded to 16, 32 or 64, or above 64 to whole 64-element chunks plus a
+// 16- or 32-element tail chunk when that covers the rest (f = 128: 128 + 16).
 inline int tc_row_len(int f) {
-  int n = f + 2;
+  const int n = f + 2;
   if (n <= 16) return 16;
   if (n <= 32) return 32;
-  return (int)round_up(n, 64);
+  if (n <= 64) return 64;
+  const int full = n / 64 * 64, rem = n - full;
+  if (rem == 0) return full;
+  if (rem <= 16) return full + 16;
+  if (rem <= 32) return full + 32;
+  return full + 64;
 }
 
 // Fill chunking, swizzle and stages for this problem so the shared memory
@@ -52,12 +60,18 @@ inline int tc_row_len(int f) {
 bool tc_plan(TcParams& p, int max_smem);
 size_t tc_smem_bytes(const TcParams& p);
 
-// K-major BF16 operand map [rows][fp], boxes of row_elems x box_rows rows.
+// K-major BF16 operand map [rows][fp], boxes of row_bytes / 2 elements x
+// box_rows rows, swizzled by row_bytes (32, 64 or 128).
 bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows);
+// The full-chunk map and, when p.tail_bytes > 0, the tail-chunk map (else a
+// copy of the first) of one operand.
+bool tc_make_maps(CUtensorMap* map, CUtensorMap* tail, const void* base, int64_t rows, const TcParams& p,
+                  int box_rows);
 int tc_users_per_tile();  // rows of a user tile (MMA M)
 int tc_items_per_tile();  // rows of an item tile (MMA N)
 
-cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_items, const TcParams& p,
+cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_users_tail,
+                                   const CUtensorMap* map_items, const CUtensorMap* map_items_tail, const TcParams& p,
                                    SelectOut o, const float2* user_aux, const float2* item_aux, DevStats* stats,
                                    int* err, int grid, cudaStream_t s);
 

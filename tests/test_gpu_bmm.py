@@ -56,6 +56,24 @@ def test_ragged_shapes(dtype, nU, nI, f, K):
     check_against_oracle(U, I, K, idx, sc)
 
 
+@pytest.mark.parametrize("f,K", [(63, 10), (64, 1), (78, 16), (80, 10), (94, 5)])
+def test_tail_chunk_rows(f, K):
+    """Operand rows of 64 + 16 or 64 + 32 BF16 elements (f + 2 = 65..96):
+    one 128-byte swizzled chunk plus a 32- or 64-byte tail chunk with its
+    own tensor map and swizzle; the tensor-core path must be the one used."""
+    U = synth.gaussian_rows(700, f, 9, synth.S_USERS, synth.S_USER_NORMS, (0.0, 0.3))
+    I = synth.gaussian_rows(3000, f, 9, synth.S_ITEMS, synth.S_ITEM_NORMS, (0.0, 0.5))
+    idx, sc, st = run_topk(U, I, K, "bf16")
+    assert st["dtype"] == 1, "BF16 tensor-core path not taken"
+    check_against_oracle(U, I, K, idx, sc)
+    index = mips.build_index(torch.from_numpy(I).cuda(), clusters=4, dtype="bf16")
+    mi, ms = mips.topk_maximus(index, torch.from_numpy(U).cuda(), K)
+    mips.sync(index)
+    assert mips.get_stats(index)["dtype"] == 1
+    index.close()
+    check_against_oracle(U, I, K, mi.cpu().numpy(), ms.cpu().numpy())
+
+
 @pytest.mark.parametrize("dtype", DTYPES)
 def test_ties_duplicates_zero_users(dtype):
     rng = np.random.default_rng(0)
