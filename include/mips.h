@@ -179,6 +179,65 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
                             void* stream);
 
 /*
+ * Serving: a request loop over one index with continuous batching.
+ * Requests (host user rows, any K) queue in arrival order; a scheduler
+ * thread forms a batch from the oldest request and the requests after it
+ * whose K falls in the same class (1; 2..10; 11..32; 33..128), up to
+ * max_batch_users users, runs it with the batch's largest K (each request
+ * keeps its own first K: the ranking is a strict order, so its top-K is the
+ * prefix of a larger K's) and starts it as soon as one of `slots` stream
+ * slots is free and the batch fits the memory budget next to the batches in
+ * flight.  Each slot owns a worker handle of the index (shared item arrays,
+ * own workspace), pinned staging and a stream, so batches overlap: one's
+ * copies and rescore with another's score kernel.  A completion thread
+ * scatters each batch's results to its requests' host buffers.  Results
+ * are those of mips_topk / mips_topk_maximus on the request alone
+ * (exact, so independent of the batch).  No counterpart in the paper,
+ * which scores offline batches (Sec. III-B); this is the serving form of
+ * its user batching.
+ */
+typedef struct mips_server_s* mips_server_t;
+
+typedef struct {
+  int method;              /* 0 = blocked multiply (mips_topk), 1 = Maximus */
+  int slots;               /* batches in flight at once (1..8), one stream each */
+  int64_t max_batch_users; /* users per batch; a larger request runs alone */
+  int64_t mem_budget;      /* device bytes the batches in flight may hold (0 = unlimited) */
+} mips_server_options;
+
+typedef struct {
+  double t_submit;      /* seconds since the server started */
+  double t_start;       /* its batch was launched */
+  double t_done;        /* its results were in its host buffers */
+  int64_t batch;        /* id of the batch that served it */
+  int64_t batch_users;  /* users in that batch */
+  int batch_K;          /* K the batch ran with */
+  int slot;             /* stream slot of the batch */
+} mips_request_info;
+
+/* Creates the server (its threads, streams, worker handles).  The index
+ * must outlive the server.  opt NULL: method 0, 2 slots, 8192 users, no
+ * budget.  Errors: MIPS_ERR_ARG (bad options), MIPS_ERR_CUDA/NOMEM. */
+mips_status mips_server_create(mips_index_t idx, const mips_server_options* opt, mips_server_t* out);
+
+/* Queues a request: users_host [n_users][f] float; results to
+ * out_idx_host / out_score_host [n_users][K].  The three host buffers
+ * must stay valid until mips_server_wait returns for the request.
+ * Returns at once; *request_id identifies it.  Errors: MIPS_ERR_ARG (K out
+ * of [1, min(n_items, 128)], n_users < 1, null pointers, server stopped). */
+mips_status mips_server_submit(mips_server_t srv, const float* users_host, int64_t n_users, int K,
+                               int32_t* out_idx_host, double* out_score_host, int64_t* request_id);
+
+/* Waits until the request is done or timeout_s passes (MIPS_ERR_TIMEOUT;
+ * the request stays queued).  info may be NULL.  A failed batch reports its
+ * error to each of its requests. */
+mips_status mips_server_wait(mips_server_t srv, int64_t request_id, double timeout_s, mips_request_info* info);
+
+/* Finishes the queued and running requests, stops the threads and frees
+ * the server's resources. */
+mips_status mips_server_destroy(mips_server_t srv);
+
+/*
  * Host-memory variant of mips_topk (method 0) / mips_topk_maximus
  * (method 1) / mips_select (method 2): copies users_host to the device,
  * runs the method and copies the results back, all on `stream`, then

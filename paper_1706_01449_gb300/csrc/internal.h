@@ -173,6 +173,11 @@ cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_b
 cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, const float* bounds, SelectOut o, int K,
                         int32_t** user_perm, int32_t* visited, DevStats* stats, cudaStream_t s, int* launches);
 
+// Worker handle sharing an index's item arrays (own workspace and events).
+mips_index_t index_worker_clone(mips_index_t src);
+int index_f(mips_index_t idx);
+int64_t index_n_items(mips_index_t idx);
+
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);
 

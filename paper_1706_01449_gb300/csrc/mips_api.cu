@@ -136,6 +136,7 @@ struct mips_index_s {
   // captured calls (mips_topk_graph): replayed while the arguments and the
   // workspace are the same
   bool capturing = false;
+  bool shares_items = false;  // a worker of another index: item arrays not owned
   struct Graph {
     int method = 0;
     const float* users = nullptr;
@@ -617,6 +618,44 @@ mips_status check_call(mips_index_t idx, const void* users, int64_t n_users, int
 
 }  // namespace
 
+// A worker handle of an index for concurrent calls on other streams: the
+// same (read-only) item arrays and tensor maps, its own workspace, error
+// flag, counters and events.  Freed with mips_free_index, which leaves the
+// shared item arrays to their owner.
+mips_index_t mips::index_worker_clone(mips_index_t src) {
+  mips_index_s* w = new (std::nothrow) mips_index_s();
+  if (!w) return nullptr;
+  w->device = src->device;
+  w->f = src->f;
+  w->n_items = src->n_items;
+  w->clusters = src->clusters;
+  w->opt = src->opt;
+  w->items = src->items;
+  w->perm = src->perm;
+  w->item_nrm = src->item_nrm;
+  w->fp = src->fp;
+  w->items_bf16 = src->items_bf16;
+  w->item_aux = src->item_aux;
+  w->n_items_pad = src->n_items_pad;
+  w->map_items = src->map_items;
+  w->map_items_tail = src->map_items_tail;
+  w->num_sms = src->num_sms;
+  w->max_smem = src->max_smem;
+  w->shares_items = true;
+  bool ok = cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i <= kStages && ok; ++i) ok = cudaEventCreate(&w->ev[i]) == cudaSuccess;
+  ok = ok && cudaMalloc(&w->err_dev, sizeof(int)) == cudaSuccess && cudaMemset(w->err_dev, 0, sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&w->stats_dev, sizeof(DevStats)) == cudaSuccess;
+  if (!ok) {
+    mips_free_index(w);
+    return nullptr;
+  }
+  return w;
+}
+
+int mips::index_f(mips_index_t idx) { return idx->f; }
+int64_t mips::index_n_items(mips_index_t idx) { return idx->n_items; }
+
 extern "C" {
 
 int mips_version(void) { return 100; }
@@ -1061,11 +1100,13 @@ void mips_free_index(mips_index_t idx) {
   for (auto& g : idx->graphs) cudaGraphExecDestroy(g.exec);
   if (idx->ws.base) cudaFree(idx->ws.base);
   if (idx->ws_sel.base) cudaFree(idx->ws_sel.base);
-  cudaFree(idx->items);
-  cudaFree(idx->perm);
-  cudaFree(idx->item_nrm);
-  cudaFree(idx->items_bf16);
-  cudaFree(idx->item_aux);
+  if (!idx->shares_items) {
+    cudaFree(idx->items);
+    cudaFree(idx->perm);
+    cudaFree(idx->item_nrm);
+    cudaFree(idx->items_bf16);
+    cudaFree(idx->item_aux);
+  }
   cudaFree(idx->err_dev);
   cudaFree(idx->stats_dev);
   if (idx->done) cudaEventDestroy(idx->done);

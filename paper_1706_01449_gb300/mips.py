@@ -28,7 +28,8 @@ METHODS = {"bmm": 0, "maximus": 1, "select": 2}
 EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_maximus",
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
            "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph",
-           "mips_autotune")
+           "mips_autotune", "mips_server_create", "mips_server_submit", "mips_server_wait",
+           "mips_server_destroy")
 
 
 class MipsError(RuntimeError):
@@ -55,6 +56,17 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("clusters", ctypes.c_int), ("block_items", ctypes.c_int), ("sample_users", ctypes.c_int64),
                 ("n_tried", ctypes.c_int), ("tried_clusters", ctypes.c_int * 32), ("tried_block", ctypes.c_int * 32),
                 ("tried_est", ctypes.c_double * 32), ("t_tune", ctypes.c_double)]
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("slots", ctypes.c_int), ("max_batch_users", ctypes.c_int64),
+                ("mem_budget", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("batch", ctypes.c_int64), ("batch_users", ctypes.c_int64), ("batch_K", ctypes.c_int),
+                ("slot", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -101,6 +113,14 @@ def load():
     lib.mips_topk_graph.restype = st
     lib.mips_autotune.argtypes = [P, P, i64, i32, P, ctypes.POINTER(TuneReport)]
     lib.mips_autotune.restype = st
+    lib.mips_server_create.argtypes = [P, ctypes.POINTER(ServerOptions), ctypes.POINTER(P)]
+    lib.mips_server_create.restype = st
+    lib.mips_server_submit.argtypes = [P, P, i64, i32, P, P, ctypes.POINTER(i64)]
+    lib.mips_server_submit.restype = st
+    lib.mips_server_wait.argtypes = [P, i64, ctypes.c_double, ctypes.POINTER(RequestInfo)]
+    lib.mips_server_wait.restype = st
+    lib.mips_server_destroy.argtypes = [P]
+    lib.mips_server_destroy.restype = st
     lib.mips_sync.argtypes = [P, P]
     lib.mips_sync.restype = st
     lib.mips_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -323,3 +343,53 @@ def topk_noalloc(items, users, K: int, out_idx, out_score, stream=None):
 
 def free_index(index: Index):
     index.close()
+
+
+class Server:
+    """Request loop with continuous batching (mips_server_*): submit host
+    user rows with any K, wait for each request's results.  The index must
+    outlive the server."""
+
+    def __init__(self, index: Index, method: str = "bmm", slots: int = 2, max_batch_users: int = 8192,
+                 mem_budget: int = 0):
+        lib = load()
+        opt = ServerOptions({"bmm": 0, "maximus": 1}[method], slots, max_batch_users, mem_budget)
+        h = ctypes.c_void_p()
+        _check(lib.mips_server_create(index.handle, ctypes.byref(opt), ctypes.byref(h)))
+        self._h, self._index, self._live = h, index, {}
+
+    def submit(self, users, K: int) -> int:
+        """users: numpy float32 [n, f] (copied to a C-contiguous array kept
+        alive until wait).  Returns the request id."""
+        import numpy as np
+        u = np.ascontiguousarray(users, dtype=np.float32)
+        if u.ndim != 2 or u.shape[1] != self._index.f:
+            raise TypeError(f"users must be [n, {self._index.f}] float32")
+        oi = np.empty((u.shape[0], K), dtype=np.int32)
+        osc = np.empty((u.shape[0], K), dtype=np.float64)
+        rid = ctypes.c_int64()
+        _check(load().mips_server_submit(self._h, u.ctypes.data, u.shape[0], K, oi.ctypes.data, osc.ctypes.data,
+                                         ctypes.byref(rid)))
+        self._live[rid.value] = (u, oi, osc)
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 60.0):
+        """Returns (idx, score, info dict) of the request."""
+        info = RequestInfo()
+        st = load().mips_server_wait(self._h, rid, timeout, ctypes.byref(info))
+        if st == MIPS_ERR_TIMEOUT:
+            raise TimeoutError(last_error())
+        _check(st)
+        u, oi, osc = self._live.pop(rid)
+        return oi, osc, {k: getattr(info, k) for k, _ in RequestInfo._fields_}
+
+    def close(self):
+        if self._h is not None:
+            _check(load().mips_server_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -54,6 +54,15 @@ def test_argument_errors_need_no_gpu():
     assert lib.mips_topk_maximus(None, fake, 4, 1, fake, fake, None) == mips.MIPS_ERR_ARG
     assert lib.mips_select(None, fake, 4, 1, fake, fake, None, None) == mips.MIPS_ERR_ARG
     assert lib.mips_sync(None, None) == mips.MIPS_ERR_ARG
+    assert lib.mips_topk_graph(None, fake, 4, 1, 0, fake, fake, None) == mips.MIPS_ERR_ARG
+    assert lib.mips_autotune(None, fake, 4, 1, None, None) == mips.MIPS_ERR_ARG
+    srv = ctypes.c_void_p()
+    sopt = mips.ServerOptions(0, 2, 1024, 0)
+    assert lib.mips_server_create(None, ctypes.byref(sopt), ctypes.byref(srv)) == mips.MIPS_ERR_ARG
+    rid = ctypes.c_int64()
+    assert lib.mips_server_submit(None, fake, 1, 1, fake, fake, ctypes.byref(rid)) == mips.MIPS_ERR_ARG
+    assert lib.mips_server_wait(None, 0, 0.0, None) == mips.MIPS_ERR_ARG
+    assert lib.mips_server_destroy(None) == mips.MIPS_OK
     lib.mips_free_index(None)
 
 
