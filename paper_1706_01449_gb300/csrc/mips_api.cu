@@ -99,8 +99,6 @@ struct mips_index_s {
   void* items_bf16 = nullptr;  // [n_items_pad][fp]
   float2* item_aux = nullptr;  // {nhat_i, alpha_i}
   int64_t n_items_pad = 0;
-  CUtensorMap map_items;       // TMA maps over items_bf16: full chunks, tail chunk
-  CUtensorMap map_items_tail;
   int num_sms = 0;
   int max_smem = 0;
   // per-call state
@@ -254,12 +252,14 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     MIPS_CUDA(cudaGetLastError());
     idx->launches += 1;
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
-    CUtensorMap map_users, map_users_tail;
-    if (!tc_make_maps(&map_users, &map_users_tail, ub16, n_users, p, tc_users_per_tile()))
-      return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the user operand");
+    // (the item maps depend on the call's plan: whole or half tiles per load)
+    CUtensorMap map_users, map_users_tail, map_items, map_items_tail;
+    if (!tc_make_maps(&map_users, &map_users_tail, ub16, n_users, p, tc_users_per_tile()) ||
+        !tc_make_maps(&map_items, &map_items_tail, idx->items_bf16, idx->n_items_pad, p, tc_items_box(p)))
+      return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operands");
     const int64_t n_ut = (n_users + tc_users_per_tile() - 1) / tc_users_per_tile();
     const int grid = (int)(n_ut < idx->num_sms ? n_ut : idx->num_sms);
-    MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &idx->map_items, &idx->map_items_tail, p, so, uaux,
+    MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &map_items, &map_items_tail, p, so, uaux,
                                      idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
     idx->launches += 1;
@@ -470,7 +470,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
     CUtensorMap map_a, map_at, map_b, map_bt;
     if (!tc_make_maps(&map_a, &map_at, m.a_rows, n_rows_max, p, tc_users_per_tile()) ||
-        !tc_make_maps(&map_b, &map_bt, m.b_rows, C * n_pad, p, tc_items_per_tile()))
+        !tc_make_maps(&map_b, &map_bt, m.b_rows, C * n_pad, p, tc_items_box(p)))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Maximus operands");
     SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
                  ws.at<float>(o_topl), K <= kRegTopK ? 1 : 0, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
@@ -637,8 +637,6 @@ mips_index_t mips::index_worker_clone(mips_index_t src) {
   w->items_bf16 = src->items_bf16;
   w->item_aux = src->item_aux;
   w->n_items_pad = src->n_items_pad;
-  w->map_items = src->map_items;
-  w->map_items_tail = src->map_items_tail;
   w->num_sms = src->num_sms;
   w->max_smem = src->max_smem;
   w->shares_items = true;
@@ -746,13 +744,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
     launch_quant_bf16(idx->items, n_items, f, idx->fp, 1, idx->items_bf16, idx->n_items_pad, idx->item_aux,
                       idx->err_dev, s);
     BUILD_CUDA(cudaGetLastError());
-    TcParams p{};
-    p.fp = idx->fp;
-    p.f = f;
-    p.K = 1;
-    tc_plan(p, idx->max_smem);  // chunking only; calls whose tiling does not fit use the FP32 pass
-    if (!tc_make_maps(&idx->map_items, &idx->map_items_tail, idx->items_bf16, idx->n_items_pad, p, tc_items_per_tile()))
-      return bail(fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the item operand"));
+    // (tensor maps are made per call: the plan depends on K)
   }
   BUILD_CUDA(cudaStreamSynchronize(s));
   int herr = 0;

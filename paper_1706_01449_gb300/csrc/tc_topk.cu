@@ -473,9 +473,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   // 1024-byte aligned carve-up (sizes in tc_smem_bytes)
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_chunk = kTileM * p.row_bytes;  // one K chunk of the user tile
-  const uint32_t b_chunk = kTileN * p.row_bytes;  // one K chunk of an item tile
+  const int bs = p.b_split;                        // loads (ring stages) per item tile
+  const uint32_t sub_rows = kTileN / bs;          // item rows per load
+  const uint32_t b_chunk = sub_rows * p.row_bytes;  // one K chunk of a load
   const uint32_t a_bytes = p.kc * a_chunk + kTileM * p.tail_bytes;  // user tile (full chunks, then the tail)
-  const uint32_t b_bytes = p.kc * b_chunk + kTileN * p.tail_bytes;  // one ring stage
+  const uint32_t b_bytes = p.kc * b_chunk + sub_rows * p.tail_bytes;  // one ring stage
   unsigned char* a_tiles = base;                                              // [KC][a_chunk] + tail
   unsigned char* b_tiles = a_tiles + a_bytes;                                 // [S]([KC][b_chunk] + tail)
   float* heap_base = (float*)(b_tiles + (size_t)p.stages * b_bytes);          // [K][256] (KR = 0)
@@ -545,19 +547,20 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full);
         if (p.tail_bytes)
           tma_load_2d(a_tiles + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full);
-        for (int j = wk.tb; j < wk.te; ++j, ++g) {
-          if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
-          if (!ok) break;
-          mbar_expect_tx(&ctl->b_full[st], b_bytes);
-          unsigned char* dst = b_tiles + (size_t)st * b_bytes;
-          for (int c = 0; c < p.kc; ++c)
-            tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, wk.b_row + j * kTileN,
-                        &ctl->b_full[st]);
-          if (p.tail_bytes)
-            tma_load_2d(dst + (size_t)p.kc * b_chunk, &map_items_t, tail_x, wk.b_row + j * kTileN, &ctl->b_full[st]);
-          if (++st == p.stages) {
-            st = 0;
-            ph ^= 1u;
+        for (int j = wk.tb; j < wk.te && ok; ++j) {
+          for (int h = 0; h < bs; ++h, ++g) {  // g: loads issued so far
+            if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
+            if (!ok) break;
+            mbar_expect_tx(&ctl->b_full[st], b_bytes);
+            unsigned char* dst = b_tiles + (size_t)st * b_bytes;
+            const int y = wk.b_row + j * kTileN + h * (int)sub_rows;
+            for (int c = 0; c < p.kc; ++c)
+              tma_load_2d(dst + (size_t)c * b_chunk, &map_items, c * p.row_elems, y, &ctl->b_full[st]);
+            if (p.tail_bytes) tma_load_2d(dst + (size_t)p.kc * b_chunk, &map_items_t, tail_x, y, &ctl->b_full[st]);
+            if (++st == p.stages) {
+              st = 0;
+              ph ^= 1u;
+            }
           }
         }
       }
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       // instruction descriptor: D = F32, A = B = BF16, both K-major, N, M
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTileN >> 3) << 17) |
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(sub_rows >> 3) << 17) |
                              ((uint32_t)(kTileM >> 4) << 24);
       const uint32_t sbo = 8 * p.row_bytes;
       const int ksteps = p.row_bytes / 32;  // K = 16 BF16 = 32 bytes per MMA
@@ -602,28 +605,32 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         ok = mbar_wait(&ctl->a_full, lt & 1, abort_flag, err);
         if (!ok) break;
         tc_fence_after();
-        for (int j = wk.tb; j < wk.te; ++j, ++g) {
-          ok = mbar_wait(&ctl->b_full[st], ph, abort_flag, err);
-          if (ok && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, abort_flag, err);
+        for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
+          for (int h = 0; h < bs && ok; ++h) {
+            ok = mbar_wait(&ctl->b_full[st], ph, abort_flag, err);
+            if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, abort_flag, err);
+            if (!ok) break;
+            tc_fence_after();
+            // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
+            const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
+            const uint64_t bst = b_desc0 + (uint64_t)(st * stage16);
+            for (int c = 0; c < p.kc; ++c) {
+              const uint64_t ad = a_desc0 + (uint64_t)(c * a16);
+              const uint64_t bd = bst + (uint64_t)(c * b16);
+              for (int k = 0; k < ksteps; ++k)
+                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (c | k) != 0);
+            }
+            const uint64_t btd = b_tdesc0 + (uint64_t)(st * stage16);
+            for (int k = 0; k < tsteps; ++k)
+              mma_bf16(d, a_tdesc + (uint64_t)(2 * k), btd + (uint64_t)(2 * k), idesc, 1u);
+            mma_commit(&ctl->b_empty[st]);
+            if (++st == p.stages) {
+              st = 0;
+              ph ^= 1u;
+            }
+          }
           if (!ok) break;
-          tc_fence_after();
-          const uint32_t d = tmem + (uint32_t)(b * kTileN);
-          const uint64_t bst = b_desc0 + (uint64_t)(st * stage16);
-          for (int c = 0; c < p.kc; ++c) {
-            const uint64_t ad = a_desc0 + (uint64_t)(c * a16);
-            const uint64_t bd = bst + (uint64_t)(c * b16);
-            for (int k = 0; k < ksteps; ++k)
-              mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (c | k) != 0);
-          }
-          const uint64_t btd = b_tdesc0 + (uint64_t)(st * stage16);
-          for (int k = 0; k < tsteps; ++k)
-            mma_bf16(d, a_tdesc + (uint64_t)(2 * k), btd + (uint64_t)(2 * k), idesc, 1u);
-          mma_commit(&ctl->b_empty[st]);
           mma_commit(&ctl->acc_full[b]);
-          if (++st == p.stages) {
-            st = 0;
-            ph ^= 1u;
-          }
           b ^= 1;
           if (b == 0) aph ^= 1u;
         }
@@ -801,10 +808,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 }  // namespace
 
 size_t tc_smem_bytes(const TcParams& p) {
-  const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = (size_t)kTileN * p.row_bytes;
+  const size_t sub_rows = kTileN / (p.b_split > 0 ? p.b_split : 1);
+  const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = sub_rows * p.row_bytes;
   const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
   const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
-  const size_t b_bytes = (size_t)p.kc * b_chunk + (size_t)kTileN * p.tail_bytes;
+  const size_t b_bytes = (size_t)p.kc * b_chunk + sub_rows * p.tail_bytes;
   return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +
          (sizeof(float2) + sizeof(int32_t)) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
@@ -813,6 +821,7 @@ size_t tc_smem_bytes(const TcParams& p) {
 
 int tc_users_per_tile() { return kTileM; }
 int tc_items_per_tile() { return kTileN; }
+int tc_items_box(const TcParams& p) { return kTileN / (p.b_split > 0 ? p.b_split : 1); }
 
 namespace {
 

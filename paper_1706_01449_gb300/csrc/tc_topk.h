@@ -34,6 +34,8 @@ struct TcParams {
   int swizzle;    // tcgen05 descriptor layout code: 6 = 32B, 4 = 64B, 2 = 128B
   int tail_bytes;    // a last, narrower chunk after kc 128-byte ones: 0, 32 or 64 bytes
   int tail_swizzle;  // its layout code (6 or 4)
+  int b_split;       // 1, or 2: an item tile is loaded and multiplied as two 128-row halves
+                     // (ring stages of half a tile, N = 128 MMAs), when whole tiles do not fit
   int stages;     // item-tile ring depth
   float g;
   int mode;       // 0: blocked multiply, 1: work list
@@ -68,7 +70,8 @@ bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int r
 bool tc_make_maps(CUtensorMap* map, CUtensorMap* tail, const void* base, int64_t rows, const TcParams& p,
                   int box_rows);
 int tc_users_per_tile();  // rows of a user tile (MMA M)
-int tc_items_per_tile();  // rows of an item tile (MMA N)
+int tc_items_per_tile();  // rows of an item tile (the select's unit)
+int tc_items_box(const TcParams& p);  // rows of one item load (tile / b_split): the item maps' box
 
 cudaError_t launch_tc_score_select(const CUtensorMap* map_users, const CUtensorMap* map_users_tail,
                                    const CUtensorMap* map_items, const CUtensorMap* map_items_tail, const TcParams& p,
