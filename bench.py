@@ -52,16 +52,15 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="plain calls instead of captured graphs")
+    p.add_argument("--serve", action="store_true",
+                   help="serving loop (mips_server_*) on serve-1000000x128: saturated throughput, then Poisson "
+                        "arrivals at 0.3 / 0.6 / 0.9 of it with p50 / p99 latency")
     p.add_argument("--autotune", action="store_true",
                    help="Maximus / selector: pick |C| and B with mips_autotune before the warm-up (timed separately)")
     return p.parse_args()
 
 
-def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+from paper_1706_01449_gb300.shard import dist_env, job_throughput, max_over_ranks, rank_users  # noqa: E402
 
 
 def load_peaks():
@@ -171,7 +170,7 @@ def make_inputs(args, rank):
     W = synth.WORKLOADS[args.workload]
     f = args.f if "fs" in W else W["f"]
     n = args.users if getattr(args, "users", 0) else None
-    U = synth.make_users(W, seed=rank, f=f, n=n)
+    U = rank_users(args.workload, rank, f=f, n=n)
     I = synth.make_items(W, seed=0, f=f)
     return W, f, U, I
 
@@ -211,10 +210,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Serving loop: requests of 1..4096 users (log-uniform) with K from
+    {1, 10, 100}; first all at once (saturated throughput), then Poisson
+    arrivals at three fractions of that request rate."""
+    import numpy as np
+    import torch
+    from paper_1706_01449_gb300 import build as libbuild
+    from paper_1706_01449_gb300 import mips, synth
+    libbuild.build()
+    W = synth.WORKLOADS["serve-1000000x128"]
+    f = W["f"]
+    I = synth.make_items(W, 0)
+    index = mips.build_index(torch.from_numpy(I).cuda(), dtype="bf16")
+    rng = np.random.default_rng(0)
+    offset = [0]
+
+    def make_requests(n):
+        out = []
+        for _ in range(n):
+            m = int(round(np.exp(rng.uniform(0, np.log(4096)))))
+            out.append((synth.serving_users(m, f, 1, offset[0]), int(rng.choice(W["ks"]))))
+            offset[0] += m
+        return out
+
+    srv = mips.Server(index, method="bmm", slots=2, max_batch_users=8192)
+    for U, K in make_requests(12):  # warm-up (workspaces, pinned staging)
+        srv.wait(srv.submit(U, K))
+    reqs = make_requests(96)
+    ids = [srv.submit(U, K) for U, K in reqs]
+    infos = [srv.wait(i, timeout=600)[2] for i in ids]
+    span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+    users = sum(U.shape[0] for U, _ in reqs)
+    sat_users, sat_rate = users / span, len(reqs) / span
+    loads = {}
+    for frac in (0.3, 0.6, 0.9):
+        reqs = make_requests(96)
+        gaps = rng.exponential(1.0 / (frac * sat_rate), size=len(reqs))
+        t0 = time.perf_counter()
+        ids, t = [], 0.0
+        for (U, K), g in zip(reqs, gaps):
+            t += g
+            while time.perf_counter() - t0 < t:
+                time.sleep(0.0001)
+            ids.append(srv.submit(U, K))
+        infos = [srv.wait(i, timeout=600)[2] for i in ids]
+        lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
+        sp = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        loads[str(frac)] = {"requests_per_s": round(len(reqs) / sp, 1),
+                            "users_per_s": sum(U.shape[0] for U, _ in reqs) / sp,
+                            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                            "mean_batch_users": float(np.mean([i["batch_users"] for i in infos]))}
+    srv.close()
+    index.close()
+    print(json.dumps({"metric": "serving users/sec (saturated)", "value": sat_users, "unit": "users/s",
+                      "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "config": {"workload": "serve-1000000x128", "n_items": W["n_items"], "f": f,
+                                 "request_users": "1..4096 log-uniform", "K": list(W["ks"]), "slots": 2,
+                                 "max_batch_users": 8192, "requests_per_load": 96},
+                      "saturated_requests_per_s": sat_rate, "loads": loads}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.serve:
+        return run_serve(args)
     import numpy as np
     import torch
     from paper_1706_01449_gb300 import build as libbuild
@@ -297,13 +359,9 @@ def main():
     clocks = sampler.stop()
     mips.sync(index)
 
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
-    value = world * nU / (ms_per_step / 1e3)
+    value = job_throughput(nU, world, ms_per_step)
 
     # end to end through the host-buffer entry point (pinned host memory)
     e2e = None

@@ -149,6 +149,10 @@ WORKLOADS = {
     "kdd-1000000x624961": dict(n_users=1000000, n_items=624961, f=51, ks=(10,),
                                users="clustered", user_norm=(0.0, 0.3),
                                item_norm=(0.0, 0.7)),
+    # serving: resident 1,000,000-item f=128 catalogue; requests of 1..4096
+    # N(0,1)/sqrt(f) users with K in {1, 10, 100} (see serving_users)
+    "serve-1000000x128": dict(n_users=4096, n_items=1000000, f=128, ks=(1, 10, 100),
+                              users="serve", item_norm=(0.0, 0.5)),
     # R2-shaped large catalogue: 1,823,179 x 136,736, f=50
     "r2-1823179x136736": dict(n_users=1823179, n_items=136736, f=50,
                               ks=(1, 10, 50), users="lognormal",
@@ -166,6 +170,8 @@ def make_users(spec: dict, seed: int, n: int | None = None, f: int | None = None
         return gaussian_rows(n, f, seed, S_USERS, S_USER_NORMS, spec["user_norm"])
     if kind == "clustered":
         return clustered_users(n, f, seed, lognormal=spec["user_norm"])
+    if kind == "serve":
+        return serving_users(n, f, seed)
     raise ValueError(kind)
 
 
