@@ -212,8 +212,22 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   p.fp = idx->fp;
   p.K = K;
   const bool use_tc = idx->opt.dtype == MIPS_BF16 && tc_plan(p, idx->max_smem);
-  // BF16: two select threads per user, each with its own sub-list
-  const int lists = use_tc ? 2 : 1;
+  // Few user tiles would leave SMs idle: the item tiles are then split into
+  // nch chunks, (user tile, chunk) pairs become the persistent grid's work
+  // items, each with its own two sub-lists per user; the rescore takes the
+  // union.  At least 8 item tiles per chunk, at most 16 chunks.
+  const int64_t n_ut = (n_users + tc_users_per_tile() - 1) / tc_users_per_tile();
+  const int n_it = (int)((idx->n_items + tc_items_per_tile() - 1) / tc_items_per_tile());
+  int nch = 1;
+  if (use_tc && n_ut * 2 <= idx->num_sms) {
+    nch = (int)((idx->num_sms + n_ut - 1) / n_ut);
+    nch = std::min(nch, std::min(16, n_it / 8));
+    if (nch < 1) nch = 1;
+  }
+  const int tpc = (n_it + nch - 1) / nch;
+  nch = (n_it + tpc - 1) / tpc;
+  // BF16: two select threads per user (and chunk), each with its own sub-list
+  const int lists = use_tc ? 2 * nch : 1;
   const int cap = lists == 1 ? cap_for(K) : (K <= kRegTopK ? 2 * K + 64 : 4 * K + 64);
   const int64_t nl = n_users * lists;
   idx->ws.reset();
@@ -228,15 +242,21 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
   size_t o_tauf = idx->ws.take(sizeof(float) * n_users);
-  size_t o_ub16 = 0, o_uaux = 0;
+  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0;
   if (use_tc) {
     o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
     o_uaux = idx->ws.take(sizeof(float2) * n_users);
   }
+  if (nch > 1) {
+    o_cw = idx->ws.take(sizeof(int) * 5 * n_ut * nch);
+    o_cnw = idx->ws.take(16);
+    o_crow = idx->ws.take(sizeof(int32_t) * n_ut * tc_users_per_tile());
+    o_cpos = idx->ws.take(sizeof(int32_t) * idx->n_items_pad);
+  }
   MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
                idx->ws.at<float>(o_ub), cap, lists,
-               lists == 2 ? idx->ws.at<float>(o_topl) : nullptr, K <= kRegTopK ? 1 : 0,
+               lists >= 2 ? idx->ws.at<float>(o_topl) : nullptr, K <= kRegTopK ? 1 : 0,
                idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc), idx->ws.at<uint32_t>(o_work),
                idx->ws.at<int>(o_workc), idx->ws.at<double>(o_sc), idx->ws.at<float>(o_tauf)};
   mips_status st;
@@ -257,8 +277,19 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     if (!tc_make_maps(&map_users, &map_users_tail, ub16, n_users, p, tc_users_per_tile()) ||
         !tc_make_maps(&map_items, &map_items_tail, idx->items_bf16, idx->n_items_pad, p, tc_items_box(p)))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the operands");
-    const int64_t n_ut = (n_users + tc_users_per_tile() - 1) / tc_users_per_tile();
-    const int grid = (int)(n_ut < idx->num_sms ? n_ut : idx->num_sms);
+    int64_t n_work = n_ut;
+    if (nch > 1) {
+      int* cw = idx->ws.at<int>(o_cw);
+      const int64_t nw = n_ut * nch;
+      launch_bmm_chunks((int)n_ut, nch, tpc, n_it, n_users, idx->n_items_pad, cw, idx->ws.at<int>(o_cnw),
+                        idx->ws.at<int32_t>(o_crow), idx->ws.at<int32_t>(o_cpos), s);
+      idx->launches += 1;
+      p.mode = 1;
+      p.work = TcWork{cw, cw + nw, cw + 2 * nw, cw + 3 * nw, idx->ws.at<int>(o_cnw), idx->ws.at<int32_t>(o_crow),
+                      idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0};
+      n_work = nw;
+    }
+    const int grid = (int)(n_work < idx->num_sms ? n_work : idx->num_sms);
     MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &map_items, &map_items_tail, p, so, uaux,
                                      idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
@@ -478,14 +509,14 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     p.n_users = n_users;
     p.mode = 1;
     const int64_t mw = max_work;
-    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c};
+    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));
     MIPS_CUDA(mx_tc_pass2(m, ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), ws.at<float>(o_bounds), so, K,
                           &user_perm, ws.at<int32_t>(o_vis), idx->stats_dev, s, &idx->launches));
-    p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c};
+    p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c, nullptr, 1};
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));

@@ -121,7 +121,37 @@ __global__ void scatter_topk_kernel(const int32_t* __restrict__ src_idx, const d
   dst_sc[(int64_t)rows[r] * K + k] = src_sc[t];
 }
 
+// Work list of the item-chunked blocked multiply: work item w = c * n_ut + t
+// is user tile t against item tiles [c * tpc, min(n_it, (c + 1) tpc)) into
+// sub-lists 2c, 2c + 1; identity row and position maps (padding rows -1).
+__global__ void bmm_chunk_work_kernel(int n_ut, int nch, int tpc, int n_it, int64_t n_users, int64_t n_items_pad,
+                                      int* __restrict__ a_row, int* __restrict__ b_row, int* __restrict__ tb,
+                                      int* __restrict__ te, int* __restrict__ l_base, int* __restrict__ n_work,
+                                      int32_t* __restrict__ row_user, int32_t* __restrict__ item_pos) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nw = (int64_t)n_ut * nch;
+  if (i0 == 0) *n_work = (int)nw;
+  for (int64_t w = i0; w < nw; w += stride) {
+    const int c = (int)(w / n_ut), t = (int)(w - (int64_t)c * n_ut);
+    a_row[w] = t * 128;
+    b_row[w] = 0;
+    tb[w] = c * tpc;
+    te[w] = min(n_it, (c + 1) * tpc);
+    l_base[w] = 2 * c;
+  }
+  for (int64_t r = i0; r < (int64_t)n_ut * 128; r += stride) row_user[r] = r < n_users ? (int32_t)r : -1;
+  for (int64_t r = i0; r < n_items_pad; r += stride) item_pos[r] = (int32_t)r;
+}
+
 }  // namespace
+
+void launch_bmm_chunks(int n_ut, int nch, int tpc, int n_it, int64_t n_users, int64_t n_items_pad, int* work5,
+                       int* n_work, int32_t* row_user, int32_t* item_pos, cudaStream_t s) {
+  const int64_t nw = (int64_t)n_ut * nch;
+  bmm_chunk_work_kernel<<<152 * 2, 256, 0, s>>>(n_ut, nch, tpc, n_it, n_users, n_items_pad, work5, work5 + nw,
+                                                work5 + 2 * nw, work5 + 3 * nw, work5 + 4 * nw, n_work, row_user,
+                                                item_pos);
+}
 
 void launch_scatter_topk(const int32_t* src_idx, const double* src_sc, const int32_t* rows, int64_t n, int K,
                          int32_t* dst_idx, double* dst_sc, cudaStream_t s) {

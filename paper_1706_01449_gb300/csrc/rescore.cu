@@ -40,6 +40,27 @@ __device__ __forceinline__ bool ranks_before(double sa, int ia, double sb, int i
 }
 
 // Relative score error bound used by the tie check (see the file comment).
+// K-th largest value of the union of m rows of K values, each row sorted
+// descending (m <= kMaxLists): K rounds of taking the largest row head.
+constexpr int kMaxLists = 64;
+__device__ __forceinline__ float union_kth(const float* __restrict__ rows, int m, int K) {
+  int head[kMaxLists];
+  for (int l = 0; l < m; ++l) head[l] = 0;
+  float v = __int_as_float(0xff800000);
+  for (int r = 0; r < K; ++r) {
+    int best = -1;
+    float bv = __int_as_float(0xff800000);
+    for (int l = 0; l < m; ++l)
+      if (head[l] < K && (best < 0 || rows[l * K + head[l]] > bv)) {
+        best = l;
+        bv = rows[l * K + head[l]];
+      }
+    v = bv;
+    ++head[best];
+  }
+  return v;
+}
+
 __device__ __forceinline__ double rescore_rel_err(int f) {
   const double gf = (double)f * 5.9604644775390625e-08;  // f 2^-24
   const double gamma_f = gf / (1.0 - gf);
@@ -143,7 +164,6 @@ __global__ void __launch_bounds__(256)
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   int nvalid = 0;
-  int n[2] = {0, 0};
   float tau = 0.f;
   bool live = false;  // this user goes through the work list
   unsigned long long n_over = 0;
@@ -152,38 +172,29 @@ __global__ void __launch_bounds__(256)
     float ss = 0.f;
     for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
     const int64_t l0 = u * o.lists;
-    n[0] = o.n_cand[l0];
-    n[1] = o.lists == 2 ? o.n_cand[l0 + 1] : 0;
+    bool over = false;
+    for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
     if (ss == 0.f) {  // zero user: every score is exactly 0
       for (int k = 0; k < K; ++k) {
         out_idx[u * K + k] = k;
         out_score[u * K + k] = 0.0;
       }
-    } else if (n[0] > o.cap || n[1] > o.cap) {
+    } else if (over) {
       const int slot = atomicAdd(o.ovf_count, 1);
       o.ovf_list[slot] = (int32_t)u;
       n_over = 1;
     } else {
-      if (o.lists == 1) {
-        tau = o.tau[l0];
-      } else if (o.topl && o.topl_sorted) {
-        const float* a = o.topl + l0 * K;
-        const float* b = a + K;
-        int ia = 0, ib = 0;
-        float v = __int_as_float(0xff800000);
-        for (int r = 0; r < K; ++r) {
-          if (a[ia] >= b[ib]) v = a[ia++];
-          else v = b[ib++];
-        }
-        tau = fmaxf(v, fmaxf(o.tau[l0], o.tau[l0 + 1]));
-      } else {
-        tau = fmaxf(o.tau[l0], o.tau[l0 + 1]);
-      }
+      // every sub-list's threshold is a valid one; with the sub-lists' K
+      // largest lower bounds (distinct items, each row descending) the K-th
+      // largest of their union is too, and the tightest
+      for (int l = 0; l < o.lists; ++l) tau = l == 0 ? o.tau[l0] : fmaxf(tau, o.tau[l0 + l]);
+      if (o.lists > 1 && o.topl && o.topl_sorted) tau = fmaxf(tau, union_kth(o.topl + l0 * K, o.lists, K));
       o.tau_final[u] = tau;
       live = true;
       for (int l = 0; l < o.lists; ++l) {
         const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
-        for (int c = 0; c < n[l]; ++c) nvalid += cu[c] >= tau;
+        const int nl = o.n_cand[l0 + l];
+        for (int c = 0; c < nl; ++c) nvalid += cu[c] >= tau;
       }
     }
   }
@@ -203,7 +214,8 @@ __global__ void __launch_bounds__(256)
     for (int l = 0; l < o.lists; ++l) {
       const int64_t row = (l0 + l) * (int64_t)o.cap;
       const float* cu = o.cand_ub + row;
-      for (int c = 0; c < n[l]; ++c)
+      const int nl = o.n_cand[l0 + l];
+      for (int c = 0; c < nl; ++c)
         if (cu[c] >= tau) o.work[base++] = (uint32_t)(row + c);
     }
   }
@@ -251,11 +263,12 @@ __global__ void __launch_bounds__(128)
   if (u < n_users) {
     const float* ur = users + u * f;
     const int64_t l0 = u * o.lists;
-    const int n0 = o.n_cand[l0], n1 = o.lists == 2 ? o.n_cand[l0 + 1] : 0;
+    bool over = false;
+    for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
     float ss = 0.f;
     for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
     // zero users are done; overflowed users belong to the warp kernel
-    if (ss != 0.f && n0 <= o.cap && n1 <= o.cap) {
+    if (ss != 0.f && !over) {
       const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
       const float tau = o.tau_final[u];
       const double rel_e = rescore_rel_err(f);
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(128)
         float nmax = 0.f;
         for (int l = 0; l < o.lists; ++l) {
           const int64_t row = (l0 + l) * (int64_t)o.cap;
-          const int nl = l == 0 ? n0 : n1;
+          const int nl = o.n_cand[l0 + l];
           for (int c = 0; c < nl; ++c) {
             if (o.cand_ub[row + c] < tau) continue;
             const int32_t pos = o.cand_pos[row + c];

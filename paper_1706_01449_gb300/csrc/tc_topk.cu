@@ -696,7 +696,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       s.ut = wi;
       s.beta_u = 0.f;
       s.nhat_u = 0.f;
-      const int64_t list = (active ? u : 0) * 2 + c2;
+      const int lbase = (MX && p.work.l_base) ? p.work.l_base[wi] : 0;
+      const int64_t list = (active ? u : 0) * (int64_t)o.lists + lbase + c2;
+      const bool restoring = MX && p.work.restore && wk.tb > 0;
       c.cand_pos = o.cand_pos + list * (int64_t)o.cap;
       c.cand_ub = o.cand_ub + list * (int64_t)o.cap;
       topk_init(s, c);
@@ -704,7 +706,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const float2 ua = user_aux[u];
         s.beta_u = ua.x;
         s.nhat_u = ua.y;
-        if (wk.tb > 0) {  // continue a walk: restore the select state
+        if (restoring) {  // continue a walk: restore the select state
           s.n_cand = o.n_cand[list];
           const float* src = o.topl + list * (int64_t)p.K;
           if constexpr (KR > 0) {
@@ -753,7 +755,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         uint32_t r[64];
-        const bool first = j == 0;
+        const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
         if (first) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
           // (inactive lanes hold tau = +inf and insert nothing)
           tmem_ld64(taddr, r);

@@ -9,12 +9,16 @@ namespace mips {
 constexpr int kMaxStages = 8;
 constexpr int kRegTopK = 16;  // K up to this keeps its top-K in registers
 
-// Work list for the kernel's second mode (Maximus walk): work item w scores
-// the 128 users at A rows [a_row[w], a_row[w] + 128) against the item tiles
-// t in [t_begin[w], t_end[w]) of the list whose rank 0 is B row b_row[w].
-// Without a work list (mode 0, the blocked multiply) work item w is user tile
-// w against every item tile, and A and B rows are user ids and item
-// positions themselves.
+// Work list for the kernel's second mode: work item w scores the 128 users
+// at A rows [a_row[w], a_row[w] + 128) against the item tiles t in
+// [t_begin[w], t_end[w]) of the list whose rank 0 is B row b_row[w], into the
+// user's candidate sub-lists l_base[w] and l_base[w] + 1 (of SelectOut.lists).
+// Maximus walk (restore = 1): a work item with t_begin > 0 continues the
+// select state a first pass left in those sub-lists.  Item-chunked blocked
+// multiply (restore = 0): every work item starts afresh (seeded by its first
+// tile).  Without a work list (mode 0, the blocked multiply) work item w is
+// user tile w against every item tile, and A and B rows are user ids and
+// item positions themselves.
 struct TcWork {
   const int* a_row;
   const int* b_row;
@@ -23,6 +27,8 @@ struct TcWork {
   const int* n_work;        // device count of work items
   const int32_t* row_user;  // A row -> user id, -1 for padding rows
   const int32_t* item_pos;  // B row -> item position
+  const int* l_base;        // first sub-list of each work item (null: 0)
+  int restore;
 };
 
 struct TcParams {

@@ -173,3 +173,16 @@ def test_netflix_shape_full_size_sampled(dtype, f, K):
     rows = np.union1d(synth.distinct_ids(U.shape[0], 384, 0, synth.S_SAMPLE),
                       np.argsort(-np.linalg.norm(U, axis=1))[:64])
     check_against_oracle(U, I, K, idx, sc, rows=rows)
+
+
+@pytest.mark.parametrize("nU,nI,f,K", [(1, 20000, 32, 10), (300, 50000, 50, 5), (1000, 30000, 24, 1),
+                                        (2000, 9000, 64, 16), (700, 12000, 40, 50)])
+def test_item_chunked_small_batches(nU, nI, f, K):
+    """Few user tiles against many item tiles: the blocked multiply splits
+    the items into chunks (a work item per user tile and chunk, two
+    sub-lists per user and chunk); the rescore takes the union."""
+    U = synth.gaussian_rows(nU, f, 13, synth.S_USERS, synth.S_USER_NORMS, (0.0, 0.3))
+    I = synth.gaussian_rows(nI, f, 13, synth.S_ITEMS, synth.S_ITEM_NORMS, (0.0, 0.7))
+    idx, sc, st = run_topk(U, I, K, "bf16")
+    assert st["dtype"] == 1
+    check_against_oracle(U, I, K, idx, sc)
