@@ -85,6 +85,10 @@ struct SelectOut {
   int* work_count;     // one counter
   double* cand_sc;     // [n_users * lists][cap]
   float* tau_final;    // [n_users]
+  // optional ([n_users], zeroed): the largest threshold any select thread of
+  // the user published, as order-preserving bits; threads scanning other
+  // item chunks of the same user raise their filter to it
+  unsigned* tau_glob = nullptr;
 };
 
 // Bytes of rescore scratch (ovf list, work list, scores, thresholds, counters)

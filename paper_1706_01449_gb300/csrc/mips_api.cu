@@ -242,7 +242,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
   size_t o_tauf = idx->ws.take(sizeof(float) * n_users);
-  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0;
+  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0;
   if (use_tc) {
     o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
     o_uaux = idx->ws.take(sizeof(float2) * n_users);
@@ -252,6 +252,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     o_cnw = idx->ws.take(16);
     o_crow = idx->ws.take(sizeof(int32_t) * n_ut * tc_users_per_tile());
     o_cpos = idx->ws.take(sizeof(int32_t) * idx->n_items_pad);
+    o_ctau = idx->ws.take(sizeof(unsigned) * n_users);
   }
   MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
@@ -287,6 +288,9 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
       p.mode = 1;
       p.work = TcWork{cw, cw + nw, cw + 2 * nw, cw + 3 * nw, idx->ws.at<int>(o_cnw), idx->ws.at<int32_t>(o_crow),
                       idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0};
+      // the chunks of a user share their thresholds (zero bits = none yet)
+      so.tau_glob = idx->ws.at<unsigned>(o_ctau);
+      MIPS_CUDA(cudaMemsetAsync(so.tau_glob, 0, sizeof(unsigned) * n_users, s));
       n_work = nw;
     }
     const int grid = (int)(n_work < idx->num_sms ? n_work : idx->num_sms);

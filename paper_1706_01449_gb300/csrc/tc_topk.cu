@@ -189,6 +189,7 @@ struct TcSel {
   int32_t* qp;
   volatile unsigned long long* tau_mine;  // published thresholds: mine, partner's
   const volatile unsigned long long* tau_partner;
+  unsigned* tau_glob;                     // this user's shared threshold (item-chunked scan) or null
   volatile int* seed_mine;                // [2][256] user tile whose seed list is published
   const volatile int* seed_partner;
   float* seed_list;                       // [2][K][256] first-tile top-K lists
@@ -287,9 +288,19 @@ __device__ __forceinline__ void seed_merge(TcUser<KR>& s, const TcSel& c, int ut
 }
 
 // Publish this thread's threshold (tagged with its user tile) for the partner.
+// float <-> unsigned with the same order (for atomicMax on thresholds)
+__device__ __forceinline__ unsigned tau_ord(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float tau_from_ord(unsigned o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
 template <int KR>
 __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) {
   *c.tau_mine = pack_tau(s.tau, s.ut);
+  if (c.tau_glob) atomicMax(c.tau_glob, tau_ord(s.tau));  // every threshold is valid for the user
 }
 
 // One hit (H >= tau_eff when queued): threshold update from its lower bound,
@@ -701,6 +712,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       const bool restoring = MX && p.work.restore && wk.tb > 0;
       c.cand_pos = o.cand_pos + list * (int64_t)o.cap;
       c.cand_ub = o.cand_ub + list * (int64_t)o.cap;
+      c.tau_glob = (active && o.tau_glob) ? o.tau_glob + u : nullptr;
       topk_init(s, c);
       if (active) {
         const float2 ua = user_aux[u];
@@ -750,6 +762,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         {  // the partner's threshold, if it is for this work item
           const unsigned long long pt = *c.tau_partner;
           if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
+          // and the one shared by the user's other item chunks (zero bits: none yet, NaN, ignored)
+          if (c.tau_glob) s.tau_eff = fmaxf(s.tau_eff, tau_from_ord(*(volatile unsigned*)c.tau_glob));
         }
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
         const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
