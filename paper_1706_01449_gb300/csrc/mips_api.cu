@@ -242,7 +242,8 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
   size_t o_tauf = idx->ws.take(sizeof(float) * n_users);
-  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0;
+  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0, o_heap = 0;
+  if (use_tc && p.heap_global) o_heap = idx->ws.take(sizeof(float) * idx->num_sms * K * 256);
   if (use_tc) {
     o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
     o_uaux = idx->ws.take(sizeof(float2) * n_users);
@@ -294,6 +295,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
       n_work = nw;
     }
     const int grid = (int)(n_work < idx->num_sms ? n_work : idx->num_sms);
+    if (p.heap_global) p.heap_mem = idx->ws.at<float>(o_heap);
     MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &map_items, &map_items_tail, p, so, uaux,
                                      idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
@@ -389,7 +391,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int64_t nl = n_users * 2;
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
-         o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0, o_clend = 0;
+         o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0, o_clend = 0,
+         o_heapm = 0;
   if (use_tc) {
     o_u16 = ws.take(sizeof(uint16_t) * n_users * fp);
     o_uaux = ws.take(sizeof(float2) * n_users);
@@ -413,6 +416,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     o_sc2 = ws.take(sizeof(double) * nl * cap2);
     o_ustop = ws.take(sizeof(int32_t) * n_users);
     o_clend = ws.take(sizeof(int) * C);
+    if (p.heap_global) o_heapm = ws.take(sizeof(float) * idx->num_sms * K * 256);
     o_wk0 = ws.take(sizeof(uint32_t) * max_work);
     o_wk1 = ws.take(sizeof(uint32_t) * max_work);
     o_wv0 = ws.take(sizeof(int32_t) * max_work);
@@ -512,6 +516,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
                  ws.at<uint32_t>(o_work2), ws.at<int>(o_workc), ws.at<double>(o_sc2), ws.at<float>(o_tauf)};
     p.n_users = n_users;
     p.mode = 1;
+    if (p.heap_global) p.heap_mem = ws.at<float>(o_heapm);
     const int64_t mw = max_work;
     p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);

@@ -13,14 +13,20 @@ bool tc_plan(TcParams& p, int max_smem) {
   p.tail_bytes = (p.fp - p.kc * p.row_elems) * 2;  // 0, 32 or 64 (tc_row_len)
   p.tail_swizzle = p.tail_bytes == 32 ? 6 : 4;
   p.g = (float)(p.fp + 4) * 9.5367432e-07f + (float)p.f * 8.8817842e-16f;
-  // whole item tiles per ring stage if two stages fit, else half tiles
-  for (int split = 1; split <= 2; ++split) {
-    p.b_split = split;
-    for (int st = kMaxStages; st >= 2; --st) {
-      p.stages = st;
-      if (tc_smem_bytes(p) <= (size_t)max_smem) return true;
+  // whole item tiles per ring stage if two stages fit, else half tiles;
+  // for K > 16, the top-K heap in shared memory if it fits, else in global
+  // memory
+  for (int hg = 0; hg <= (p.K > kRegTopK ? 1 : 0); ++hg) {
+    p.heap_global = hg;
+    for (int split = 1; split <= 2; ++split) {
+      p.b_split = split;
+      for (int st = kMaxStages; st >= 2; --st) {
+        p.stages = st;
+        if (tc_smem_bytes(p) <= (size_t)max_smem) return true;
+      }
     }
   }
+  p.heap_global = 0;
   p.b_split = 1;
   p.stages = 2;
   return false;

@@ -491,8 +491,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const uint32_t b_bytes = p.kc * b_chunk + sub_rows * p.tail_bytes;  // one ring stage
   unsigned char* a_tiles = base;                                              // [KC][a_chunk] + tail
   unsigned char* b_tiles = a_tiles + a_bytes;                                 // [S]([KC][b_chunk] + tail)
-  float* heap_base = (float*)(b_tiles + (size_t)p.stages * b_bytes);          // [K][256] (KR = 0)
-  float2* aux_base = (float2*)(heap_base + (KR > 0 ? 0 : (size_t)p.K * kEpiThreads));  // [8 warps][128]
+  float* heap_smem = (float*)(b_tiles + (size_t)p.stages * b_bytes);          // [K][256] (KR = 0)
+  const bool heap_in_smem = KR == 0 && !p.heap_global;
+  float* heap_base = heap_in_smem ? heap_smem : p.heap_mem + (size_t)blockIdx.x * p.K * kEpiThreads;
+  float2* aux_base = (float2*)(heap_smem + (heap_in_smem ? (size_t)p.K * kEpiThreads : 0));  // [8 warps][128]
   int32_t* posb_base = (int32_t*)(aux_base + (size_t)kEpiWarps * kHalfN);      // [8 warps][128]
   float* qh_base = (float*)(posb_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
   int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
@@ -826,7 +828,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 size_t tc_smem_bytes(const TcParams& p) {
   const size_t sub_rows = kTileN / (p.b_split > 0 ? p.b_split : 1);
   const size_t a_chunk = (size_t)kTileM * p.row_bytes, b_chunk = sub_rows * p.row_bytes;
-  const size_t heap = p.K > kRegTopK ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
+  const size_t heap = p.K > kRegTopK && !p.heap_global ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
   const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
   const size_t b_bytes = (size_t)p.kc * b_chunk + sub_rows * p.tail_bytes;
   return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +

@@ -42,6 +42,8 @@ struct TcParams {
   int tail_swizzle;  // its layout code (6 or 4)
   int b_split;       // 1, or 2: an item tile is loaded and multiplied as two 128-row halves
                      // (ring stages of half a tile, N = 128 MMAs), when whole tiles do not fit
+  int heap_global;   // K > 16 and the heap does not fit shared memory: it lives in heap_mem,
+  float* heap_mem;   // [grid][K][256] floats of global memory (L2-resident), set by the caller
   int stages;     // item-tile ring depth
   float g;
   int mode;       // 0: blocked multiply, 1: work list

@@ -57,13 +57,14 @@ def test_ragged_shapes(dtype, nU, nI, f, K):
 
 
 @pytest.mark.parametrize("f,K", [(63, 10), (64, 1), (78, 16), (80, 10), (94, 5), (120, 3), (126, 16), (128, 10),
-                                 (128, 1)])
+                                 (128, 1), (128, 100), (64, 128)])
 def test_tail_chunk_rows(f, K):
     """Operand rows of 64 + 16 or 64 + 32 BF16 elements (f + 2 = 65..96,
     129..130): full 128-byte swizzled chunks plus a 32- or 64-byte tail
     chunk with its own tensor map and swizzle; for f near 128 the item tile
-    is loaded as two 128-row halves (N = 128 MMAs) to fit shared memory.
-    The tensor-core path must be the one used."""
+    is loaded as two 128-row halves (N = 128 MMAs) to fit shared memory, and
+    a large-K heap that still does not fit lives in global memory.  The
+    tensor-core path must be the one used."""
     U = synth.gaussian_rows(700, f, 9, synth.S_USERS, synth.S_USER_NORMS, (0.0, 0.3))
     I = synth.gaussian_rows(3000, f, 9, synth.S_ITEMS, synth.S_ITEM_NORMS, (0.0, 0.5))
     idx, sc, st = run_topk(U, I, K, "bf16")
