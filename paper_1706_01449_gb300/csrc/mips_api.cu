@@ -195,7 +195,27 @@ mips_status end_call(mips_index_t idx, cudaStream_t s) {
   return MIPS_OK;
 }
 
-int cap_for(int K) { return 4 * K + 96; }
+// Candidate capacity of the FP32 kernels' single list per user over n
+// items (no seeding): the record count K (1 + ln(n / K)) with room to spare.
+int cap_for(int K, int64_t n) {
+  const double r = n > K ? std::log((double)n / K) : 0.0;
+  return std::max(4 * K + 96, (int)std::min<int64_t>((int64_t)std::ceil(K * (2.0 + r)) + 96, n + 96));
+}
+
+// Candidate capacity of a tensor-core sub-list scanning n items.  With the
+// register top-K (K <= 16) the first tile seeds the threshold and the two
+// halves of a user merge their seeds: 2K + 64 is ample.  A heap-held top-K
+// (K > 16) or an item chunk seeds from few items, and its threshold rises
+// like the K-th largest of a stream: about K (1 + ln(n / K)) values pass,
+// the count of K-th-largest records (plus the band between lower and upper
+// bounds); the capacity is that with K + 64 to spare.
+int tc_cap(int K, int64_t n, bool chunked) {
+  const int base = K <= kRegTopK ? 2 * K + 64 : 4 * K + 64;
+  if (K <= kRegTopK && !chunked) return base;
+  const double r = n > K ? std::log((double)n / K) : 0.0;
+  const int grow = (int)std::ceil(K * (2.0 + r)) + 64;
+  return std::max(base, (int)std::min<int64_t>(grow, n + 64));
+}
 
 // Blocked multiply (Sec. III-B) over the index's items with fused select,
 // then the exact rescore.
@@ -228,7 +248,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   nch = (n_it + tpc - 1) / tpc;
   // BF16: two select threads per user (and chunk), each with its own sub-list
   const int lists = use_tc ? 2 * nch : 1;
-  const int cap = lists == 1 ? cap_for(K) : (K <= kRegTopK ? 2 * K + 64 : 4 * K + 64);
+  const int cap = lists == 1 ? cap_for(K, idx->n_items) : tc_cap(K, (int64_t)tpc * tc_items_per_tile() / 2, nch > 1);
   const int64_t nl = n_users * lists;
   idx->ws.reset();
   size_t o_tau = idx->ws.take(sizeof(float) * nl);
@@ -340,7 +360,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int f = idx->f;
   const int64_t nI = idx->n_items;
   const int C = (int)(idx->clusters < n_users ? idx->clusters : n_users);
-  const int cap = cap_for(K);
+  const int cap = cap_for(K, nI);
   const int64_t CI = (int64_t)C * nI;
   // walk on tcgen05 when the index has BF16 operands and the tiling fits
   TcParams p{};
@@ -387,7 +407,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int blk = idx->opt.block_items > 0 ? idx->opt.block_items : 4096;
   const int t1 = (int)((blk + 255) / 256) < n_it ? (int)((blk + 255) / 256) : n_it;
   const int64_t n_pad = round_up(nI, 256);
-  const int cap2 = K <= kRegTopK ? 2 * K + 64 : 4 * K + 64;
+  const int cap2 = tc_cap(K, (nI + 1) / 2, false);
   const int64_t nl = n_users * 2;
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
