@@ -765,7 +765,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           const unsigned long long pt = *c.tau_partner;
           if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
           // and the one shared by the user's other item chunks (zero bits: none yet, NaN, ignored)
-          if (c.tau_glob) s.tau_eff = fmaxf(s.tau_eff, tau_from_ord(*(volatile unsigned*)c.tau_glob));
+          if constexpr (MX)
+            if (c.tau_glob) s.tau_eff = fmaxf(s.tau_eff, tau_from_ord(*(volatile unsigned*)c.tau_glob));
         }
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
         const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
@@ -774,20 +775,24 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
         if (first) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
           // (inactive lanes hold tau = +inf and insert nothing)
-          tmem_ld64(taddr, r);
-          seed64(s, c, r, 0, valid, aux_tile);
-          tmem_ld64(taddr + 64, r);
-          seed64(s, c, r, 64, valid - 64, aux_tile);
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            tmem_ld64(taddr + 64 * h, r);
+            seed64(s, c, r, 64 * h, valid - 64 * h, aux_tile);
+          }
           if (active) {
             s.tau_eff = s.tau;
             tc_publish(s, c);
             if constexpr (KR > 0) seed_merge(s, c, wi, lt & 1);
           }
         }
-        tmem_ld64(taddr, r);
-        select64<KR, MX>(s, c, r, 0, valid, aux_tile, rank0, pos_tile, slow, first);
-        tmem_ld64(taddr + 64, r);
-        select64<KR, MX>(s, c, r, 64, valid - 64, aux_tile, rank0, pos_tile, slow, first);
+        // the two 64-column halves run through one copy of the select code
+        // (a second inlined copy costs more in instruction-cache misses)
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld64(taddr + 64 * h, r);
+          select64<KR, MX>(s, c, r, 64 * h, valid - 64 * h, aux_tile, rank0, pos_tile, slow, first);
+        }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&ctl->acc_empty[b]);
