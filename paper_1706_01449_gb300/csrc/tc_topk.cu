@@ -443,6 +443,7 @@ struct WorkItem {
   int a_row;   // first A row of the user tile
   int b_row;   // B row of list rank 0
   int tb, te;  // item tiles [tb, te)
+  int q;       // index into the work arrays
 };
 
 template <bool MX>
@@ -453,11 +454,19 @@ __device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it
     w.b_row = 0;
     w.tb = 0;
     w.te = n_it;
+    w.q = wi;
   } else {
-    w.a_row = p.work.a_row[wi];
-    w.b_row = p.work.b_row[wi];
-    w.tb = p.work.t_begin[wi];
-    w.te = p.work.t_end[wi];
+    // CTAs take work items round-robin (item wi in round wi / gridDim.x);
+    // odd rounds run backwards, so a list sorted by length does not hand the
+    // longest item of every round to the same CTA
+    const int G = (int)gridDim.x, r = wi / G, k = wi - r * G;
+    const int in_round = min(G, *p.work.n_work - r * G);
+    const int q = (r & 1) ? r * G + (in_round - 1 - k) : wi;
+    w.a_row = p.work.a_row[q];
+    w.b_row = p.work.b_row[q];
+    w.tb = p.work.t_begin[q];
+    w.te = p.work.t_end[q];
+    w.q = q;
   }
   return w;
 }
@@ -709,7 +718,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       s.ut = wi;
       s.beta_u = 0.f;
       s.nhat_u = 0.f;
-      const int lbase = (MX && p.work.l_base) ? p.work.l_base[wi] : 0;
+      const int lbase = (MX && p.work.l_base) ? p.work.l_base[wk.q] : 0;
       const int64_t list = (active ? u : 0) * (int64_t)o.lists + lbase + c2;
       const bool restoring = MX && p.work.restore && wk.tb > 0;
       c.cand_pos = o.cand_pos + list * (int64_t)o.cap;
