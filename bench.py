@@ -315,9 +315,11 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)  # torch work (flush, events) and the calls share it
 
+    last_report = {}
+
     def step():
         if args.method == "select":
-            mips.select(index, U_d, K, out_idx, out_sc, stream=stream)
+            last_report.update(mips.select(index, U_d, K, out_idx, out_sc, stream=stream)[2])
         elif use_graph:
             mips.topk_graph(index, U_d, K, args.method, out_idx, out_sc, stream=stream)
         else:
@@ -391,7 +393,10 @@ def main():
     # algorithmic work of the scoring kernel: every (user, item) pair it
     # scores; the Maximus walk scores only the pairs its bounds leave
     walked = args.method == "maximus" or (args.method == "select" and stats["ms_walk"] > 0 and not stats["ms_score"])
-    flops = 2.0 * f * (stats["pairs_scored"] if walked else nU * nI)
+    # (the selector's stage times are those of its last run: the users
+    # outside the timed sample)
+    scored_users = nU - last_report.get("sample_users", 0) if args.method == "select" else nU
+    flops = 2.0 * f * (stats["pairs_scored"] if walked else scored_users * nI)
     kms = statistics.mean(score_ms)
     if dtype == "bf16":
         bound, peak, unit = "tensor", peaks["bf16_tflops"], "TFLOP/s"

@@ -57,6 +57,9 @@ void launch_scatter_topk(const int32_t* src_idx, const double* src_sc, const int
                          int32_t* dst_idx, double* dst_sc, cudaStream_t s);
 // Gather rows of x by perm into out (out[r] = x[perm[r]]).
 void launch_gather_rows(const float* x, const int32_t* perm, int64_t n, int f, float* out, cudaStream_t s);
+// Sample split of the selector: keys 0 for the ns users whose image under
+// the affine permutation (a u + b) mod n is below ns, else 1; ids = u.
+void launch_sample_keys(int64_t n, uint64_t a, uint64_t b, int64_t ns, uint32_t* keys, int32_t* ids, cudaStream_t s);
 // Work list of the item-chunked blocked multiply (work5: 5 arrays of
 // n_ut * nch ints: a_row, b_row, t_begin, t_end, l_base) and identity maps.
 void launch_bmm_chunks(int n_ut, int nch, int tpc, int n_it, int64_t n_users, int64_t n_items_pad, int* work5,

@@ -8,7 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
-#include <set>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -333,24 +333,20 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
 
 // C distinct user ids from a counter-based stream (SplitMix64 of seed and
 // counter), Floyd's method: the k-means initial centroids.
-// C distinct values of [0, n): Floyd's algorithm over SplitMix64 draws of a
-// counter keyed by the seed (the selector's user sample).
-void draw_distinct_host(int64_t n, int64_t C, uint64_t seed, std::vector<int64_t>& out) {
+// Parameters of a seeded affine permutation of [0, n): u -> (a u + b) mod n
+// with a coprime to n (SplitMix64 draws).  The users whose image is below
+// ns form a sample of exactly ns distinct users.
+void affine_sample(int64_t n, uint64_t seed, uint64_t* a_out, uint64_t* b_out) {
   auto mix = [](uint64_t z) {
     z += 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
   };
-  out.clear();
-  std::set<int64_t> chosen;
-  uint64_t ctr = 0;
-  for (int64_t j = n - C; j < n; ++j) {
-    const int64_t t = (int64_t)(mix(seed ^ mix(++ctr)) % (uint64_t)(j + 1));
-    const int64_t pick = chosen.count(t) ? j : t;
-    chosen.insert(pick);
-    out.push_back(pick);
-  }
+  uint64_t a = n > 1 ? 1 + mix(seed) % (uint64_t)(n - 1) : 1;
+  while (std::gcd(a, (uint64_t)n) != 1) a = a % (uint64_t)(n - 1) + 1;
+  *a_out = a;
+  *b_out = n > 0 ? mix(seed ^ 1ull) % (uint64_t)n : 0;
 }
 
 // Maximus (Sec. IV, Algorithm 1): k-means, theta_b + CBound, per-cluster
@@ -588,28 +584,32 @@ mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, in
   int64_t ns = (int64_t)ceil(idx->opt.sample_frac * (double)n_users);
   if (ns < floor_users) ns = floor_users;
   if (ns > n_users) ns = n_users;
-  // seeded sample of distinct users, ascending; the rest, ascending
-  std::vector<int64_t> pick;
-  draw_distinct_host(n_users, ns, idx->opt.seed ^ 0x5EEDull, pick);
-  std::vector<char> in_sample((size_t)n_users, 0);
-  for (int64_t v : pick) in_sample[v] = 1;
-  std::vector<int32_t> sample, rest;
-  sample.reserve(ns);
-  rest.reserve(n_users - ns);
-  for (int64_t u = 0; u < n_users; ++u) (in_sample[u] ? sample : rest).push_back((int32_t)u);
+  // seeded sample: the users u whose image under a seeded affine
+  // permutation of [0, n), (a u + b) mod n with a coprime to n, falls below
+  // ns -- exactly ns distinct users; sample and rest each ascending, split
+  // on the device by a stable one-digit radix pass
+  uint64_t a = 1, b = 0;
+  affine_sample(n_users, idx->opt.seed ^ 0x5EEDull, &a, &b);
   const int64_t nr = n_users - ns;
   const int f = idx->f;
   Arena& w = idx->ws_sel;
   w.reset();
-  size_t o_sid = w.take(4 * ns), o_rid = w.take(4 * (nr > 0 ? nr : 1));
+  size_t o_keys = w.take(4 * n_users), o_ids = w.take(4 * n_users), o_keys2 = w.take(4 * n_users),
+         o_ids2 = w.take(4 * n_users), o_tmp = w.take(radix_sort_temp_bytes(n_users, 1));
   size_t o_su = w.take(sizeof(float) * ns * f), o_ru = w.take(sizeof(float) * (nr > 0 ? nr : 1) * f);
   size_t o_bi = w.take(4 * ns * K), o_bs = w.take(8 * ns * K), o_mi = w.take(4 * ns * K), o_ms = w.take(8 * ns * K);
   size_t o_ri = w.take(4 * (nr > 0 ? nr : 1) * K), o_rs = w.take(8 * (nr > 0 ? nr : 1) * K);
   MIPS_CUDA(w.ensure(w.used, s));
-  MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_sid), sample.data(), 4 * ns, cudaMemcpyHostToDevice, s));
-  if (nr > 0) MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_rid), rest.data(), 4 * nr, cudaMemcpyHostToDevice, s));
-  launch_gather_rows(users, w.at<int32_t>(o_sid), ns, f, w.at<float>(o_su), s);
-  if (nr > 0) launch_gather_rows(users, w.at<int32_t>(o_rid), nr, f, w.at<float>(o_ru), s);
+  uint32_t* keys = w.at<uint32_t>(o_keys);
+  int32_t* ids = w.at<int32_t>(o_ids);
+  uint32_t* keys2 = w.at<uint32_t>(o_keys2);
+  int32_t* ids2 = w.at<int32_t>(o_ids2);
+  launch_sample_keys(n_users, a, b, ns, keys, ids, s);
+  MIPS_CUDA(radix_sort_pairs(keys, ids, keys2, ids2, n_users, 1, 0, 8, w.at<uint32_t>(o_tmp), s, nullptr));
+  const int32_t* sample_ids = ids;       // the first ns of the split
+  const int32_t* rest_ids = ids + ns;    // then the rest
+  launch_gather_rows(users, sample_ids, ns, f, w.at<float>(o_su), s);
+  if (nr > 0) launch_gather_rows(users, rest_ids, nr, f, w.at<float>(o_ru), s);
   MIPS_CUDA(cudaGetLastError());
 
   cudaEvent_t e[3];
@@ -652,15 +652,20 @@ mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, in
   r.choice = r.est_index < r.est_bmm ? 1 : 0;
   if (rep) *rep = r;
   // the sample's results (both paths are exact and agree), then the rest
-  launch_scatter_topk(w.at<int32_t>(r.choice ? o_mi : o_bi), w.at<double>(r.choice ? o_ms : o_bs),
-                      w.at<int32_t>(o_sid), ns, K, out_idx, out_score, s);
+  launch_scatter_topk(w.at<int32_t>(r.choice ? o_mi : o_bi), w.at<double>(r.choice ? o_ms : o_bs), sample_ids, ns, K,
+                      out_idx, out_score, s);
   if (nr > 0) {
+    // the call's stage times are those of this last run
+    for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
+    idx->n_order = 0;
+    idx->last_stage = -1;
+    MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
     if (r.choice == 1)
       st = run_maximus(idx, w.at<float>(o_ru), nr, K, w.at<int32_t>(o_ri), w.at<double>(o_rs), s);
     else
       st = run_bmm(idx, w.at<float>(o_ru), nr, K, w.at<int32_t>(o_ri), w.at<double>(o_rs), s);
     if (st != MIPS_OK) return st;
-    launch_scatter_topk(w.at<int32_t>(o_ri), w.at<double>(o_rs), w.at<int32_t>(o_rid), nr, K, out_idx, out_score, s);
+    launch_scatter_topk(w.at<int32_t>(o_ri), w.at<double>(o_rs), rest_ids, nr, K, out_idx, out_score, s);
   }
   MIPS_CUDA(cudaGetLastError());
   idx->last_users = n_users;
@@ -861,18 +866,25 @@ mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_us
   int64_t ns = n_users / 8;
   if (ns < 2ll * idx->num_sms * 128) ns = 2ll * idx->num_sms * 128;
   if (ns > n_users) ns = n_users;
-  std::vector<int64_t> pick;
-  draw_distinct_host(n_users, ns, idx->opt.seed ^ 0x7E57ull, pick);
-  std::sort(pick.begin(), pick.end());
-  std::vector<int32_t> sample(pick.begin(), pick.end());
   const int f = idx->f;
   Arena& w = idx->ws_sel;
   w.reset();
-  size_t o_sid = w.take(4 * ns), o_su = w.take(sizeof(float) * ns * f);
+  size_t o_keys = w.take(4 * n_users), o_ids = w.take(4 * n_users), o_keys2 = w.take(4 * n_users),
+         o_ids2 = w.take(4 * n_users), o_tmp = w.take(radix_sort_temp_bytes(n_users, 1));
+  size_t o_su = w.take(sizeof(float) * ns * f);
   size_t o_oi = w.take(4 * ns * K), o_os = w.take(8 * ns * K);
   MIPS_CUDA(w.ensure(w.used, s));
-  MIPS_CUDA(cudaMemcpyAsync(w.at<int32_t>(o_sid), sample.data(), 4 * ns, cudaMemcpyHostToDevice, s));
-  launch_gather_rows(users_dev, w.at<int32_t>(o_sid), ns, f, w.at<float>(o_su), s);
+  {  // seeded sample of ns distinct users (affine permutation, as the selector's)
+    uint64_t a = 1, b = 0;
+    affine_sample(n_users, idx->opt.seed ^ 0x7E57ull, &a, &b);
+    uint32_t* keys = w.at<uint32_t>(o_keys);
+    int32_t* ids = w.at<int32_t>(o_ids);
+    uint32_t* keys2 = w.at<uint32_t>(o_keys2);
+    int32_t* ids2 = w.at<int32_t>(o_ids2);
+    launch_sample_keys(n_users, a, b, ns, keys, ids, s);
+    MIPS_CUDA(radix_sort_pairs(keys, ids, keys2, ids2, n_users, 1, 0, 8, w.at<uint32_t>(o_tmp), s, nullptr));
+    launch_gather_rows(users_dev, ids, ns, f, w.at<float>(o_su), s);
+  }
   MIPS_CUDA(cudaGetLastError());
   const int saved_c = idx->clusters, saved_b = idx->opt.block_items;
   const double scale = (double)ns / (double)n_users;

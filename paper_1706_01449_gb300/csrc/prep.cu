@@ -143,7 +143,23 @@ __global__ void bmm_chunk_work_kernel(int n_ut, int nch, int tpc, int n_it, int6
   for (int64_t r = i0; r < n_items_pad; r += stride) item_pos[r] = (int32_t)r;
 }
 
+// Sample split keys: 0 for the users whose image (a u + b) mod n is below
+// ns, 1 for the rest; ids = u.
+__global__ void sample_keys_kernel(int64_t n, uint64_t a, uint64_t b, int64_t ns, uint32_t* __restrict__ keys,
+                                   int32_t* __restrict__ ids) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n) return;
+  const uint64_t img = (a * (uint64_t)u + b) % (uint64_t)n;  // a, u < 2^31: no overflow
+  keys[u] = img < (uint64_t)ns ? 0u : 1u;
+  ids[u] = (int32_t)u;
+}
+
 }  // namespace
+
+void launch_sample_keys(int64_t n, uint64_t a, uint64_t b, int64_t ns, uint32_t* keys, int32_t* ids, cudaStream_t s) {
+  if (n <= 0) return;
+  sample_keys_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b, ns, keys, ids);
+}
 
 void launch_bmm_chunks(int n_ut, int nch, int tpc, int n_it, int64_t n_users, int64_t n_items_pad, int* work5,
                        int* n_work, int32_t* row_user, int32_t* item_pos, cudaStream_t s) {
