@@ -157,7 +157,7 @@ struct MxTc {
   int32_t* pos_c = nullptr;          // [C * n_pad] item positions of the B rows
   int* w1 = nullptr;                 // [4][max_work] a_row, b_row, t_begin, t_end (pass 1)
   int* w2 = nullptr;                 // [4][max_work] (pass 2, longest first)
-  int* n_work = nullptr;             // [2] work items of pass 1, pass 2
+  int* n_work = nullptr;             // [3] work items of pass 1, pass 2; pass-2 claim counter
   int* work_end = nullptr;           // [max_work] item tiles each A tile walks
   int32_t* ustop = nullptr;          // [n_users] item tiles each user needs
   int* cl_end = nullptr;             // [C] item tiles any member of the cluster needs

@@ -308,7 +308,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
       idx->launches += 1;
       p.mode = 1;
       p.work = TcWork{cw, cw + nw, cw + 2 * nw, cw + 3 * nw, idx->ws.at<int>(o_cnw), idx->ws.at<int32_t>(o_crow),
-                      idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0};
+                      idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0, nullptr};
       // the chunks of a user share their thresholds (zero bits = none yet)
       so.tau_glob = idx->ws.at<unsigned>(o_ctau);
       MIPS_CUDA(cudaMemsetAsync(so.tau_glob, 0, sizeof(unsigned) * n_users, s));
@@ -534,14 +534,17 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     p.mode = 1;
     if (p.heap_global) p.heap_mem = ws.at<float>(o_heapm);
     const int64_t mw = max_work;
-    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1};
+    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1, nullptr};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));
     MIPS_CUDA(mx_tc_pass2(m, ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), ws.at<float>(o_bounds), so, K,
                           &user_perm, ws.at<int32_t>(o_vis), idx->stats_dev, s, &idx->launches));
-    p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c, nullptr, 1};
+    // second pass: uneven work items, claimed dynamically (counter in n_work[2])
+    MIPS_CUDA(cudaMemsetAsync(m.n_work + 2, 0, sizeof(int), s));
+    p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c, nullptr, 1,
+                    m.n_work + 2};
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));

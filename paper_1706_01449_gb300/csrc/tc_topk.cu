@@ -456,12 +456,15 @@ __device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it
     w.te = n_it;
     w.q = wi;
   } else {
-    // CTAs take work items round-robin (item wi in round wi / gridDim.x);
-    // odd rounds run backwards, so a list sorted by length does not hand the
-    // longest item of every round to the same CTA
-    const int G = (int)gridDim.x, r = wi / G, k = wi - r * G;
-    const int in_round = min(G, *p.work.n_work - r * G);
-    const int q = (r & 1) ? r * G + (in_round - 1 - k) : wi;
+    // without a work counter, CTAs take work items round-robin (item wi in
+    // round wi / gridDim.x); odd rounds run backwards, so a list sorted by
+    // length does not hand the longest item of every round to the same CTA
+    int q = wi;
+    if (!p.work.next) {
+      const int G = (int)gridDim.x, r = wi / G, k = wi - r * G;
+      const int in_round = min(G, *p.work.n_work - r * G);
+      q = (r & 1) ? r * G + (in_round - 1 - k) : wi;
+    }
     w.a_row = p.work.a_row[q];
     w.b_row = p.work.b_row[q];
     w.tb = p.work.t_begin[q];
@@ -471,12 +474,20 @@ __device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it
   return w;
 }
 
+// The CTA's work sequence: the producer takes its lt-th work item (static:
+// round-robin over the CTAs; with a work counter: the next unclaimed item)
+// and publishes the index in ring slot lt % kWQ, where the MMA thread and the
+// select warps read it; an index >= n_work ends the sequence.
+constexpr int kWQ = 4;
+
 struct Smem {
   uint64_t b_full[kMaxStages];
   uint64_t b_empty[kMaxStages];
   uint64_t a_full, a_empty;
   uint64_t acc_full[2], acc_empty[2];
   uint64_t drain;
+  uint64_t wq_full[kWQ], wq_empty[kWQ];
+  int wq[kWQ];
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -530,6 +541,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       mbar_init(&ctl->acc_empty[b], kEpiWarps);
     }
     mbar_init(&ctl->drain, 1);
+    for (int w = 0; w < kWQ; ++w) {
+      mbar_init(&ctl->wq_full[w], 1);
+      mbar_init(&ctl->wq_empty[w], 1 + kEpiWarps);  // the MMA thread and every select warp
+    }
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -558,9 +573,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       long long g = 0;  // item tiles issued so far
       int st = 0;        // ring stage of tile g
       uint32_t ph = 0;   // ring pass parity of tile g
-      int lt = 0;
       bool ok = true;
-      for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+      const bool dyn = MX && p.work.next;
+      for (int lt = 0; ok; ++lt) {
+        // take and publish the next work item
+        const int slot = lt % kWQ;
+        if (lt >= kWQ) ok = mbar_wait(&ctl->wq_empty[slot], (uint32_t)((lt / kWQ - 1) & 1), abort_flag, err);
+        if (!ok) break;
+        int wi = dyn ? atomicAdd(p.work.next, 1) : (int)blockIdx.x + lt * (int)gridDim.x;
+        if (wi > n_work) wi = n_work;
+        ctl->wq[slot] = wi;
+        mbar_arrive(&ctl->wq_full[slot]);
+        if (wi >= n_work) break;
         const WorkItem wk = get_work<MX>(p, wi, n_it);
         if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
         if (!ok) break;
@@ -620,9 +644,14 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       uint32_t ph = 0;   // ring pass parity
       int b = 0;         // accumulator of tile g
       uint32_t aph = 0;  // accumulator pass parity
-      int lt = 0;
       bool ok = true;
-      for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+      for (int lt = 0; ok; ++lt) {
+        const int slot = lt % kWQ;
+        ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), abort_flag, err);
+        if (!ok) break;
+        const int wi = *(volatile int*)&ctl->wq[slot];
+        mbar_arrive(&ctl->wq_empty[slot]);
+        if (wi >= n_work) break;
         const WorkItem wk = get_work<MX>(p, wi, n_it);
         ok = mbar_wait(&ctl->a_full, lt & 1, abort_flag, err);
         if (!ok) break;
@@ -703,12 +732,28 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         if constexpr (MX) prep[t] = p.work.item_pos[br];
       }
     };
-    if (blockIdx.x < n_work) {
-      const WorkItem w0 = get_work<MX>(p, blockIdx.x, n_it);
-      prefetch((int64_t)w0.b_row + (int64_t)w0.tb * kTileN + c2 * kHalfN);
+    // the index of the CTA's lt-th work item (waits for the producer to
+    // publish it; warp-uniform)
+    auto peek_work = [&](int lt_, int* wi_out) {
+      bool okp = mbar_wait(&ctl->wq_full[lt_ % kWQ], (uint32_t)((lt_ / kWQ) & 1), abort_flag, err);
+      okp = __all_sync(0xffffffffu, okp);
+      *wi_out = okp ? *(volatile int*)&ctl->wq[lt_ % kWQ] : n_work;
+      return okp;
+    };
+    {
+      int w0i = n_work;
+      ok = peek_work(0, &w0i);
+      if (ok && w0i < n_work) {
+        const WorkItem w0 = get_work<MX>(p, w0i, n_it);
+        prefetch((int64_t)w0.b_row + (int64_t)w0.tb * kTileN + c2 * kHalfN);
+      }
     }
-    int lt = 0;  // work items done by this CTA
-    for (int wi = blockIdx.x; wi < n_work && ok; wi += gridDim.x, ++lt) {
+    for (int lt = 0; ok; ++lt) {  // work items of this CTA
+      int wi = n_work;
+      ok = peek_work(lt, &wi);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl->wq_empty[lt % kWQ]);
+      if (!ok || wi >= n_work) break;
       const WorkItem wk = get_work<MX>(p, wi, n_it);
       const int64_t u = MX ? (int64_t)p.work.row_user[wk.a_row + row] : (int64_t)wk.a_row + row;
       const bool active = u >= 0 && u < p.n_users;
@@ -763,9 +808,12 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         if constexpr (MX) {
           if (j + 1 < wk.te) {
             prefetch((int64_t)wk.b_row + (int64_t)(j + 1) * kTileN + c2 * kHalfN);
-          } else if (wi + (int)gridDim.x < n_work) {
-            const WorkItem wn = get_work<MX>(p, wi + gridDim.x, n_it);
-            prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
+          } else {  // the first tile of the next work item, once published
+            int wni = n_work;
+            if (peek_work(lt + 1, &wni) && wni < n_work) {
+              const WorkItem wn = get_work<MX>(p, wni, n_it);
+              prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
+            }
           }
         } else {  // next tile (wraps to the first of the next user tile)
           prefetch((int64_t)((j + 1 < n_it) ? j + 1 : 0) * kTileN + c2 * kHalfN);

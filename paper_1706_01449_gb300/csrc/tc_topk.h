@@ -29,6 +29,7 @@ struct TcWork {
   const int32_t* item_pos;  // B row -> item position
   const int* l_base;        // first sub-list of each work item (null: 0)
   int restore;
+  int* next;                // zeroed work counter: CTAs claim items dynamically (null: round-robin)
 };
 
 struct TcParams {
