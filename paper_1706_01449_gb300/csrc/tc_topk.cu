@@ -216,12 +216,12 @@ __device__ __forceinline__ float topk_insert(TcUser<KR>& s, const TcSel& c, floa
     nd[0] = fmaxf(s.d[0], L);
 #pragma unroll
     for (int i = 1; i < KR; ++i) nd[i] = (L > s.d[i - 1]) ? s.d[i - 1] : fmaxf(s.d[i], L);
+#pragma unroll
+    for (int i = 0; i < KR; ++i) s.d[i] = nd[i];
+    if (c.K == KR) return nd[KR - 1];  // K fills the array (warp-uniform)
     float t = nd[0];  // ends as nd[K - 1] (static indices keep d in registers)
 #pragma unroll
-    for (int i = 0; i < KR; ++i) {
-      s.d[i] = nd[i];
-      t = (i < c.K) ? nd[i] : t;
-    }
+    for (int i = 0; i < KR; ++i) t = (i < c.K) ? nd[i] : t;
     return t;
   } else {
     return heap_replace_min(c.heap, kEpiThreads, c.K, L);
