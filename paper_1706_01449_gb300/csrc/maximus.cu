@@ -218,7 +218,7 @@ __global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, in
 // descending), value = item position.  [C][n_items], cluster-major.
 // One block: 128 items (one per thread, staged in shared memory as
 // [f][129] to keep the banks apart) against a chunk of 32 centroids
-// ([f][32], read four at a time); every dot product, item norm and
+// ([f][32], read eight at a time); every dot product, item norm and
 // centroid norm is summed sequentially over k with FMA.
 constexpr int kCbItems = 128, kCbChunk = 32;
 
@@ -281,19 +281,23 @@ __global__ void __launch_bounds__(kCbItems)
   if (t >= rows) return;
   const int64_t i = i0 + t;
   const float ni = item_nrm[i];
-  for (int jj = 0; jj < nc; jj += 4) {
-    float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+  for (int jj = 0; jj < nc; jj += 8) {  // eight centroids at a time: eight independent sums
+    float d[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < f; ++k) {
       const float v = it[k * (kCbItems + 1) + t];
-      const float4 c4 = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj);
-      d0 = __fmaf_rn(c4.x, v, d0);
-      d1 = __fmaf_rn(c4.y, v, d1);
-      d2 = __fmaf_rn(c4.z, v, d2);
-      d3 = __fmaf_rn(c4.w, v, d3);
+      const float4 ca = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj);
+      const float4 cb = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj + 4);
+      d[0] = __fmaf_rn(ca.x, v, d[0]);
+      d[1] = __fmaf_rn(ca.y, v, d[1]);
+      d[2] = __fmaf_rn(ca.z, v, d[2]);
+      d[3] = __fmaf_rn(ca.w, v, d[3]);
+      d[4] = __fmaf_rn(cb.x, v, d[4]);
+      d[5] = __fmaf_rn(cb.y, v, d[5]);
+      d[6] = __fmaf_rn(cb.z, v, d[6]);
+      d[7] = __fmaf_rn(cb.w, v, d[7]);
     }
-    const float d[4] = {d0, d1, d2, d3};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       if (jj + q < nc) {
         const int j = j0 + jj + q;
         const float y = ord2f(cosb_ord[j]);
