@@ -1,12 +1,18 @@
 // Fused BF16 blocked multiply + top-K candidate select on tcgen05 tensor
 // cores (the paper's BMM, Sec. III-B, with the per-user selection fused so
-// the |U| x |I| score matrix never leaves the SM).
+// the |U| x |I| score matrix never leaves the SM), and the same machinery
+// walking Maximus's per-cluster item lists (Sec. IV, Algorithm 1).
 //
 // Persistent kernel, one CTA per SM, 12 warps, user tiles of 128 rows and
 // item tiles of 256 rows (an M = 128, N = 256 MMA runs at the tensor pipe's
 // full rate; N = 128 costs nearly the same time per instruction):
-//   warp 0      TMA producer: the user tile once per tile, then item tiles
-//               through an S-stage shared-memory ring;
+//   warp 0      TMA producer: takes the CTA's next work item (user tile x
+//               range of item tiles), publishes it in a shared-memory ring
+//               for the other roles, loads the user tile, then the item
+//               tiles through an S-stage ring (whole tiles, or two 128-row
+//               halves when whole tiles do not fit shared memory; operand
+//               rows of 128-byte chunks plus a 32/64-byte tail chunk, each
+//               with its own tensor map and swizzle);
 //   warp 1      MMA issuer (one thread): D = A . B^T with tcgen05.mma
 //               kind::f16 (BF16 x BF16 -> FP32) into one of two TMEM
 //               accumulators of 128 lanes x 256 columns, so the MMAs of item
@@ -20,6 +26,9 @@
 //               their thresholds through shared memory (either one is a valid
 //               lower bound on the user's K-th score, so the larger filters
 //               both halves).
+// Work items: without a work list (blocked multiply) user tile w against
+// every item tile; with one (item-chunked blocked multiply, Maximus walk)
+// as the list gives them, claimed round-robin or from a global counter.
 // Operands are K-major rows (prep.cu): the two bound columns make every
 // accumulator entry an upper bound H >= u^T i, so the common case costs one
 // maximum over 16 scores and a compare.
