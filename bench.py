@@ -55,6 +55,9 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="serving loop (mips_server_*) on serve-1000000x128: saturated throughput, then Poisson "
                         "arrivals at 0.3 / 0.6 / 0.9 of it with p50 / p99 latency")
+    p.add_argument("--fit-frac", type=float, default=0.0,
+                   help="Maximus / selector: fit the centroids once on this fraction of the users before the "
+                        "warm-up (Sec. IV-E dynamic users); timed steps then only assign users")
     p.add_argument("--autotune", action="store_true",
                    help="Maximus / selector: pick |C| and B with mips_autotune before the warm-up (timed separately)")
     return p.parse_args()
@@ -325,6 +328,13 @@ def main():
         else:
             fn(index, U_d, K, out_idx, out_sc, stream=stream)
 
+    fit = None
+    if args.fit_frac > 0 and args.method != "bmm":
+        n_fit = max(1, int(round(nU * args.fit_frac)))
+        t0 = time.perf_counter()
+        mips.fit_clusters(index, U_d[:n_fit], stream=stream)
+        mips.sync(index, stream)
+        fit = {"users": n_fit, "seconds": time.perf_counter() - t0}
     tune = None
     if args.autotune and args.method != "bmm":
         tune = mips.autotune(index, U_d, K, stream=stream)
@@ -433,6 +443,7 @@ def main():
                    "launch": "cuda graph replay" if use_graph else "plain calls",
                    **({"clusters": stats["clusters"]} if args.method != "bmm" else {}),
                    **({"autotune": tune} if tune else {}),
+                   **({"centroids_fitted_before_timing": fit} if fit else {}),
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -111,6 +111,24 @@ mips_status mips_topk(mips_index_t idx, const float* users_dev, int64_t n_users,
 mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
                               int32_t* out_idx_dev, double* out_score_dev, void* stream);
 
+/*
+ * Dynamic users (Sec. IV-E, "Practical Usage"): run k-means (the index's
+ * kmeans_iters Lloyd iterations, initial centroids a seeded draw of users)
+ * on these users (device FP32 [n_users][f], read during the call only) and
+ * keep the min(|C|, n_users) centroids in the index.  Afterwards every
+ * Maximus call on this index (mips_topk_maximus, mips_select, graphs,
+ * servers and worker handles created later) assigns its users to these
+ * centroids with one assignment step instead of clustering them; theta_b,
+ * the bounds and the lists are still those of the call's users, and only
+ * the clusters that receive users are walked.  The result stays exact
+ * whatever the centroids.  mips_autotune then tunes B only.
+ * users_dev = NULL with n_users = 0 drops the fitted centroids (clustering
+ * per call again).  Errors: MIPS_ERR_ARG (null index, null users with
+ * n_users != 0, n_users < 0 or >= 2^31), MIPS_ERR_NOMEM, MIPS_ERR_CUDA.
+ * Asynchronous on stream; the index owns the centroid buffer.
+ */
+mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t n_users, void* stream);
+
 /* Report of one Optimus decision (Sec. V, "Overhead of Optimizer"). */
 typedef struct {
   int choice;           /* 0 = blocked multiply, 1 = Maximus */

@@ -126,6 +126,12 @@ cudaError_t make_float_desc_keys(const float* x, int64_t n, uint32_t* keys, int3
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
                            uint32_t* absmax, float* scale, cudaStream_t s, int* launches);
+// Assignment of the call's users to fitted centroids (cent_fit [C_fit][f]),
+// then the used clusters packed into slots 0.. of cent [C_eff][f] and the
+// assignment renumbered to those slots (C_eff >= the number of used clusters).
+cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, const float* cent_fit, int C_fit,
+                                  float* hn2_fit, int32_t* assign, int* used, int* remap, float* cent, int C_eff,
+                                  cudaStream_t s, int* launches);
 cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int32_t* assign, const float* cent, int C,
                            const float* items, const float* item_nrm, int64_t n_items, uint32_t* cosb_ord,
                            uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches);

@@ -871,10 +871,109 @@ cudaError_t draw_init_ids(int64_t n, int C, uint64_t seed, uint32_t* chosen_bits
 }
 
 // ---------------------------------------------------------------- host side
+namespace {
+
+// One assignment step over n_users users and C centroids (hn2 = ||c_j||^2 / 2).
+cudaError_t launch_kmeans_assign(const float* users, int64_t n_users, int f, const float* cent, const float* hn2,
+                                 int C, int32_t* assign, cudaStream_t s) {
+  const int fp = (int)round_up(f, 8);
+  const unsigned blocks = (unsigned)((n_users + kThreads - 1) / kThreads);
+  switch (fp) {
+#define MIPS_KM_CASE(N) \
+  case N:               \
+    kmeans_assign_kernel<N><<<blocks, kThreads, 0, s>>>(users, n_users, f, cent, hn2, C, assign); \
+    break;
+    MIPS_KM_CASE(8) MIPS_KM_CASE(16) MIPS_KM_CASE(24) MIPS_KM_CASE(32) MIPS_KM_CASE(40) MIPS_KM_CASE(48)
+    MIPS_KM_CASE(56) MIPS_KM_CASE(64) MIPS_KM_CASE(72) MIPS_KM_CASE(80) MIPS_KM_CASE(88) MIPS_KM_CASE(96)
+    MIPS_KM_CASE(104) MIPS_KM_CASE(112) MIPS_KM_CASE(120) MIPS_KM_CASE(128)
+#undef MIPS_KM_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+// Dynamic users (Sec. IV-E, practical usage): a call's users are assigned to
+// centroids fitted earlier, and only the clusters that receive users are
+// kept.  used[j] marks cluster j.
+__global__ void cluster_used_kernel(const int32_t* __restrict__ assign, int64_t n, int* __restrict__ used) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    used[assign[u]] = 1;
+}
+
+// One block of 1024 threads: the used clusters, in cluster order, get the
+// slots 0, 1, ... (remap[j] = slot, or -1 for an unused cluster) and their
+// centroids are packed into cent_out.  Slots past the last used cluster (up
+// to C_eff) repeat the first packed centroid; no user is assigned to them.
+__global__ void __launch_bounds__(1024) cluster_pack_kernel(const int* __restrict__ used, int C_fit,
+                                                            const float* __restrict__ cent_fit, int f, int C_eff,
+                                                            int* __restrict__ remap, float* __restrict__ cent_out) {
+  __shared__ int s_warp[32];
+  __shared__ int s_base;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < C_fit; c0 += 1024) {
+    const int j = c0 + tid;
+    const int v = j < C_fit ? (used[j] != 0) : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int w = s_warp[lane], wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += t;
+      }
+      s_warp[lane] = wi - w;  // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    const int slot = s_base + s_warp[wid] + incl - v;
+    if (j < C_fit) remap[j] = v ? slot : -1;
+    if (v)
+      for (int k = 0; k < f; ++k) cent_out[(int64_t)slot * f + k] = cent_fit[(int64_t)j * f + k];
+    __syncthreads();  // every thread has read s_base and s_warp
+    if (tid == 1023) s_base = slot + v;
+    __syncthreads();
+  }
+  const int n_used = s_base;
+  for (int e = tid; e < (C_eff - n_used) * f; e += 1024) {
+    const int d = n_used + e / f, k = e % f;
+    cent_out[(int64_t)d * f + k] = cent_out[k];
+  }
+}
+
+__global__ void cluster_remap_kernel(int32_t* __restrict__ assign, int64_t n, const int* __restrict__ remap) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x)
+    assign[u] = remap[assign[u]];
+}
+
+}  // namespace
+
+cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, const float* cent_fit, int C_fit,
+                                  float* hn2_fit, int32_t* assign, int* used, int* remap, float* cent, int C_eff,
+                                  cudaStream_t s, int* launches) {
+  half_norm2_kernel<<<(C_fit + 127) / 128, 128, 0, s>>>(cent_fit, C_fit, f, hn2_fit);
+  cudaError_t e = launch_kmeans_assign(users, n_users, f, cent_fit, hn2_fit, C_fit, assign, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int) * C_fit, s);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, 152 * 8));
+  cluster_used_kernel<<<g, 256, 0, s>>>(assign, n_users, used);
+  cluster_pack_kernel<<<1, 1024, 0, s>>>(used, C_fit, cent_fit, f, C_eff, remap, cent);
+  cluster_remap_kernel<<<g, 256, 0, s>>>(assign, n_users, remap);
+  *launches += 5;
+  return cudaGetLastError();
+}
+
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
                            uint32_t* absmax, float* scale, cudaStream_t s, int* launches) {
-  const int fp = (int)round_up(f, 8);
   gather_rows_i64<<<(unsigned)((C * f + 255) / 256), 256, 0, s>>>(users, init_ids_dev, C, f, cent);
   cudaError_t e = cudaMemsetAsync(absmax, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
@@ -884,19 +983,8 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
   *launches += 1;
   for (int it = 0; it < iters; ++it) {
     half_norm2_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f, hn2);
-    const unsigned blocks = (unsigned)((n_users + kThreads - 1) / kThreads);
-    switch (fp) {
-#define MIPS_KM_CASE(N) \
-  case N:               \
-    kmeans_assign_kernel<N><<<blocks, kThreads, 0, s>>>(users, n_users, f, cent, hn2, C, assign); \
-    break;
-      MIPS_KM_CASE(8) MIPS_KM_CASE(16) MIPS_KM_CASE(24) MIPS_KM_CASE(32) MIPS_KM_CASE(40) MIPS_KM_CASE(48)
-      MIPS_KM_CASE(56) MIPS_KM_CASE(64) MIPS_KM_CASE(72) MIPS_KM_CASE(80) MIPS_KM_CASE(88) MIPS_KM_CASE(96)
-      MIPS_KM_CASE(104) MIPS_KM_CASE(112) MIPS_KM_CASE(120) MIPS_KM_CASE(128)
-#undef MIPS_KM_CASE
-      default:
-        return cudaErrorInvalidValue;
-    }
+    e = launch_kmeans_assign(users, n_users, f, cent, hn2, C, assign, s);
+    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * C * f, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned int) * C, s);
     if (e != cudaSuccess) return e;

@@ -90,6 +90,11 @@ struct mips_index_s {
   int64_t n_items = 0;
   int clusters = 0;
   mips_options opt{};
+  // centroids fitted by mips_fit_clusters ([fit_C][f], owned; 0 = none)
+  float* fit_cent = nullptr;
+  int fit_C = 0;
+  int64_t fit_cap = 0;   // floats allocated at fit_cent
+  uint64_t fit_gen = 0;  // bumped by every fit or clear (captured graphs hold the old state)
   // item data, in the index's item order ("sorted position")
   float* items = nullptr;      // FP32 master rows [n_items][f]
   int32_t* perm = nullptr;     // sorted position -> item id
@@ -143,6 +148,9 @@ struct mips_index_s {
     int32_t* out_idx = nullptr;
     double* out_score = nullptr;
     uint64_t ws_gen = 0;
+    // index settings the capture baked in
+    int cfg_clusters = 0, cfg_block = 0;
+    uint64_t cfg_fit = 0;
     cudaGraphExec_t exec = nullptr;
     // host bookkeeping of the captured call, restored on replay
     bool stage_ran[kStages] = {};
@@ -355,7 +363,9 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
                         double* out_score, cudaStream_t s) {
   const int f = idx->f;
   const int64_t nI = idx->n_items;
-  const int C = (int)(idx->clusters < n_users ? idx->clusters : n_users);
+  // with fitted centroids only the clusters that receive users are kept
+  const bool fitted = idx->fit_C > 0;
+  const int C = (int)std::min<int64_t>(fitted ? idx->fit_C : idx->clusters, n_users);
   const int cap = cap_for(K, nI);
   const int64_t CI = (int64_t)C * nI;
   // walk on tcgen05 when the index has BF16 operands and the tiling fits
@@ -378,6 +388,9 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_cosb = ws.take(sizeof(uint32_t) * C), o_cosbf = ws.take(sizeof(float) * C);
   size_t o_keys = ws.take(sizeof(uint32_t) * CI), o_vals = ws.take(sizeof(int32_t) * CI);
   size_t o_keys2 = ws.take(sizeof(uint32_t) * CI), o_vals2 = ws.take(sizeof(int32_t) * CI);
+  const int C_fit = fitted ? idx->fit_C : 0;
+  size_t o_fhn2 = ws.take(sizeof(float) * C_fit), o_used = ws.take(sizeof(int) * C_fit),
+         o_remap = ws.take(sizeof(int) * C_fit);
   const int64_t n_rows_max = round_up(n_users, 128) + 128ll * C;  // A rows of the tensor-core walk
   const int64_t max_work = n_rows_max / 128;
   size_t tmp_bytes = radix_sort_temp_bytes(nI, C);
@@ -440,14 +453,22 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   }
   MIPS_CUDA(ws.ensure(ws.used, s));
 
-  // k-means initial centroids: a seeded draw of C distinct users (on the
-  // device, so that a captured call holds no host data)
-  MIPS_CUDA(draw_init_ids(n_users, C, idx->opt.seed, ws.at<uint32_t>(o_bits), ws.at<int64_t>(o_ids), s));
-  idx->launches += 1;
+  if (fitted) {
+    // dynamic users (Sec. IV-E): one assignment step to the fitted centroids
+    MIPS_CUDA(maximus_assign_fitted(users, n_users, f, idx->fit_cent, C_fit, ws.at<float>(o_fhn2),
+                                    ws.at<int32_t>(o_assign), ws.at<int>(o_used), ws.at<int>(o_remap),
+                                    ws.at<float>(o_cent), C, s, &idx->launches));
+  } else {
+    // k-means initial centroids: a seeded draw of C distinct users (on the
+    // device, so that a captured call holds no host data)
+    MIPS_CUDA(draw_init_ids(n_users, C, idx->opt.seed, ws.at<uint32_t>(o_bits), ws.at<int64_t>(o_ids), s));
+    idx->launches += 1;
+    MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
+                             ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
+                             ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
+                             ws.at<float>(o_scale), s, &idx->launches));
+  }
   mips_status st;
-  MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids), ws.at<float>(o_cent),
-                           ws.at<float>(o_hn2), ws.at<int32_t>(o_assign), ws.at<unsigned long long>(o_sums),
-                           ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax), ws.at<float>(o_scale), s, &idx->launches));
   if ((st = end_stage(idx, ST_KMEANS, s)) != MIPS_OK) return st;
   MIPS_CUDA(maximus_bounds(users, n_users, f, ws.at<int32_t>(o_assign), ws.at<float>(o_cent), C, idx->items,
                            idx->item_nrm, nI, ws.at<uint32_t>(o_cosb), ws.at<uint32_t>(o_keys), ws.at<int32_t>(o_vals),
@@ -709,6 +730,17 @@ mips_index_t mips::index_worker_clone(mips_index_t src) {
   w->max_smem = src->max_smem;
   w->shares_items = true;
   bool ok = cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) == cudaSuccess;
+  if (ok && src->fit_C > 0) {  // its own copy of the fitted centroids
+    const size_t bytes = sizeof(float) * (size_t)src->fit_C * src->f;
+    if (src->has_done) ok = cudaEventSynchronize(src->done) == cudaSuccess;
+    ok = ok && cudaMalloc(&w->fit_cent, bytes) == cudaSuccess &&
+         cudaMemcpy(w->fit_cent, src->fit_cent, bytes, cudaMemcpyDeviceToDevice) == cudaSuccess;
+    if (ok) {
+      w->fit_C = src->fit_C;
+      w->fit_cap = (int64_t)src->fit_C * src->f;
+      w->fit_gen = src->fit_gen;
+    }
+  }
   for (int i = 0; i <= kStages && ok; ++i) ok = cudaEventCreate(&w->ev[i]) == cudaSuccess;
   ok = ok && cudaMalloc(&w->err_dev, sizeof(int)) == cudaSuccess && cudaMemset(w->err_dev, 0, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&w->stats_dev, sizeof(DevStats)) == cudaSuccess;
@@ -845,6 +877,56 @@ mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t 
   return end_call(idx, s);
 }
 
+mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t n_users, void* stream) {
+  g_err.clear();
+  if (!idx) return fail(MIPS_ERR_ARG, "null index");
+  if (!users_dev && n_users == 0) {  // back to clustering each call's users
+    if (idx->has_done) MIPS_CUDA(cudaEventSynchronize(idx->done));
+    if (idx->fit_cent) MIPS_CUDA(cudaFree(idx->fit_cent));
+    idx->fit_cent = nullptr;
+    idx->fit_C = 0;
+    idx->fit_cap = 0;
+    ++idx->fit_gen;
+    return MIPS_OK;
+  }
+  if (!users_dev) return fail(MIPS_ERR_ARG, "null users");
+  if (n_users < 1 || n_users >= INT32_MAX) return fail(MIPS_ERR_ARG, "n_users out of range");
+  mips_status st = check_device(idx);
+  if (st != MIPS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = begin_call(idx, s)) != MIPS_OK) return st;
+  const int f = idx->f;
+  const int C = (int)std::min<int64_t>(idx->clusters, n_users);
+  Arena& ws = idx->ws;
+  ws.reset();
+  size_t o_ids = ws.take(sizeof(int64_t) * C), o_cent = ws.take(sizeof(float) * C * f), o_hn2 = ws.take(sizeof(float) * C);
+  size_t o_bits = ws.take(sizeof(uint32_t) * ((n_users + 31) / 32));
+  size_t o_assign = ws.take(sizeof(int32_t) * n_users), o_sums = ws.take(sizeof(unsigned long long) * C * f);
+  size_t o_cnt = ws.take(sizeof(unsigned) * C), o_amax = ws.take(16), o_scale = ws.take(16);
+  MIPS_CUDA(ws.ensure(ws.used, s));
+  idx->mx.C = 0;  // the workspace is reused: earlier Maximus views are gone
+  MIPS_CUDA(draw_init_ids(n_users, C, idx->opt.seed, ws.at<uint32_t>(o_bits), ws.at<int64_t>(o_ids), s));
+  idx->launches += 1;
+  MIPS_CUDA(maximus_kmeans(users_dev, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
+                           ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
+                           ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
+                           ws.at<float>(o_scale), s, &idx->launches));
+  if (idx->fit_cap < (int64_t)C * f) {  // (every call on this index is ordered after idx->done)
+    if (idx->has_done) MIPS_CUDA(cudaEventSynchronize(idx->done));
+    if (idx->fit_cent) MIPS_CUDA(cudaFree(idx->fit_cent));
+    idx->fit_cent = nullptr;
+    idx->fit_C = 0;
+    idx->fit_cap = 0;
+    MIPS_CUDA(cudaMalloc(&idx->fit_cent, sizeof(float) * C * f));
+    idx->fit_cap = (int64_t)C * f;
+  }
+  MIPS_CUDA(cudaMemcpyAsync(idx->fit_cent, ws.at<float>(o_cent), sizeof(float) * C * f, cudaMemcpyDeviceToDevice, s));
+  idx->fit_C = C;
+  ++idx->fit_gen;
+  if ((st = end_stage(idx, ST_KMEANS, s)) != MIPS_OK) return st;
+  return end_call(idx, s);
+}
+
 mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_users, int K,
                         int32_t* out_idx_dev, double* out_score_dev, void* stream,
                         mips_select_report* rep) {
@@ -893,9 +975,17 @@ mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_us
   const double scale = (double)ns / (double)n_users;
   struct Cand { int C, B; double est; };
   std::vector<Cand> tried;
-  for (int C = 16; C <= 1024 && C <= n_users / 32; C *= 2) {
-    int Cs = (int)llround(C * scale);
-    if (Cs < 1) Cs = 1;
+  // |C| candidates with the users each sample cluster stands for; fitted
+  // centroids fix |C| and leave only B to tune
+  std::vector<std::pair<int, int>> cands;
+  if (idx->fit_C > 0) {
+    cands.push_back({idx->fit_C, idx->fit_C});
+  } else {
+    for (int C = 16; C <= 1024 && C <= n_users / 32; C *= 2)
+      cands.push_back({C, std::max(1, (int)llround(C * scale))});
+  }
+  for (const auto& cc : cands) {
+    const int C = cc.first, Cs = cc.second;
     for (int B : {1024, 4096, 16384}) {
       idx->clusters = Cs;
       idx->opt.block_items = B;
@@ -931,7 +1021,7 @@ mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_us
     for (const Cand& c : tried)
       if (c.est < best.est) best = c;
   }
-  idx->clusters = best.C;
+  idx->clusters = idx->fit_C > 0 ? saved_c : best.C;
   idx->opt.block_items = best.B;
   if (rep) {
     memset(rep, 0, sizeof(*rep));
@@ -963,7 +1053,8 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
   if (s == nullptr) return plain();  // the legacy default stream cannot be captured
   for (auto& g : idx->graphs) {
     if (g.method != method || g.users != users_dev || g.n_users != n_users || g.K != K || g.out_idx != out_idx_dev ||
-        g.out_score != out_score_dev || g.ws_gen != idx->ws.gen)
+        g.out_score != out_score_dev || g.ws_gen != idx->ws.gen || g.cfg_clusters != idx->clusters ||
+        g.cfg_block != idx->opt.block_items || g.cfg_fit != idx->fit_gen)
       continue;
     if (idx->has_done) MIPS_CUDA(cudaStreamWaitEvent(s, idx->done, 0));
     MIPS_CUDA(cudaGraphLaunch(g.exec, s));
@@ -1010,6 +1101,9 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
   g.out_idx = out_idx_dev;
   g.out_score = out_score_dev;
   g.ws_gen = gen;
+  g.cfg_clusters = idx->clusters;
+  g.cfg_block = idx->opt.block_items;
+  g.cfg_fit = idx->fit_gen;
   for (int i = 0; i < kStages; ++i) {
     g.stage_ran[i] = idx->stage_ran[i];
     g.order[i] = idx->order[i];
@@ -1174,6 +1268,7 @@ void mips_free_index(mips_index_t idx) {
     cudaFree(idx->items_bf16);
     cudaFree(idx->item_aux);
   }
+  cudaFree(idx->fit_cent);
   cudaFree(idx->err_dev);
   cudaFree(idx->stats_dev);
   if (idx->done) cudaEventDestroy(idx->done);

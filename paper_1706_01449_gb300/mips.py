@@ -29,7 +29,7 @@ EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_m
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
            "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph",
            "mips_autotune", "mips_server_create", "mips_server_submit", "mips_server_wait",
-           "mips_server_destroy")
+           "mips_server_destroy", "mips_fit_clusters")
 
 
 class MipsError(RuntimeError):
@@ -105,6 +105,8 @@ def load():
         fn = getattr(lib, name)
         fn.argtypes = [P, P, i64, i32, P, P, P]
         fn.restype = st
+    lib.mips_fit_clusters.argtypes = [P, P, i64, P]
+    lib.mips_fit_clusters.restype = st
     lib.mips_select.argtypes = [P, P, i64, i32, P, P, P, ctypes.POINTER(SelectReport)]
     lib.mips_select.restype = st
     lib.mips_topk_host.argtypes = [P, P, i64, i32, i32, P, P, P]
@@ -233,6 +235,19 @@ def topk(index: Index, users, K: int, out_idx=None, out_score=None, stream=None)
 def topk_maximus(index: Index, users, K: int, out_idx=None, out_score=None, stream=None):
     """Maximus (mips_topk_maximus).  Asynchronous on the stream."""
     return _run(load().mips_topk_maximus, index, users, K, out_idx, out_score, stream)
+
+
+def fit_clusters(index: Index, users, stream=None):
+    """mips_fit_clusters: k-means on these users; later Maximus calls on the
+    index assign their users to the fitted centroids (Sec. IV-E, dynamic
+    users).  users=None drops the fitted centroids.  Asynchronous."""
+    lib = load()
+    if users is None:
+        _check(lib.mips_fit_clusters(index.handle, None, 0, None))
+        return
+    users = _dev_f32(users, "users")
+    _check(lib.mips_fit_clusters(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0],
+                                 _stream_ptr(stream)))
 
 
 def topk_graph(index: Index, users, K: int, method: str = "bmm", out_idx=None, out_score=None, stream=None):

@@ -56,6 +56,8 @@ def test_argument_errors_need_no_gpu():
     assert lib.mips_sync(None, None) == mips.MIPS_ERR_ARG
     assert lib.mips_topk_graph(None, fake, 4, 1, 0, fake, fake, None) == mips.MIPS_ERR_ARG
     assert lib.mips_autotune(None, fake, 4, 1, None, None) == mips.MIPS_ERR_ARG
+    assert lib.mips_fit_clusters(None, fake, 4, None) == mips.MIPS_ERR_ARG
+    assert lib.mips_fit_clusters(None, None, 0, None) == mips.MIPS_ERR_ARG
     srv = ctypes.c_void_p()
     sopt = mips.ServerOptions(0, 2, 1024, 0)
     assert lib.mips_server_create(None, ctypes.byref(sopt), ctypes.byref(srv)) == mips.MIPS_ERR_ARG
