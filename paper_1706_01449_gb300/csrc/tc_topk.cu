@@ -168,6 +168,16 @@ __device__ __forceinline__ float max3(float a, float b, float c) {
   return r;
 }
 
+// maximum of 16 scores (a tree of three-input maxima)
+__device__ __forceinline__ float max16(const uint32_t* r) {
+  const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
+  const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
+  const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
+  const float m3 = max3(__uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
+  const float m4 = max3(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]));
+  return max3(max3(m0, m1, m2), m3, fmaxf(m4, __uint_as_float(r[15])));
+}
+
 // A threshold published for the partner thread, tagged with its user tile
 // so that a value from another user is never taken.
 __device__ __forceinline__ unsigned long long pack_tau(float t, int ut) {
@@ -392,6 +402,11 @@ __device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t
     for (int q = 0; q < 64; ++q)
       if (q >= valid) r[q] = 0xff800000u;  // -inf
   }
+  // fast path: one maximum over the 64 scores and one warp vote (the four
+  // groups of 16 are looked at only when some lane has a hit)
+  const float g0 = max16(r), g1 = max16(r + 16), g2 = max16(r + 32), g3 = max16(r + 48);
+  const float mm = max3(g0, g1, fmaxf(g2, g3));
+  if (!__any_sync(0xffffffffu, mm >= s.tau_eff)) return;
 #pragma unroll
   for (int g = 0; g < 4; ++g)
     select16<KR, MX>(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos0, pos_tile, slow, emit_only);
