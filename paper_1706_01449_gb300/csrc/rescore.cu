@@ -68,9 +68,54 @@ __device__ __forceinline__ double rescore_rel_err(int f) {
   return 2.0 * (2.0 * gamma_2f * gamma_f + (double)(f + 2) * 1.1102230246251565e-16);
 }
 
+// Row loads: two elements at a time when both rows start on 8 bytes and f is
+// even (half the load instructions), else one.  The arithmetic runs over
+// k = 0, 1, ... either way.
+__device__ __forceinline__ bool pairs_ok(const float* a, const float* b, int f) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 7) == 0 && (f & 1) == 0;
+}
+
+__device__ __forceinline__ float norm2_seq(const float* __restrict__ r, int f) {
+  float ss = 0.f;
+  if (pairs_ok(r, r, f)) {
+    const float2* r2 = reinterpret_cast<const float2*>(r);
+    for (int k = 0; k < f / 2; ++k) {
+      const float2 x = r2[k];
+      ss = __fmaf_rn(x.x, x.x, ss);
+      ss = __fmaf_rn(x.y, x.y, ss);
+    }
+    return ss;
+  }
+  for (int k = 0; k < f; ++k) ss = __fmaf_rn(r[k], r[k], ss);
+  return ss;
+}
+
 __device__ __forceinline__ double score_dot2(const float* __restrict__ u, const float* __restrict__ v, int f) {
   Dot2 acc{0.f, 0.f};
   int k = 0;
+  if (pairs_ok(u, v, f)) {
+    const float2* u2 = reinterpret_cast<const float2*>(u);
+    const float2* v2 = reinterpret_cast<const float2*>(v);
+    for (; k + 8 <= f; k += 8) {  // the loads of 8 terms before their arithmetic
+      float2 a[4], b[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        a[j] = u2[k / 2 + j];
+        b[j] = v2[k / 2 + j];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        dot2_step(acc, a[j].x, b[j].x);
+        dot2_step(acc, a[j].y, b[j].y);
+      }
+    }
+    for (; k < f; k += 2) {
+      const float2 a = u2[k / 2], b = v2[k / 2];
+      dot2_step(acc, a.x, b.x);
+      dot2_step(acc, a.y, b.y);
+    }
+    return dot2_value(acc);
+  }
   for (; k + 8 <= f; k += 8) {  // issue the loads of 8 terms before their arithmetic
     float a[8], b[8];
 #pragma unroll
@@ -169,8 +214,7 @@ __global__ void __launch_bounds__(256)
   unsigned long long n_over = 0;
   if (u < n_users) {
     const float* ur = users + u * f;
-    float ss = 0.f;
-    for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
+    const float ss = norm2_seq(ur, f);
     const int64_t l0 = u * o.lists;
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
@@ -265,8 +309,7 @@ __global__ void __launch_bounds__(128)
     const int64_t l0 = u * o.lists;
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
-    float ss = 0.f;
-    for (int k = 0; k < f; ++k) ss = __fmaf_rn(ur[k], ur[k], ss);
+    const float ss = norm2_seq(ur, f);
     // zero users are done; overflowed users belong to the warp kernel
     if (ss != 0.f && !over) {
       const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
