@@ -79,7 +79,7 @@ struct SelectOut {
   // ([n_users * lists][K]); with two sub-lists the rescore's threshold is the
   // K-th largest of their union (entries are distinct items)
   float* topl;
-  int topl_sorted;     // 1: each topl row is sorted descending
+  int topl_sorted;     // 1: each topl row is sorted descending (the tensor-core select writes them so)
   // users whose candidate list overflowed, for the exhaustive rescore
   int32_t* ovf_list;   // [n_users]
   int* ovf_count;      // one counter, zero before the rescore

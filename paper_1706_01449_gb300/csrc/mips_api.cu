@@ -286,7 +286,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
                idx->ws.at<float>(o_ub), cap, lists,
-               lists >= 2 ? idx->ws.at<float>(o_topl) : nullptr, K <= kRegTopK ? 1 : 0,
+               lists >= 2 ? idx->ws.at<float>(o_topl) : nullptr, 1,
                idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc), idx->ws.at<uint32_t>(o_work),
                idx->ws.at<int>(o_workc), idx->ws.at<double>(o_sc), idx->ws.at<float>(o_tauf)};
   mips_status st;
@@ -549,7 +549,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
         !tc_make_maps(&map_b, &map_bt, m.b_rows, C * n_pad, p, tc_items_box(p)))
       return fail(MIPS_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Maximus operands");
     SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
-                 ws.at<float>(o_topl), K <= kRegTopK ? 1 : 0, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
+                 ws.at<float>(o_topl), 1, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
                  ws.at<uint32_t>(o_work2), ws.at<int>(o_workc), ws.at<double>(o_sc2), ws.at<float>(o_tauf)};
     p.n_users = n_users;
     p.mode = 1;

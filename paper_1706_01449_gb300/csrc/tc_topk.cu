@@ -807,8 +807,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             s.tau = s.d[0];
 #pragma unroll
             for (int i = 0; i < KR; ++i) s.tau = (i < p.K) ? s.d[i] : s.tau;
-          } else {
-            for (int i = 0; i < p.K; ++i) c.heap[i * kEpiThreads] = src[i];
+          } else {  // the row is descending: reversed, it is a min-heap
+            for (int i = 0; i < p.K; ++i) c.heap[i * kEpiThreads] = src[p.K - 1 - i];
             s.tau = c.heap[0];
           }
           s.tau_eff = fmaxf(s.tau, o.tau[list]);
@@ -889,8 +889,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
 #pragma unroll
             for (int i = 0; i < KR; ++i)
               if (i < p.K) dst[i] = s.d[i];
-          } else {
-            for (int i = 0; i < p.K; ++i) dst[i] = c.heap[i * kEpiThreads];
+          } else {  // heap sort: the minima, popped in turn, fill the row from the back
+            for (int n = p.K; n > 0; --n) {
+              dst[n - 1] = c.heap[0];
+              if (n > 1) heap_replace_min(c.heap, kEpiThreads, n - 1, c.heap[(n - 1) * kEpiThreads]);
+            }
           }
         }
       }
