@@ -87,7 +87,7 @@ struct SelectOut {
   uint32_t* work;      // [n_users * lists * cap]
   int* work_count;     // one counter
   double* cand_sc;     // [n_users * lists][cap]
-  float* tau_final;    // [n_users]
+  float* tau_final;    // [n_users][2]: the rescore threshold, ||u||^2
   // optional ([n_users], zeroed): the largest threshold any select thread of
   // the user published, as order-preserving bits; threads scanning other
   // item chunks of the same user raise their filter to it
@@ -98,7 +98,7 @@ struct SelectOut {
 // for n_users users with `lists` sub-lists of `cap` candidates each.
 inline size_t rescore_scratch_bytes(int64_t n_users, int lists, int cap) {
   const size_t slots = (size_t)n_users * lists * cap;
-  return 4 * (size_t)n_users + 4 * slots + 8 * slots + 4 * (size_t)n_users + 1024;
+  return 4 * (size_t)n_users + 4 * slots + 8 * slots + 8 * (size_t)n_users + 1024;
 }
 bool fp32_supported(int f, int K);
 cudaError_t launch_fp32_score_select(const float* users, int64_t n_users, int f, const float* items,

@@ -269,7 +269,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_work = idx->ws.take(sizeof(uint32_t) * nl * cap);
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
-  size_t o_tauf = idx->ws.take(sizeof(float) * n_users);
+  size_t o_tauf = idx->ws.take(sizeof(float) * 2 * n_users);
   size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0, o_heap = 0;
   if (use_tc && p.heap_global) o_heap = idx->ws.take(sizeof(float) * idx->num_sms * K * 256);
   if (use_tc) {
@@ -407,7 +407,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_pos = ws.take(sizeof(int32_t) * n_users * cap1), o_ub = ws.take(sizeof(float) * n_users * cap1);
   size_t o_ovf = ws.take(sizeof(int32_t) * n_users), o_ovfc = ws.take(sizeof(int));
   size_t o_work = ws.take(sizeof(uint32_t) * n_users * cap1), o_workc = ws.take(sizeof(int));
-  size_t o_sc = ws.take(sizeof(double) * n_users * cap1), o_tauf = ws.take(sizeof(float) * n_users);
+  size_t o_sc = ws.take(sizeof(double) * n_users * cap1), o_tauf = ws.take(sizeof(float) * 2 * n_users);
   // tensor-core walk buffers: BF16 user rows grouped by cluster (each
   // cluster padded to whole 128-row tiles), per-cluster BF16 item copies in
   // bound order, two work lists, two-list select state

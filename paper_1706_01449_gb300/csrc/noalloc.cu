@@ -94,7 +94,7 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
   const int cap = 4 * K + 96;
   const size_t slots = (size_t)n_users * cap;
   const size_t need = up256(sizeof(DevStats)) + up256(sizeof(int)) * 3 + up256(4 * (size_t)n_items) * 2 +
-                      up256(4 * (size_t)n_users) * 4 + up256(4 * slots) * 3 + up256(8 * slots);
+                      up256(4 * (size_t)n_users) * 3 + up256(8 * (size_t)n_users) + up256(4 * slots) * 3 + up256(8 * slots);
   if (need > kNoAllocScratchBytes)
     return report(MIPS_ERR_ARG, "problem needs %zu scratch bytes, the static scratch holds %zu (use fewer users per call)",
                   need, kNoAllocScratchBytes);

@@ -215,6 +215,7 @@ __global__ void __launch_bounds__(256)
   if (u < n_users) {
     const float* ur = users + u * f;
     const float ss = norm2_seq(ur, f);
+    o.tau_final[2 * u + 1] = ss;  // (for the select kernel)
     const int64_t l0 = u * o.lists;
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(256)
       // largest of their union is too, and the tightest
       for (int l = 0; l < o.lists; ++l) tau = l == 0 ? o.tau[l0] : fmaxf(tau, o.tau[l0 + l]);
       if (o.lists > 1 && o.topl && o.topl_sorted) tau = fmaxf(tau, union_kth(o.topl + l0 * K, o.lists, K));
-      o.tau_final[u] = tau;
+      o.tau_final[2 * u] = tau;
       live = true;
       for (int l = 0; l < o.lists; ++l) {
         const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
@@ -309,11 +310,11 @@ __global__ void __launch_bounds__(128)
     const int64_t l0 = u * o.lists;
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
-    const float ss = norm2_seq(ur, f);
+    const float ss = o.tau_final[2 * u + 1];  // ||u||^2 as the collect kernel computed it
     // zero users are done; overflowed users belong to the warp kernel
     if (ss != 0.f && !over) {
       const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
-      const float tau = o.tau_final[u];
+      const float tau = o.tau_final[2 * u];
       const double rel_e = rescore_rel_err(f);
       KeyHeap heap{ls + t, li + t, T};
       for (int mode = 0; mode < 2; ++mode) {
