@@ -23,7 +23,12 @@
 //     the exact order, which equals the FP64 definition's order;
 //   * a zero user has every score exactly 0: its answer is items 0..K-1;
 //   * a user whose candidate list overflowed is queued for the warp kernel,
-//     one warp per queued user, scoring every item.
+//     one warp per queued user, scoring every item;
+//   * so is a non-zero user with ||u||^2 < 2^-100 in FP32 (its squares or
+//     products may be subnormal, where the relative bounds above fail): the
+//     warp kernel scores it with the FP64 definition's arithmetic only;
+//   * the tie-check margin also carries an absolute f 2^-148 for subnormal
+//     products of normal-range users (each loses at most 2^-150 in TwoProduct).
 #include "common.cuh"
 
 namespace mips {
@@ -59,6 +64,18 @@ __device__ __forceinline__ float union_kth(const float* __restrict__ rows, int m
     ++head[best];
   }
   return v;
+}
+
+// Users with ||u||^2 below this (FP32) are scored in FP64 only.
+constexpr float kTinyNorm2 = 7.8886090522101181e-31f;  // 2^-100
+
+// Absolute part of the tie-check margin: subnormal products.
+__device__ __forceinline__ double rescore_abs_err(int f) { return (double)f * 2.8025969286496341e-45; }  // f 2^-148
+
+__device__ __forceinline__ bool row_all_zero(const float* __restrict__ r, int f) {
+  for (int k = 0; k < f; ++k)
+    if (r[k] != 0.f) return false;
+  return true;
 }
 
 __device__ __forceinline__ double rescore_rel_err(int f) {
@@ -219,12 +236,12 @@ __global__ void __launch_bounds__(256)
     const int64_t l0 = u * o.lists;
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
-    if (ss == 0.f) {  // zero user: every score is exactly 0
+    if (ss == 0.f && row_all_zero(ur, f)) {  // zero user: every score is exactly 0
       for (int k = 0; k < K; ++k) {
         out_idx[u * K + k] = k;
         out_score[u * K + k] = 0.0;
       }
-    } else if (over) {
+    } else if (over || ss < kTinyNorm2) {
       const int slot = atomicAdd(o.ovf_count, 1);
       o.ovf_list[slot] = (int32_t)u;
       n_over = 1;
@@ -311,8 +328,8 @@ __global__ void __launch_bounds__(128)
     bool over = false;
     for (int l = 0; l < o.lists; ++l) over |= o.n_cand[l0 + l] > o.cap;
     const float ss = o.tau_final[2 * u + 1];  // ||u||^2 as the collect kernel computed it
-    // zero users are done; overflowed users belong to the warp kernel
-    if (ss != 0.f && !over) {
+    // zero users are done; overflowed and tiny users belong to the warp kernel
+    if (ss >= kTinyNorm2 && !over) {
       const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
       const float tau = o.tau_final[2 * u];
       const double rel_e = rescore_rel_err(f);
@@ -338,7 +355,7 @@ __global__ void __launch_bounds__(128)
           break;
         }
         if (mode == 1) break;
-        const double e2 = 2.0 * rel_e * nu * (double)nmax;
+        const double e2 = 2.0 * rel_e * nu * (double)nmax + rescore_abs_err(f);
         bool amb = false;
         for (int p = 0; p + 1 < cnt; ++p) amb |= (ls[p * T + t] - ls[(p + 1) * T + t]) <= e2;
         if (!amb) break;
@@ -438,7 +455,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(kFull, ss, off);
     __syncwarp();
     const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
-    for (int mode = 0; mode < 2; ++mode) {
+    for (int mode = ss < kTinyNorm2 ? 1 : 0; mode < 2; ++mode) {
       WarpList Lw{s_s[w], s_id[w], 0, false, 0.0, 0};
       float nmax = 0.f;
       for (int64_t base = 0; base < n_items; base += 32) {
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       if (mode == 1) break;
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(kFull, nmax, off));
-      const double e2 = 2.0 * rel_e * nu * (double)nmax;
+      const double e2 = 2.0 * rel_e * nu * (double)nmax + rescore_abs_err(f);
       bool amb = false;
       for (int p0 = 0; p0 < Lw.cnt; p0 += 32) {
         const int p = p0 + lane;
