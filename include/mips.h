@@ -258,9 +258,12 @@ mips_status mips_server_destroy(mips_server_t srv);
 /*
  * Host-memory variant of mips_topk (method 0) / mips_topk_maximus
  * (method 1) / mips_select (method 2): copies users_host to the device,
- * runs the method and copies the results back, all on `stream`, then
- * synchronises it.  Host buffers are used as given (pinned memory gives
- * asynchronous copies).  Same result semantics as the device entry points.
+ * runs the method and copies the results back, then synchronises `stream`.
+ * Host buffers are used as given (pinned memory gives asynchronous copies).
+ * Same result semantics as the device entry points.  Method 0 with at least
+ * 131,072 users runs in up to four user chunks whose copies (on a stream the
+ * index owns) overlap the other chunks' compute on `stream`; mips_get_stats
+ * then reports the last chunk.
  */
 mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_users, int K,
                            int method, int32_t* out_idx_host, double* out_score_host,

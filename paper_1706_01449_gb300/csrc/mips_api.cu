@@ -114,6 +114,7 @@ struct mips_index_s {
   cudaEvent_t done = nullptr;   // end of the last call (orders calls on different streams)
   bool has_done = false;
   cudaStream_t last_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;  // host-buffer calls: copies beside the compute (created on first use)
   int64_t last_users = 0;
   int last_dtype = 0;
   int last_clusters = 0;
@@ -1137,8 +1138,9 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   if (st != MIPS_OK) return st;
   if (method < 0 || method > 2) return fail(MIPS_ERR_ARG, "method must be 0, 1 or 2");
   cudaStream_t s = (cudaStream_t)stream;
+  const int f = idx->f;
   // device staging for this call (stream-ordered allocation)
-  const size_t b_users = sizeof(float) * n_users * idx->f;
+  const size_t b_users = sizeof(float) * n_users * f;
   const size_t b_idx = sizeof(int32_t) * n_users * K;
   const size_t b_sc = sizeof(double) * n_users * K;
   char* stage = nullptr;
@@ -1146,25 +1148,72 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   float* d_users = (float*)stage;
   int32_t* d_idx = (int32_t*)(stage + ((b_users + 255) & ~size_t(255)));
   double* d_sc = (double*)(stage + ((b_users + 255) & ~size_t(255)) + ((b_idx + 255) & ~size_t(255)));
-  cudaError_t e = cudaMemcpyAsync(d_users, users_host, b_users, cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) {
+  // The blocked multiply runs in up to four chunks of users (at least 65,536
+  // each), so that the copies of one chunk overlap the compute of another:
+  // all host-to-device copies go first on the copy stream, each chunk's call
+  // waits for its own, and each chunk's results go back on the copy stream
+  // once its call is done.  Maximus and the selector take the batch whole.
+  int64_t chunk = n_users;
+  if (method == 0 && n_users >= 2 * 65536) {
+    chunk = std::max<int64_t>(65536, round_up((n_users + 3) / 4, 128));
+    if (!idx->copy_stream) MIPS_CUDA(cudaStreamCreateWithFlags(&idx->copy_stream, cudaStreamNonBlocking));
+  }
+  const int nch = (int)((n_users + chunk - 1) / chunk);
+  cudaStream_t cs = nch > 1 ? idx->copy_stream : s;
+  cudaEvent_t ev[9] = {};  // [0, 4): users copied, [4, 8): chunk done, [8]: copies back done
+  auto cleanup = [&](mips_status r) {
     cudaFreeAsync(stage, s);
-    return cuda_fail(e, "host-to-device copy of users");
+    for (cudaEvent_t& e : ev)
+      if (e) cudaEventDestroy(e);
+    return r;
+  };
+  cudaError_t e = cudaSuccess;
+  if (nch > 1) {
+    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[8], s);  // the staging allocation is ordered on s
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[8], 0);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "copy stream setup"));
   }
-  if (method == 0)
-    st = mips_topk(idx, d_users, n_users, K, d_idx, d_sc, stream);
-  else if (method == 1)
-    st = mips_topk_maximus(idx, d_users, n_users, K, d_idx, d_sc, stream);
-  else
-    st = mips_select(idx, d_users, n_users, K, d_idx, d_sc, stream, nullptr);
-  if (st == MIPS_OK) {
-    e = cudaMemcpyAsync(out_idx_host, d_idx, b_idx, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_score_host, d_sc, b_sc, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) st = cuda_fail(e, "device-to-host copy of results");
+  for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
+    e = cudaMemcpyAsync(d_users + u0 * f, users_host + u0 * f, sizeof(float) * n * f, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess && nch > 1) e = cudaEventRecord(ev[c], cs);
   }
-  cudaFreeAsync(stage, s);
-  if (st != MIPS_OK) return st;
-  return mips_sync(idx, stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "host-to-device copy of users"));
+  for (int c = 0; c < nch && st == MIPS_OK; ++c) {
+    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
+    if (nch > 1 && (e = cudaStreamWaitEvent(s, ev[c], 0)) != cudaSuccess) return cleanup(cuda_fail(e, "stream wait"));
+    if (method == 0)
+      st = mips_topk(idx, d_users + u0 * f, n, K, d_idx + u0 * K, d_sc + u0 * K, stream);
+    else if (method == 1)
+      st = mips_topk_maximus(idx, d_users, n_users, K, d_idx, d_sc, stream);
+    else
+      st = mips_select(idx, d_users, n_users, K, d_idx, d_sc, stream, nullptr);
+    if (st == MIPS_OK && nch > 1 && (e = cudaEventRecord(ev[4 + c], s)) != cudaSuccess)
+      return cleanup(cuda_fail(e, "event record"));
+  }
+  if (st != MIPS_OK) {
+    if (nch > 1) cudaStreamSynchronize(cs);  // (the staging is freed on s)
+    return cleanup(st);
+  }
+  for (int c = 0; c < nch && e == cudaSuccess; ++c) {
+    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
+    if (nch > 1) e = cudaStreamWaitEvent(cs, ev[4 + c], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_idx_host + u0 * K, d_idx + u0 * K, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out_score_host + u0 * K, d_sc + u0 * K, sizeof(double) * n * K, cudaMemcpyDeviceToHost, cs);
+  }
+  if (e == cudaSuccess && nch > 1) {  // s resumes (and frees the staging) after the copies back
+    e = cudaEventRecord(ev[8], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[8], 0);
+  }
+  if (e != cudaSuccess) {
+    if (nch > 1) cudaStreamSynchronize(cs);
+    return cleanup(cuda_fail(e, "device-to-host copy of results"));
+  }
+  st = mips_sync(idx, stream);
+  return cleanup(st);
 }
 
 mips_status mips_sync(mips_index_t idx, void* stream) {
@@ -1268,6 +1317,7 @@ void mips_free_index(mips_index_t idx) {
     cudaFree(idx->items_bf16);
     cudaFree(idx->item_aux);
   }
+  if (idx->copy_stream) cudaStreamDestroy(idx->copy_stream);
   cudaFree(idx->fit_cent);
   cudaFree(idx->err_dev);
   cudaFree(idx->stats_dev);
