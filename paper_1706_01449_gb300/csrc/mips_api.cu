@@ -1153,14 +1153,19 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   // all host-to-device copies go first on the copy stream, each chunk's call
   // waits for its own, and each chunk's results go back on the copy stream
   // once its call is done.  Maximus and the selector take the batch whole.
-  int64_t chunk = n_users;
+  constexpr int kMaxChunks = 8;
+  int64_t bnd[kMaxChunks + 1] = {0, n_users};  // chunk c is users [bnd[c], bnd[c + 1])
+  int nch = 1;
   if (method == 0 && n_users >= 2 * 65536) {
-    chunk = std::max<int64_t>(65536, round_up((n_users + 3) / 4, 128));
+    const int64_t chunk = std::max<int64_t>(65536, round_up((n_users + 3) / 4, 128));
+    nch = (int)((n_users + chunk - 1) / chunk);
+    for (int c = 0; c <= nch; ++c) bnd[c] = std::min<int64_t>(c * chunk, n_users);
     if (!idx->copy_stream) MIPS_CUDA(cudaStreamCreateWithFlags(&idx->copy_stream, cudaStreamNonBlocking));
   }
-  const int nch = (int)((n_users + chunk - 1) / chunk);
   cudaStream_t cs = nch > 1 ? idx->copy_stream : s;
-  cudaEvent_t ev[9] = {};  // [0, 4): users copied, [4, 8): chunk done, [8]: copies back done
+  // [0, nch): users copied, [kMaxChunks, kMaxChunks + nch): chunk done, last: copies back done
+  cudaEvent_t ev[2 * kMaxChunks + 1] = {};
+  const int ev_back = 2 * kMaxChunks;
   auto cleanup = [&](mips_status r) {
     cudaFreeAsync(stage, s);
     for (cudaEvent_t& e : ev)
@@ -1169,19 +1174,19 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   };
   cudaError_t e = cudaSuccess;
   if (nch > 1) {
-    for (int i = 0; i < 9 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[8], s);  // the staging allocation is ordered on s
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[8], 0);
+    for (int i = 0; i <= ev_back && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[ev_back], s);  // the staging allocation is ordered on s
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[ev_back], 0);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "copy stream setup"));
   }
   for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
+    const int64_t u0 = bnd[c], n = bnd[c + 1] - bnd[c];
     e = cudaMemcpyAsync(d_users + u0 * f, users_host + u0 * f, sizeof(float) * n * f, cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess && nch > 1) e = cudaEventRecord(ev[c], cs);
   }
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "host-to-device copy of users"));
   for (int c = 0; c < nch && st == MIPS_OK; ++c) {
-    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
+    const int64_t u0 = bnd[c], n = bnd[c + 1] - bnd[c];
     if (nch > 1 && (e = cudaStreamWaitEvent(s, ev[c], 0)) != cudaSuccess) return cleanup(cuda_fail(e, "stream wait"));
     if (method == 0)
       st = mips_topk(idx, d_users + u0 * f, n, K, d_idx + u0 * K, d_sc + u0 * K, stream);
@@ -1189,7 +1194,7 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
       st = mips_topk_maximus(idx, d_users, n_users, K, d_idx, d_sc, stream);
     else
       st = mips_select(idx, d_users, n_users, K, d_idx, d_sc, stream, nullptr);
-    if (st == MIPS_OK && nch > 1 && (e = cudaEventRecord(ev[4 + c], s)) != cudaSuccess)
+    if (st == MIPS_OK && nch > 1 && (e = cudaEventRecord(ev[kMaxChunks + c], s)) != cudaSuccess)
       return cleanup(cuda_fail(e, "event record"));
   }
   if (st != MIPS_OK) {
@@ -1197,16 +1202,16 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
     return cleanup(st);
   }
   for (int c = 0; c < nch && e == cudaSuccess; ++c) {
-    const int64_t u0 = c * chunk, n = std::min(chunk, n_users - u0);
-    if (nch > 1) e = cudaStreamWaitEvent(cs, ev[4 + c], 0);
+    const int64_t u0 = bnd[c], n = bnd[c + 1] - bnd[c];
+    if (nch > 1) e = cudaStreamWaitEvent(cs, ev[kMaxChunks + c], 0);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out_idx_host + u0 * K, d_idx + u0 * K, sizeof(int32_t) * n * K, cudaMemcpyDeviceToHost, cs);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(out_score_host + u0 * K, d_sc + u0 * K, sizeof(double) * n * K, cudaMemcpyDeviceToHost, cs);
   }
   if (e == cudaSuccess && nch > 1) {  // s resumes (and frees the staging) after the copies back
-    e = cudaEventRecord(ev[8], cs);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[8], 0);
+    e = cudaEventRecord(ev[ev_back], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[ev_back], 0);
   }
   if (e != cudaSuccess) {
     if (nch > 1) cudaStreamSynchronize(cs);
