@@ -168,6 +168,33 @@ def cpu_baseline(U, I, K, target_s=12.0, max_users=20000):
             "sample": f"first {n} users of the workload ({dt:.1f} s of FP64 brute force, full sort per user)"}
 
 
+def cpu_fp32_bmm(U, I, K, target_s=4.0, max_users=200000, block=4096):
+    """The plain multithreaded FP32 CPU form: blocked torch.mm on the host
+    (all threads) and torch.topk per block of users, on a bounded user
+    sample; users/sec.  FP32 and not tie-aware, so not exact: a speed
+    reference only."""
+    import numpy as np
+    import torch
+    It = torch.from_numpy(np.ascontiguousarray(I, dtype=np.float32)).t().contiguous()
+
+    def run(n):
+        for u0 in range(0, n, block):
+            S = torch.from_numpy(U[u0:min(n, u0 + block)]) @ It
+            torch.topk(S, K, dim=1)
+
+    n0 = min(block, U.shape[0])
+    t = time.perf_counter()
+    run(n0)
+    per_user = (time.perf_counter() - t) / n0
+    n = int(min(max_users, U.shape[0], max(n0, target_s / max(per_user, 1e-9))))
+    t = time.perf_counter()
+    run(n)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "users/s", "cores": torch.get_num_threads(),
+            "kind": "fp32 torch.mm + torch.topk on the host (not exact)",
+            "sample": f"first {n} users of the workload in blocks of {block} ({dt:.1f} s)"}
+
+
 def make_inputs(args, rank):
     from paper_1706_01449_gb300 import synth
     W = synth.WORKLOADS[args.workload]
@@ -427,9 +454,10 @@ def main():
                                 else f"derived: SMs x 128 FP32 FMA/clk x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"),
                 "algorithmic_flops_per_launch": flops}
 
-    cpu = None
+    cpu = cpu32 = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(U, I, K)
+        cpu32 = cpu_fp32_bmm(U, I, K)
 
     tiles = (stats["blocks_walked"] if walked else ((nU + 127) // 128) * ((nI + 255) // 256))
     line = {
@@ -447,6 +475,7 @@ def main():
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
+        "cpu_fp32_bmm": cpu32,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
