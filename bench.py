@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--serve", action="store_true",
                    help="serving loop (mips_server_*) on serve-1000000x128: saturated throughput, then Poisson "
                         "arrivals at 0.3 / 0.6 / 0.9 of it with p50 / p99 latency")
+    p.add_argument("--kmeans-spherical", action="store_true",
+                   help="Maximus / selector: spherical k-means (unit-length centroids)")
     p.add_argument("--fit-frac", type=float, default=0.0,
                    help="Maximus / selector: fit the centroids once on this fraction of the users before the "
                         "warm-up (Sec. IV-E dynamic users); timed steps then only assign users")
@@ -332,7 +334,7 @@ def main():
     index = None
     for cand in (["bf16", "fp32"] if dtype == "auto" else [dtype]):
         try:
-            index = mips.build_index(I_d, clusters=args.clusters, dtype=cand)
+            index = mips.build_index(I_d, clusters=args.clusters, dtype=cand, kmeans_spherical=args.kmeans_spherical)
             dtype = cand
             break
         except mips.MipsError as e:
@@ -472,6 +474,7 @@ def main():
                    **({"clusters": stats["clusters"]} if args.method != "bmm" else {}),
                    **({"autotune": tune} if tune else {}),
                    **({"centroids_fitted_before_timing": fit} if fit else {}),
+                   **({"kmeans": "spherical"} if args.kmeans_spherical else {}),
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -483,6 +486,7 @@ def main():
                                                        "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
         "candidates_per_user": stats["cand_emitted"] / nU, "rescored_per_user": stats["cand_rescored"] / nU,
         "users_overflow": stats["users_overflow"], "users_fp64": stats["users_fp64"],
+        **({"pairs_scored_per_user": stats["pairs_scored"] / nU} if walked else {}),
         # per warp and 16-score chunk of the tiles the score kernel processed
         # (128 users x 256 items each)
         "select_slow_chunk_frac": (stats["select_slow"] / (tiles * 8 * 8) if dtype == "bf16" and tiles else None),

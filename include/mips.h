@@ -72,6 +72,7 @@ typedef struct {
   double sample_frac; /* Optimus user sample fraction (Sec. V: 0.005) */
   int autotune;       /* reserved */
   uint64_t seed;      /* seed of the k-means initial centroids and samples */
+  int kmeans_spherical; /* 1: spherical k-means (Sec. IV-A): unit-length centroids, largest cosine */
 } mips_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -125,7 +125,7 @@ cudaError_t make_float_desc_keys(const float* x, int64_t n, uint32_t* keys, int3
 // ---- Maximus (maximus.cu) -------------------------------------------------
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
-                           uint32_t* absmax, float* scale, cudaStream_t s, int* launches);
+                           uint32_t* absmax, float* scale, bool spherical, cudaStream_t s, int* launches);
 // Assignment of the call's users to fitted centroids (cent_fit [C_fit][f]),
 // then the used clusters packed into slots 0.. of cent [C_eff][f] and the
 // assignment renumbered to those slots (C_eff >= the number of used clusters).

@@ -185,6 +185,22 @@ __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ sums
   cent[t] = (float)(s * (double)scale[1] / (double)n);
 }
 
+// Spherical k-means (Sec. IV-A: the clustering that minimises the user-
+// centroid angles; the paper itself runs plain k-means as the faster one):
+// centroids scaled to unit length after the draw and after every update, so
+// the assignment step picks the largest cosine (||c_j||^2 / 2 is the same for
+// every centroid).  A zero centroid stays zero.
+__global__ void normalize_rows_kernel(float* __restrict__ cent, int C, int f) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= C) return;
+  float* c = cent + (int64_t)j * f;
+  float s = 0.f;
+  for (int k = 0; k < f; ++k) s = __fmaf_rn(c[k], c[k], s);
+  if (!(s > 0.f)) return;
+  const float n = __fsqrt_rn(s);
+  for (int k = 0; k < f; ++k) c[k] = __fdiv_rn(c[k], n);
+}
+
 // ---------------------------------------------------------------- bounds
 // cos_b[j] (as order-preserving bits, initialised to +1): a lower bound of
 // the smallest cosine between a member of cluster j and c_j.  Zero users are
@@ -973,8 +989,12 @@ cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, co
 
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
-                           uint32_t* absmax, float* scale, cudaStream_t s, int* launches) {
+                           uint32_t* absmax, float* scale, bool spherical, cudaStream_t s, int* launches) {
   gather_rows_i64<<<(unsigned)((C * f + 255) / 256), 256, 0, s>>>(users, init_ids_dev, C, f, cent);
+  if (spherical) {
+    normalize_rows_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f);
+    *launches += 1;
+  }
   cudaError_t e = cudaMemsetAsync(absmax, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
   absmax_kernel<<<152 * 4, 256, 0, s>>>(users, n_users * f, absmax);
@@ -1001,6 +1021,10 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
     }
     kmeans_update_kernel<<<(C * f + 255) / 256, 256, 0, s>>>(sums, counts, C, f, scale, cent);
     *launches += 4;
+    if (spherical) {
+      normalize_rows_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f);
+      *launches += 1;
+    }
   }
   return cudaGetLastError();
 }

@@ -467,7 +467,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
                              ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
                              ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
-                             ws.at<float>(o_scale), s, &idx->launches));
+                             ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, s, &idx->launches));
   }
   mips_status st;
   if ((st = end_stage(idx, ST_KMEANS, s)) != MIPS_OK) return st;
@@ -769,6 +769,7 @@ void mips_default_options(mips_options* opt) {
   opt->sample_frac = 0.005;
   opt->autotune = 0;
   opt->seed = 0;
+  opt->kmeans_spherical = 0;
 }
 
 mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int clusters,
@@ -911,7 +912,7 @@ mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t 
   MIPS_CUDA(maximus_kmeans(users_dev, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
                            ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
                            ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
-                           ws.at<float>(o_scale), s, &idx->launches));
+                           ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, s, &idx->launches));
   if (idx->fit_cap < (int64_t)C * f) {  // (every call on this index is ordered after idx->done)
     if (idx->has_done) MIPS_CUDA(cudaEventSynchronize(idx->done));
     if (idx->fit_cent) MIPS_CUDA(cudaFree(idx->fit_cent));

@@ -40,7 +40,8 @@ class MipsError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("kmeans_iters", ctypes.c_int), ("block_items", ctypes.c_int),
-                ("sample_frac", ctypes.c_double), ("autotune", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("sample_frac", ctypes.c_double), ("autotune", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("kmeans_spherical", ctypes.c_int)]
 
 
 class SelectReport(ctypes.Structure):
@@ -189,7 +190,8 @@ class Index:
 
 
 def build_index(items, clusters: int = 8, dtype: str = "bf16", kmeans_iters: int = 3,
-                block_items: int = 0, sample_frac: float = 0.005, seed: int = 0, stream=None) -> Index:
+                block_items: int = 0, sample_frac: float = 0.005, seed: int = 0, kmeans_spherical: bool = False,
+                stream=None) -> Index:
     lib = load()
     items = _dev_f32(items, "items")
     opt = Options()
@@ -199,6 +201,7 @@ def build_index(items, clusters: int = 8, dtype: str = "bf16", kmeans_iters: int
     opt.block_items = block_items
     opt.sample_frac = sample_frac
     opt.seed = seed
+    opt.kmeans_spherical = 1 if kmeans_spherical else 0
     h = ctypes.c_void_p()
     _check(lib.mips_build_index(ctypes.c_void_p(items.data_ptr()), items.shape[0], items.shape[1], clusters,
                                 ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)))

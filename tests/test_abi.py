@@ -36,6 +36,7 @@ def test_version_and_defaults():
     lib.mips_default_options(ctypes.byref(opt))
     assert opt.dtype == mips.DTYPES["bf16"] and opt.kmeans_iters == 3
     assert abs(opt.sample_frac - 0.005) < 1e-12
+    assert opt.kmeans_spherical == 0
 
 
 def test_argument_errors_need_no_gpu():

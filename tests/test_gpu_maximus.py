@@ -9,7 +9,8 @@ through the C ABI:
     "monotonicity of sorted index lists");
   * pruning invariant: every item a user did not score has
     ||u|| CBound < (the user's K-th score);
-  * k-means: each user sits at a nearest centroid, centroids are member means;
+  * k-means: each user sits at a nearest centroid, centroids are member means
+    (spherical k-means: unit vectors along the member means);
   * pruning happens on clustered users; degenerate cases (C = 1, K = n_items,
     zero users, duplicate items)."""
 import math
@@ -115,6 +116,29 @@ def test_kmeans_invariants():
         if m.any():
             np.testing.assert_allclose(cent[j], U64[m].mean(axis=0), rtol=1e-4, atol=1e-5)
     assert d.shape == (U.shape[0], cent.shape[0])
+
+
+@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+def test_spherical_kmeans(dtype):
+    """kmeans_spherical (Sec. IV-A): exact results; every centroid is the unit
+    vector along its members' mean (of the last assignment step)."""
+    U, I = clustered(2500, 900, 12, seed=8)
+    K, C = 10, 12
+    index = mips.build_index(torch.from_numpy(I).cuda(), clusters=C, dtype=dtype, kmeans_spherical=True)
+    idx, sc = mips.topk_maximus(index, torch.from_numpy(U).cuda(), K)
+    mips.sync(index)
+    Ce = mips.get_stats(index)["clusters"]
+    nU, f = U.shape
+    a = mips.get_buffer(index, "assign", torch.int32, (nU,)).cpu().numpy()
+    cent = mips.get_buffer(index, "centroids", torch.float32, (Ce, f)).cpu().numpy().astype(np.float64)
+    check_against_oracle(U, I, K, idx.cpu().numpy(), sc.cpu().numpy())
+    U64 = U.astype(np.float64)
+    for j in range(Ce):
+        m = a == j
+        if m.any():
+            mu = U64[m].mean(axis=0)
+            np.testing.assert_allclose(cent[j], mu / np.linalg.norm(mu), rtol=1e-4, atol=1e-5)
+    index.close()
 
 
 @pytest.mark.parametrize("dtype", ["fp32", "bf16"])
