@@ -1149,8 +1149,8 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   float* d_users = (float*)stage;
   int32_t* d_idx = (int32_t*)(stage + ((b_users + 255) & ~size_t(255)));
   double* d_sc = (double*)(stage + ((b_users + 255) & ~size_t(255)) + ((b_idx + 255) & ~size_t(255)));
-  // The blocked multiply runs in up to four chunks of users (at least 65,536
-  // each), so that the copies of one chunk overlap the compute of another:
+  // The blocked multiply runs in up to eight chunks of users, so that the
+  // copies of one chunk overlap the compute of another:
   // all host-to-device copies go first on the copy stream, each chunk's call
   // waits for its own, and each chunk's results go back on the copy stream
   // once its call is done.  Maximus and the selector take the batch whole.
@@ -1158,9 +1158,16 @@ mips_status mips_topk_host(mips_index_t idx, const float* users_host, int64_t n_
   int64_t bnd[kMaxChunks + 1] = {0, n_users};  // chunk c is users [bnd[c], bnd[c + 1])
   int nch = 1;
   if (method == 0 && n_users >= 2 * 65536) {
-    const int64_t chunk = std::max<int64_t>(65536, round_up((n_users + 3) / 4, 128));
-    nch = (int)((n_users + chunk - 1) / chunk);
-    for (int c = 0; c <= nch; ++c) bnd[c] = std::min<int64_t>(c * chunk, n_users);
+    // whole waves of 128-user tiles over the SMs (the score kernel deals its
+    // tiles round-robin), a short first chunk so the compute starts early,
+    // the partial wave at the end
+    const int64_t wave = 128ll * idx->num_sms;
+    const int64_t first = std::min<int64_t>(3 * wave, n_users / 2);
+    int64_t rest = 6 * wave;
+    if (n_users - first > rest * (kMaxChunks - 1))
+      rest = round_up((n_users - first + kMaxChunks - 2) / (kMaxChunks - 1), wave);
+    bnd[1] = first;
+    for (nch = 1; bnd[nch] < n_users; ++nch) bnd[nch + 1] = std::min<int64_t>(bnd[nch] + rest, n_users);
     if (!idx->copy_stream) MIPS_CUDA(cudaStreamCreateWithFlags(&idx->copy_stream, cudaStreamNonBlocking));
   }
   cudaStream_t cs = nch > 1 ? idx->copy_stream : s;
