@@ -262,7 +262,7 @@ mips_status mips_server_destroy(mips_server_t srv);
  * runs the method and copies the results back, then synchronises `stream`.
  * Host buffers are used as given (pinned memory gives asynchronous copies).
  * Same result semantics as the device entry points.  Method 0 with at least
- * 131,072 users runs in up to four user chunks whose copies (on a stream the
+ * 131,072 users runs in up to eight user chunks whose copies (on a stream the
  * index owns) overlap the other chunks' compute on `stream`; mips_get_stats
  * then reports the last chunk.
  */
