@@ -55,28 +55,33 @@ __global__ void row_norm_ub_kernel(const float* __restrict__ x, int64_t n, int f
   }
 }
 
-__global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role,
-                                  __nv_bfloat16* __restrict__ out, int64_t n_rows_out,
-                                  float2* __restrict__ aux, int* err) {
-  int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (row >= n_rows_out) return;
+// Rows per warp of the quantisation kernel: the loads of all of them are
+// issued before any row's arithmetic (f <= 128: four elements per lane).
+constexpr int kQuantRows = 4;
+
+// One row whose elements this lane holds in v (element lane + 32 j in v[j]).
+__device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row, int64_t n, int f, int fp, int role,
+                                               __nv_bfloat16* __restrict__ out, float2* __restrict__ aux, int* err,
+                                               int lane) {
   __nv_bfloat16* o = out + row * fp;
   if (row >= n) {  // padding rows
     for (int k = lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
     return;
   }
-  const float* r = x + row * f;
   float ss_x = 0.f, ss_t = 0.f, ss_d = 0.f;
-  for (int k = lane; k < f; k += 32) {
-    float v = r[k];
-    __nv_bfloat16 q = __float2bfloat16_rn(v);
-    float t = __bfloat162float(q);
-    float d = __fsub_rn(v, t);  // exact: t is v rounded to 8 significant bits
-    ss_x = __fmaf_rn(v, v, ss_x);
-    ss_t = __fmaf_rn(t, t, ss_t);
-    ss_d = __fmaf_rn(d, d, ss_d);
-    o[k] = q;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = lane + 32 * j;
+    if (k < f) {
+      const float x = v[j];
+      const __nv_bfloat16 q = __float2bfloat16_rn(x);
+      const float t = __bfloat162float(q);
+      const float d = __fsub_rn(x, t);  // exact: t is x rounded to 8 significant bits
+      ss_x = __fmaf_rn(x, x, ss_x);
+      ss_t = __fmaf_rn(t, t, ss_t);
+      ss_d = __fmaf_rn(d, d, ss_d);
+      o[k] = q;
+    }
   }
   ss_x = warp_sum(ss_x);
   ss_t = warp_sum(ss_t);
@@ -99,6 +104,28 @@ __global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f,
     }
   }
   for (int k = f + 2 + lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
+}
+
+// A warp per kQuantRows consecutive rows.
+__global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role,
+                                  __nv_bfloat16* __restrict__ out, int64_t n_rows_out,
+                                  float2* __restrict__ aux, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * kQuantRows;
+  if (row0 >= n_rows_out) return;
+  float v[kQuantRows][4];
+#pragma unroll
+  for (int q = 0; q < kQuantRows; ++q) {
+    const int64_t row = row0 + q;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = lane + 32 * j;
+      v[q][j] = (row < n && k < f) ? x[row * f + k] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kQuantRows; ++q)
+    if (row0 + q < n_rows_out) quant_bf16_row(v[q], row0 + q, n, f, fp, role, out, aux, err, lane);
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ x, const int32_t* __restrict__ perm,
@@ -184,8 +211,8 @@ void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* er
 void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void* out_bf16,
                        int64_t n_rows_out, float2* aux, int* err, cudaStream_t s) {
   if (n_rows_out <= 0) return;
-  int wpb = 8;
-  quant_bf16_kernel<<<(unsigned)((n_rows_out + wpb - 1) / wpb), wpb * 32, 0, s>>>(
+  const int64_t rows_per_block = 8 * kQuantRows;
+  quant_bf16_kernel<<<(unsigned)((n_rows_out + rows_per_block - 1) / rows_per_block), 8 * 32, 0, s>>>(
       x, n, f, fp, role, (__nv_bfloat16*)out_bf16, n_rows_out, aux, err);
 }
 
