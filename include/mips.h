@@ -85,7 +85,10 @@ void mips_default_options(mips_options* opt);
  * fixed here and used by mips_topk_maximus.  The index copies the items
  * (FP32 master + quantised copies + per-item bounds); the caller may free
  * items_dev once the stream has passed this call.
- * Limits: 1 <= f <= 128, 1 <= n_items < 2^31, 1 <= clusters <= 4096.
+ * Limits: 1 <= f <= 128, 1 <= n_items < 2^31, 1 <= clusters <= 4096;
+ * options: 0 <= kmeans_iters <= 100, block_items >= 0, 0 < sample_frac <= 1,
+ * kmeans_spherical 0 or 1 (else MIPS_ERR_ARG); dtype MIPS_FP32 or MIPS_BF16
+ * (MIPS_FP8_E4M3: MIPS_ERR_UNIMPLEMENTED).
  * *out receives the handle; free it with mips_free_index.
  */
 mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int clusters,

@@ -786,6 +786,9 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   if (opt) o = *opt;
   if (o.dtype != MIPS_FP32 && o.dtype != MIPS_BF16) return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d not built", o.dtype);
   if (o.kmeans_iters < 0 || o.kmeans_iters > 100) return fail(MIPS_ERR_ARG, "kmeans_iters out of range");
+  if (o.block_items < 0) return fail(MIPS_ERR_ARG, "block_items must be >= 0 (0 = default)");
+  if (!(o.sample_frac > 0.0 && o.sample_frac <= 1.0)) return fail(MIPS_ERR_ARG, "sample_frac out of range (0,1]");
+  if (o.kmeans_spherical != 0 && o.kmeans_spherical != 1) return fail(MIPS_ERR_ARG, "kmeans_spherical must be 0 or 1");
   cudaStream_t s = (cudaStream_t)stream;
 
   mips_index_s* idx = new (std::nothrow) mips_index_s();

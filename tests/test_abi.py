@@ -51,6 +51,17 @@ def test_argument_errors_need_no_gpu():
     assert lib.mips_build_index(fake, 10, 129, 2, ctypes.byref(opt), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
     assert lib.mips_build_index(fake, 0, 4, 2, ctypes.byref(opt), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
     assert lib.mips_build_index(fake, 10, 4, 0, ctypes.byref(opt), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
+    for field, bad in (("kmeans_iters", 101), ("kmeans_iters", -1), ("block_items", -5), ("sample_frac", 0.0),
+                       ("sample_frac", 1.5), ("sample_frac", float("nan")), ("kmeans_spherical", 2)):
+        o2 = mips.Options()
+        lib.mips_default_options(ctypes.byref(o2))
+        setattr(o2, field, bad)
+        assert lib.mips_build_index(fake, 10, 4, 2, ctypes.byref(o2), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG, field
+    o2 = mips.Options()
+    lib.mips_default_options(ctypes.byref(o2))
+    o2.dtype = mips.DTYPES.get("fp8", 2)
+    assert lib.mips_build_index(fake, 10, 4, 2, ctypes.byref(o2), None, ctypes.byref(h)) == mips.MIPS_ERR_UNIMPLEMENTED
+    assert lib.mips_build_index(fake, 10, 4, 4097, ctypes.byref(opt), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
     assert lib.mips_topk(None, fake, 4, 1, fake, fake, None) == mips.MIPS_ERR_ARG
     assert lib.mips_topk_maximus(None, fake, 4, 1, fake, fake, None) == mips.MIPS_ERR_ARG
     assert lib.mips_select(None, fake, 4, 1, fake, fake, None, None) == mips.MIPS_ERR_ARG
