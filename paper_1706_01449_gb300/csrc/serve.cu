@@ -1,5 +1,8 @@
 // Serving runtime: a request queue over one index with continuous batching
-// (mips_server_* in include/mips.h).  Host code only.
+// (mips_server_* in include/mips.h).  Host code only.  Sec. III-A notes that
+// the index also serves a subset of users at a time, as in a model-serving
+// system that collects requests; each batch here is such a subset and gets
+// the same exact top-K as the batch problem.
 //
 // Threads: the caller's (submit / wait), a scheduler that forms batches and
 // launches them on free stream slots, and a completion thread that polls the
