@@ -33,18 +33,22 @@ EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_m
 
 
 class MipsError(RuntimeError):
+    """A non-OK status from the library; ``status`` is the mips_status code
+    and the message is mips_last_error()."""
     def __init__(self, status: int, message: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
 
 
 class Options(ctypes.Structure):
+    """mips_options (include/mips.h)."""
     _fields_ = [("dtype", ctypes.c_int), ("kmeans_iters", ctypes.c_int), ("block_items", ctypes.c_int),
                 ("sample_frac", ctypes.c_double), ("autotune", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("kmeans_spherical", ctypes.c_int)]
 
 
 class SelectReport(ctypes.Structure):
+    """mips_select_report: the Optimus decision and its estimates."""
     _fields_ = [("choice", ctypes.c_int), ("t_build", ctypes.c_double), ("q_user", ctypes.c_double),
                 ("m_user", ctypes.c_double), ("sample_users", ctypes.c_int64),
                 ("est_index", ctypes.c_double), ("est_bmm", ctypes.c_double)]
@@ -54,23 +58,27 @@ class SelectReport(ctypes.Structure):
 
 
 class TuneReport(ctypes.Structure):
+    """mips_tune_report: the autotuner's choice and the candidates it timed."""
     _fields_ = [("clusters", ctypes.c_int), ("block_items", ctypes.c_int), ("sample_users", ctypes.c_int64),
                 ("n_tried", ctypes.c_int), ("tried_clusters", ctypes.c_int * 32), ("tried_block", ctypes.c_int * 32),
                 ("tried_est", ctypes.c_double * 32), ("t_tune", ctypes.c_double)]
 
 
 class ServerOptions(ctypes.Structure):
+    """mips_server_options: method, stream slots, batch size cap, memory budget."""
     _fields_ = [("method", ctypes.c_int), ("slots", ctypes.c_int), ("max_batch_users", ctypes.c_int64),
                 ("mem_budget", ctypes.c_int64)]
 
 
 class RequestInfo(ctypes.Structure):
+    """mips_request_info: a served request's timestamps and the batch it ran in."""
     _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
                 ("batch", ctypes.c_int64), ("batch_users", ctypes.c_int64), ("batch_K", ctypes.c_int),
                 ("slot", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
+    """mips_stats: counters and per-stage times of the index's last call."""
     _fields_ = [("cand_emitted", ctypes.c_uint64), ("cand_rescored", ctypes.c_uint64),
                 ("users_overflow", ctypes.c_uint64), ("users_fp64", ctypes.c_uint64),
                 ("pairs_scored", ctypes.c_uint64), ("blocks_walked", ctypes.c_uint64),
@@ -143,6 +151,7 @@ def load():
 
 
 def last_error() -> str:
+    """The calling thread's last error message from the library."""
     return load().mips_last_error().decode()
 
 
@@ -173,11 +182,13 @@ class Index:
 
     @property
     def handle(self):
+        """The mips_index_t pointer (raises once the index is freed)."""
         if self._h is None:
             raise ValueError("index already freed")
         return self._h
 
     def close(self):
+        """mips_free_index (waits for the index's work first); idempotent."""
         if self._h is not None and _lib is not None:
             _lib.mips_free_index(self._h)
         self._h = None
@@ -192,6 +203,9 @@ class Index:
 def build_index(items, clusters: int = 8, dtype: str = "bf16", kmeans_iters: int = 3,
                 block_items: int = 0, sample_frac: float = 0.005, seed: int = 0, kmeans_spherical: bool = False,
                 stream=None) -> Index:
+    """mips_build_index over a 2-D float32 CUDA tensor of items [n_items, f]:
+    ``clusters`` is |C| for Maximus, ``dtype`` the candidate pass ("bf16" or
+    "fp32"), the rest are mips_options fields.  Returns an owning Index."""
     lib = load()
     items = _dev_f32(items, "items")
     opt = Options()
@@ -313,10 +327,12 @@ def topk_host(index: Index, users_host, K: int, method: str = "bmm", out_idx=Non
 
 
 def sync(index: Index, stream=None):
+    """mips_sync: wait for the stream and raise on any device-side error."""
     _check(load().mips_sync(index.handle, _stream_ptr(stream)))
 
 
 def get_stats(index: Index) -> dict:
+    """mips_get_stats of the index's last call, as a dict."""
     st = Stats()
     _check(load().mips_get_stats(index.handle, ctypes.byref(st)))
     return st.as_dict()
@@ -360,6 +376,7 @@ def topk_noalloc(items, users, K: int, out_idx, out_score, stream=None):
 
 
 def free_index(index: Index):
+    """Free the index now (same as index.close())."""
     index.close()
 
 
@@ -402,6 +419,7 @@ class Server:
         return oi, osc, {k: getattr(info, k) for k, _ in RequestInfo._fields_}
 
     def close(self):
+        """mips_server_destroy: finish the queued requests and release the server."""
         if self._h is not None:
             _check(load().mips_server_destroy(self._h))
             self._h = None
