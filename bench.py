@@ -1,20 +1,37 @@
 """Benchmark: exact batch top-K MIPS throughput (users/sec) on GB300.
 
-One step = one mips_topk call (the whole hot path: user quantisation,
-fused score + select, exact rescore) over all users of the workload, with
-users and items already resident in HBM.  Prints ONE JSON line (rank 0).
-The blocked multiply and Maximus steps go through mips_topk_graph on a
-created stream (the call is captured into a CUDA graph in the warm-up and
-replayed); --no-graph runs the plain calls.
+Default workload: the KDD shape -- 1,000,000 clustered users x 624,961
+items, f = 51, K = 10 -- searched with Maximus (Sec. IV, Algorithm 1) with
+its cluster count |C| and item block B picked by the library's autotuner.
+One step = one Maximus call over all users (user quantisation, k-means,
+theta_b + CBound, per-cluster lists, the two-pass tensor-core walk, the
+exact rescore), replayed from a captured CUDA graph on a created stream,
+with users and items already resident in HBM.  The step's value is the
+line's `value`.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype bf16|fp32]
-                    [--method bmm|maximus|select] [--f 50] [--k 10]
-                    [--impl ours|reference] [--no-graph]
+In the same run, on the same inputs, `legs` times the other forms the
+metric compares: the BF16 blocked multiply with fused select (Sec. III-B,
+graph replays) and the plain FP32 CUDA-core blocked multiply (plain calls),
+each with its users/sec and its own roofline.  `e2e` is the default form
+through the host-buffer entry point (pinned host users in, host results
+out, copies inside the timed region).  `cpu_baseline` is the FP64 oracle
+on a bounded user sample on the host cores; the GPU's results for those
+users are compared with the oracle's (`exact_sample`).
 
-Under torchrun (N > 1) every rank runs the same workload on its own users
-(seed = rank) with no collective on the data path: weak scaling; the time
-is the max over ranks.  --impl reference times the CPU oracle (FP64 brute
-force, all host cores) on a bounded user sample per step.
+Rooflines (every kernel): the slowest of three ceilings -- tensor (or FP32
+FMA) FLOPs at the measured peak, HBM bytes at the measured copy bandwidth,
+and the select's issue rate at one instruction per score -- over the
+kernel's own device time (CUDA events around its launches).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--workload NAME] [--method maximus|bmm|select]
+                    [--dtype bf16|fp32] [--f F] [--k K] [--legs bmm,fp32]
+                    [--impl ours|reference] [--serve]
+
+Under torchrun (N > 1) the job's user matrix is N x the workload's users;
+rank r scores its contiguous slice (weak scaling) with no collective on the
+data path; the time is the max over ranks.  --impl reference times the CPU
+oracle (FP64 brute force, all host cores) on a bounded user sample per step.
 """
 from __future__ import annotations
 
@@ -31,22 +48,28 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "netflix-480189x17770"
-SM_COUNT_FALLBACK = 152
+WORKLOAD = "kdd-1000000x624961"
+METRIC = "exact top-K users/sec (BF16/FP8+rescore & Maximus vs FP32 BMM), % roofline"
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--dtype", default="auto", choices=["auto", "bf16", "fp32"])
-    p.add_argument("--method", default="bmm", choices=["bmm", "maximus", "select"])
+    p.add_argument("--method", default="maximus", choices=["bmm", "maximus", "select"])
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--f", type=int, default=50)
+    p.add_argument("--f", type=int, default=0, help="dimension (Netflix shape: 10, 50 or 100; default 50; others: their own f)")
     p.add_argument("--k", type=int, default=10)
-    p.add_argument("--clusters", type=int, default=64)
+    p.add_argument("--clusters", type=int, default=64, help="|C| when the autotuner is off")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="Maximus / selector: keep --clusters and the default block instead of mips_autotune")
+    p.add_argument("--legs", default="bmm,fp32",
+                   help="extra forms timed after the main steps on the same inputs: comma list of bmm (BF16 "
+                        "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply); 'none' for none")
+    p.add_argument("--leg-steps", type=int, default=3)
     p.add_argument("--users", type=int, default=0,
                    help="use only the first N users (profiling captures; not the benchmark workload)")
     p.add_argument("--no-e2e", action="store_true")
@@ -60,9 +83,7 @@ def parse():
     p.add_argument("--fit-frac", type=float, default=0.0,
                    help="Maximus / selector: fit the centroids once on this fraction of the users before the "
                         "warm-up (Sec. IV-E dynamic users); timed steps then only assign users")
-    p.add_argument("--autotune", action="store_true",
-                   help="Maximus / selector: pick |C| and B with mips_autotune before the warm-up (timed separately)")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 from paper_1706_01449_gb300.shard import dist_env, job_throughput, max_over_ranks, rank_users  # noqa: E402
@@ -153,30 +174,76 @@ def traffic_for(kernel_key, src_hash):
     return e.get("bytes_per_launch")
 
 
+def roofline(dtype, f, scores, kernel_ms, hbm_bytes, peaks, peak_src, sm_count, clock_mhz, kernel_key, src_files):
+    """The kernel's roofline: the slowest of three ceilings over its device time.
+
+    * tensor (BF16: 2 f FLOP per score at the measured BF16 burst peak) or,
+      for the FP32 CUDA-core form, FP32 FMA (SMs x 128 FMA/clk x 2 x clock);
+    * HBM: the algorithmic bytes at the measured copy bandwidth;
+    * select issue: one warp instruction slot per 32 scores on every SM
+      sub-partition (SMs x 4 x 32 scores/clk), the algorithmic minimum of
+      looking at every score once.
+    `frac` is that ceiling's time over the measured time (= achieved / peak
+    in the ceiling's own unit)."""
+    s = kernel_ms / 1e3
+    flops = 2.0 * f * scores
+    clk = clock_mhz * 1e6
+    ceil = {}
+    if dtype == "bf16":
+        pk = peaks["bf16_tflops"]
+        ceil["tensor"] = {"time_ms": flops / (pk * 1e12) * 1e3, "achieved": flops / s / 1e12, "peak": pk,
+                          "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 burst"}
+    else:
+        pk = sm_count * 128 * 2 * clk / 1e12
+        ceil["alu_fp32_fma"] = {"time_ms": flops / (pk * 1e12) * 1e3, "achieved": flops / s / 1e12, "peak": pk,
+                                "unit": "TFLOP/s",
+                                "peak_source": f"derived: {sm_count} SMs x 128 FP32 FMA/clk x 2 x {clock_mhz:.0f} MHz"}
+    hb = peaks["hbm_gbs"]
+    ceil["hbm"] = {"time_ms": hbm_bytes / (hb * 1e9) * 1e3, "achieved": hbm_bytes / s / 1e9, "peak": hb,
+                   "unit": "GB/s", "peak_source": f"{peak_src} copy bandwidth"}
+    sp = sm_count * 4 * 32 * clk / 1e9
+    ceil["select_issue"] = {"time_ms": scores / (sp * 1e9) * 1e3, "achieved": scores / s / 1e9, "peak": sp,
+                            "unit": "G scores/s",
+                            "peak_source": f"derived: {sm_count} SMs x 4 sub-partitions x 32 lanes x {clock_mhz:.0f} "
+                                           f"MHz (one instruction per score)"}
+    name = max(ceil, key=lambda k: ceil[k]["time_ms"])
+    c = ceil[name]
+    bound = {"tensor": "tensor", "hbm": "hbm"}.get(name, "alu")
+    return {"bound": bound, "ceiling": name, "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
+            "frac": c["achieved"] / c["peak"], "traffic": traffic_for(kernel_key, kernel_source_hash(src_files)),
+            "kernel": kernel_key.split()[0], "kernel_ms": kernel_ms, "peak_source": c["peak_source"],
+            "algorithmic": {"scores": scores, "flops": flops, "hbm_bytes": hbm_bytes},
+            "ceilings_ms": {k: v["time_ms"] for k, v in ceil.items()},
+            "fracs": {k: v["time_ms"] / kernel_ms for k, v in ceil.items()}}
+
+
 def cpu_baseline(U, I, K, target_s=12.0, max_users=20000):
     """The oracle as it stands (FP64 brute force, full sort, OpenMP over all
-    host cores) on a bounded user sample; users/sec."""
+    host cores) on a bounded user sample; users/sec, plus the oracle's
+    results for those users (the first n of the workload)."""
     import oracle
     oracle.build()
-    n0 = min(64, U.shape[0])
+    n0 = min(32, U.shape[0])
     t = time.perf_counter()
     _, _, nt = oracle.topk(U[:n0], I, K, return_threads=True)
     per_user = (time.perf_counter() - t) / n0
     n = int(min(max_users, U.shape[0], max(n0, target_s / max(per_user, 1e-9))))
     t = time.perf_counter()
-    _, _, nt = oracle.topk(U[:n], I, K, return_threads=True)
+    idx, sc, nt = oracle.topk(U[:n], I, K, return_threads=True)
     dt = time.perf_counter() - t
-    return {"value": n / dt, "unit": "users/s", "cores": nt, "kind": "oracle",
-            "sample": f"first {n} users of the workload ({dt:.1f} s of FP64 brute force, full sort per user)"}
+    return ({"value": n / dt, "unit": "users/s", "cores": nt, "kind": "oracle",
+             "sample": f"first {n} users of the workload ({dt:.1f} s of FP64 brute force, full sort per user)"},
+            idx, sc)
 
 
 def cpu_fp32_bmm(U, I, K, target_s=4.0, max_users=200000, block=4096):
     """The plain multithreaded FP32 CPU form: blocked torch.mm on the host
     (all threads) and torch.topk per block of users, on a bounded user
     sample; users/sec.  FP32 and not tie-aware, so not exact: a speed
-    reference only."""
+    reference only.  Blocks are capped so a block's scores stay near 1 GB."""
     import numpy as np
     import torch
+    block = max(16, min(block, (1 << 28) // max(1, I.shape[0])))
     It = torch.from_numpy(np.ascontiguousarray(I, dtype=np.float32)).t().contiguous()
 
     def run(n):
@@ -197,10 +264,22 @@ def cpu_fp32_bmm(U, I, K, target_s=4.0, max_users=200000, block=4096):
             "sample": f"first {n} users of the workload in blocks of {block} ({dt:.1f} s)"}
 
 
+def exact_sample(gpu_idx, gpu_sc, ref_idx, ref_sc):
+    """The GPU's rows for the oracle's sample users against the oracle's:
+    index equality and the largest score error relative to |oracle score|
+    (floor 1e-30)."""
+    import numpy as np
+    n = ref_idx.shape[0]
+    gi, gs = gpu_idx[:n], gpu_sc[:n]
+    err = np.abs(gs - ref_sc) / np.maximum(np.abs(ref_sc), 1e-30)
+    return {"users": int(n), "indices_equal": bool(np.array_equal(gi, ref_idx)),
+            "rows_differing": int((gi != ref_idx).any(axis=1).sum()), "max_rel_score_err": float(err.max())}
+
+
 def make_inputs(args, rank):
     from paper_1706_01449_gb300 import synth
     W = synth.WORKLOADS[args.workload]
-    f = args.f if "fs" in W else W["f"]
+    f = (args.f or W["fs"][1]) if "fs" in W else W["f"]
     n = args.users if getattr(args, "users", 0) else None
     U = rank_users(args.workload, rank, f=f, n=n)
     I = synth.make_items(W, seed=0, f=f)
@@ -208,6 +287,8 @@ def make_inputs(args, rank):
 
 
 def run_reference(args):
+    """The oracle as it stands (FP64 brute force, full sort per user, all
+    host cores) on a bounded sample of the workload's users per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -230,7 +311,7 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     ms = 1e3 * sum(times) / len(times)
     value = n / (ms / 1e3)
-    line = {"impl": "reference", "metric": "exact top-K users/sec", "value": value, "unit": "users/s",
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "users/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
@@ -303,13 +384,54 @@ def run_serve(args):
                       "saturated_requests_per_s": sat_rate, "loads": loads}), flush=True)
 
 
-def main():
-    args = parse()
+def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk, workload):
+    """Roofline of the call's dominant kernel from its counters: the fused
+    score + select kernel (every (user, item) pair), or the Maximus walk
+    (the pairs it scored).  Algorithmic bytes: user rows and item rows once
+    in the operand dtype, candidate lists out (8 bytes each)."""
+    scores = stats["pairs_scored"] if walked else nU * nI
+    b = 2 if dtype == "bf16" else 4
+    hbm = nU * f * b + nI * f * b + 8 * stats["cand_emitted"]
+    kms = stats["ms_kernel"] or (stats["ms_walk"] if walked else stats["ms_score"])
+    kern = "tc_score_select" if dtype == "bf16" else ("fp32_score_select" if not walked else "maximus_walk")
+    key = f"{kern}{' walk' if walked else ''} {dtype} {workload} f={f} K={K}"
+    src = ["tc_topk.cu"] if dtype == "bf16" else ["fp32_topk.cu" if not walked else "maximus.cu"]
+    return roofline(dtype, f, scores, kms, hbm, peaks, peak_src, sm, clk, key, src)
+
+
+def timed_steps(step, n_warm, n_steps, stream, flush, index, mips):
+    """n_warm untimed calls, then n_steps timed ones (CUDA events on the
+    call's stream, L2 flushed before each); per-step ms, the dominant
+    kernel's ms, kernel launches, and the last step's counters."""
+    import torch
+    for _ in range(n_warm):
+        flush.fill_(1.0)
+        step()
+    mips.sync(index)
+    ms, launches, stats = [], 0, None
+    kms = []
+    for _ in range(n_steps):
+        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats = mips.get_stats(index)
+        kms.append(stats["ms_kernel"])
+        launches += stats["launches"]
+    mips.sync(index)
+    return ms, kms, launches, stats
+
+
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.serve:
         return run_serve(args)
-    import numpy as np
     import torch
     from paper_1706_01449_gb300 import build as libbuild
     from paper_1706_01449_gb300 import mips
@@ -342,20 +464,22 @@ def main():
                 raise
     out_idx = torch.empty((nU, K), dtype=torch.int32, device=dev)
     out_sc = torch.empty((nU, K), dtype=torch.float64, device=dev)
-    fn = {"bmm": mips.topk, "maximus": mips.topk_maximus}.get(args.method)
     use_graph = args.method != "select" and not args.no_graph
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)  # torch work (flush, events) and the calls share it
-
     last_report = {}
 
-    def step():
-        if args.method == "select":
-            last_report.update(mips.select(index, U_d, K, out_idx, out_sc, stream=stream)[2])
-        elif use_graph:
-            mips.topk_graph(index, U_d, K, args.method, out_idx, out_sc, stream=stream)
-        else:
-            fn(index, U_d, K, out_idx, out_sc, stream=stream)
+    def make_step(idx, method, oi, osc, graph):
+        fn = {"bmm": mips.topk, "maximus": mips.topk_maximus}.get(method)
+
+        def step():
+            if method == "select":
+                last_report.update(mips.select(idx, U_d, K, oi, osc, stream=stream)[2])
+            elif graph:
+                mips.topk_graph(idx, U_d, K, method, oi, osc, stream=stream)
+            else:
+                fn(idx, U_d, K, oi, osc, stream=stream)
+        return step
 
     fit = None
     if args.fit_frac > 0 and args.method != "bmm":
@@ -365,11 +489,12 @@ def main():
         mips.sync(index, stream)
         fit = {"users": n_fit, "seconds": time.perf_counter() - t0}
     tune = None
-    if args.autotune and args.method != "bmm":
+    if not args.no_autotune and args.method != "bmm":
         tune = mips.autotune(index, U_d, K, stream=stream)
         tune = {"clusters": tune["clusters"], "block_items": tune["block_items"],
                 "sample_users": tune["sample_users"], "seconds": tune["t_tune"], "candidates": len(tune["tried"])}
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    step = make_step(index, args.method, out_idx, out_sc, use_graph)
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -377,28 +502,14 @@ def main():
 
     sampler = ClockSampler(local)
     sampler.start()
-    step_ms, score_ms, launches = [], [], 0
-    stats = None
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        stats = mips.get_stats(index)
-        score_ms.append(stats["ms_score"] if args.method == "bmm" else stats["ms_walk"] or stats["ms_score"])
-        launches += stats["launches"]
+    step_ms, kern_ms, launches, stats = timed_steps(step, 0, args.steps, stream, flush, index, mips)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
-    mips.sync(index)
 
     total_ms = max_over_ranks(sum(step_ms), device=dev)
     ms_per_step = total_ms / args.steps
@@ -410,17 +521,19 @@ def main():
         U_h = torch.from_numpy(U).pin_memory()
         oi_h = torch.empty((nU, K), dtype=torch.int32).pin_memory()
         os_h = torch.empty((nU, K), dtype=torch.float64).pin_memory()
-        method = {"bmm": "bmm", "maximus": "maximus", "select": "select"}[args.method]
-        mips.topk_host(index, U_h, K, method, oi_h, os_h)
+        mips.topk_host(index, U_h, K, args.method, oi_h, os_h)
         ts = []
         for _ in range(min(3, args.steps)):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t = time.perf_counter()
-            mips.topk_host(index, U_h, K, method, oi_h, os_h)
+            mips.topk_host(index, U_h, K, args.method, oi_h, os_h)
             ts.append(time.perf_counter() - t)
-        e2e = {"value": nU / statistics.median(ts), "unit": "users/s",
-               "h2d_bytes_per_step": int(U_h.numel() * 4), "d2h_bytes_per_step": int(nU * K * (4 + 8))}
+        e2e_s = max_over_ranks(statistics.median(ts), device=dev)
+        e2e = {"value": world * nU / e2e_s, "unit": "users/s",
+               "h2d_bytes_per_step": int(U_h.numel() * 4), "d2h_bytes_per_step": int(nU * K * (4 + 8)),
+               "entry_point": "mips_topk_host", "same_result_as_device_call":
+                   bool(torch.equal(oi_h, out_idx.cpu()) and torch.equal(os_h, out_sc.cpu()))}
 
     if rank != 0:
         index.close()
@@ -429,41 +542,64 @@ def main():
         return
 
     peaks, peak_src = load_peaks()
-    # algorithmic work of the scoring kernel: every (user, item) pair it
-    # scores; the Maximus walk scores only the pairs its bounds leave
+    props = torch.cuda.get_device_properties(dev)
+    sm = props.multi_processor_count
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
     walked = args.method == "maximus" or (args.method == "select" and stats["ms_walk"] > 0 and not stats["ms_score"])
-    # (the selector's stage times are those of its last run: the users
-    # outside the timed sample)
-    scored_users = nU - last_report.get("sample_users", 0) if args.method == "select" else nU
-    flops = 2.0 * f * (stats["pairs_scored"] if walked else scored_users * nI)
-    kms = statistics.mean(score_ms)
-    if dtype == "bf16":
-        bound, peak, unit = "tensor", peaks["bf16_tflops"], "TFLOP/s"
-        kernel_key = f"tc_score_select bf16 {args.workload} f={f} K={K}"
-        src = ["tc_topk.cu"]
+    st_main = dict(stats)
+    st_main["ms_kernel"] = statistics.mean(kern_ms) if any(kern_ms) else 0.0
+    if args.method == "select":  # the selector's counters are those of its last run (the users outside the sample)
+        nU_sel = nU - last_report.get("sample_users", 0)
     else:
-        props = torch.cuda.get_device_properties(dev)
-        sm = getattr(props, "multi_processor_count", SM_COUNT_FALLBACK)
-        bound, unit = "alu", "TFLOP/s"
-        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        kernel_key = f"fp32_score_select {args.workload} f={f} K={K}"
-        src = ["fp32_topk.cu"]
-    achieved = flops / (kms / 1e3) / 1e12
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic_for(kernel_key, kernel_source_hash(src)),
-                "kernel": kernel_key.split()[0], "kernel_ms": kms,
-                "peak_source": (f"{peak_src} bf16 burst" if bound == "tensor"
-                                else f"derived: SMs x 128 FP32 FMA/clk x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"),
-                "algorithmic_flops_per_launch": flops}
+        nU_sel = nU
+    rl = score_roofline(dtype, walked, f, nU_sel, nI, K, st_main, peaks, peak_src, sm, clk, args.workload)
+    rl["launches_per_step"] = 2 if walked else 1
 
-    cpu = cpu32 = None
+    # the other forms, same inputs, same run (one GPU only)
+    legs = {}
+    leg_names = [x for x in args.legs.split(",") if x and x != "none"] if world == 1 else []
+    for leg in leg_names:
+        if leg == args.method and dtype == "bf16":
+            continue
+        if leg not in ("bmm", "maximus", "fp32"):
+            raise SystemExit(f"unknown leg {leg}")
+        oi = torch.empty_like(out_idx)
+        osc = torch.empty_like(out_sc)
+        if leg == "fp32":
+            idx_l = mips.build_index(I_d, clusters=args.clusters, dtype="fp32")
+            l_method, l_dtype, l_graph, n_warm = "bmm", "fp32", False, 1
+        else:
+            idx_l = index
+            l_method, l_dtype, l_graph, n_warm = leg, dtype, use_graph, 2
+        if leg == "maximus" and not args.no_autotune:
+            mips.autotune(idx_l, U_d, K, stream=stream)
+        lstep = make_step(idx_l, l_method, oi, osc, l_graph)
+        lms, lkms, _, lst = timed_steps(lstep, n_warm, args.leg_steps, stream, flush, idx_l, mips)
+        lst = dict(lst)
+        lst["ms_kernel"] = statistics.mean(lkms)
+        l_walk = l_method == "maximus"
+        lrl = score_roofline(l_dtype, l_walk, f, nU, nI, K, lst, peaks, peak_src, sm, clk, args.workload)
+        legs[leg] = {"value": nU / (statistics.mean(lms) / 1e3), "unit": "users/s", "ms_per_step": statistics.mean(lms),
+                     "steps": args.leg_steps, "warmup": n_warm, "candidate_pass": l_dtype,
+                     "launch": "cuda graph replay" if l_graph else "plain calls",
+                     "same_result_as_main": bool(torch.equal(oi, out_idx) and torch.equal(osc, out_sc)),
+                     "stages_ms_last_step": {k: lst[k] for k in ("ms_prep", "ms_score", "ms_rescore", "ms_kmeans",
+                                                                 "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
+                     "roofline": lrl}
+        if idx_l is not index:
+            idx_l.close()
+        del oi, osc
+
+    cpu = cpu32 = exact = None
     if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(U, I, K)
+        cpu, ref_idx, ref_sc = cpu_baseline(U, I, K)
+        n_chk = ref_idx.shape[0]
+        exact = exact_sample(out_idx[:n_chk].cpu().numpy(), out_sc[:n_chk].cpu().numpy(), ref_idx, ref_sc)
         cpu32 = cpu_fp32_bmm(U, I, K)
 
-    tiles = (stats["blocks_walked"] if walked else ((nU + 127) // 128) * ((nI + 255) // 256))
+    tiles = (stats["blocks_walked"] if walked else ((nU_sel + 127) // 128) * ((nI + 255) // 256))
     line = {
-        "metric": "exact top-K users/sec", "value": value, "unit": "users/s", "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": "users/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if dtype == "bf16" else "f32",
         "data": "synthetic",
@@ -475,21 +611,24 @@ def main():
                    **({"autotune": tune} if tune else {}),
                    **({"centroids_fitted_before_timing": fit} if fit else {}),
                    **({"kmeans": "spherical"} if args.kmeans_spherical else {}),
-                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"users sharded, {world} rank(s)"},
-        "roofline": roofline,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"users sharded: {world} rank(s), contiguous slices of one user matrix"},
+        "roofline": rl,
+        "legs": legs,
         "cpu_baseline": cpu,
         "cpu_fp32_bmm": cpu32,
+        "exact_sample": exact,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
         "stages_ms_last_step": {k: stats[k] for k in ("ms_prep", "ms_score", "ms_rescore", "ms_kmeans",
-                                                       "ms_bounds", "ms_sort", "ms_walk", "ms_total")},
+                                                       "ms_bounds", "ms_sort", "ms_walk", "ms_total", "ms_kernel")},
         "candidates_per_user": stats["cand_emitted"] / nU, "rescored_per_user": stats["cand_rescored"] / nU,
         "users_overflow": stats["users_overflow"], "users_fp64": stats["users_fp64"],
         **({"pairs_scored_per_user": stats["pairs_scored"] / nU} if walked else {}),
-        # per warp and 16-score chunk of the tiles the score kernel processed
-        # (128 users x 256 items each)
-        "select_slow_chunk_frac": (stats["select_slow"] / (tiles * 8 * 8) if dtype == "bf16" and tiles else None),
+        # per warp and 64-score chunk of the tiles the score kernel processed
+        # (128 users x 256 items each, eight select warps of 128 columns)
+        "select_slow_chunk_frac": (stats["select_slow"] / (tiles * 8 * 2) if dtype == "bf16" and tiles else None),
     }
     print(json.dumps(line), flush=True)
     index.close()

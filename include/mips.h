@@ -301,6 +301,10 @@ typedef struct {
   double ms_walk;          /* Maximus: grouped walk (score + select) */
   double ms_total;         /* whole call */
   uint64_t select_slow;    /* select slow-path entries (warp x 64-score chunk), BF16 path */
+  double ms_kernel;        /* device time of the call's dominant kernel alone: the fused score + select
+                            * launch of a blocked multiply, or the sum of the Maximus walk's two launches
+                            * (first block, then the rest), without the work between them (CUDA events
+                            * around the launches; the first two launches of a call are counted) */
 } mips_stats;
 mips_status mips_get_stats(mips_index_t idx, mips_stats* out);
 

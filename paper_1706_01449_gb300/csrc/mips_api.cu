@@ -132,6 +132,10 @@ struct mips_index_s {
   } mx;
   // per-stage timing: ev[0] = call start, ev[1 + stage] = end of stage
   cudaEvent_t ev[kStages + 1] = {};
+  // around the launches of the call's dominant kernel (the fused score +
+  // select, or the two passes of the Maximus walk): start/end pairs
+  cudaEvent_t kev[4] = {};
+  int n_kev = 0;
   bool stage_ran[kStages] = {};
   int last_stage = -1;
   int order[kStages] = {};  // stages in the order they ran in the last call
@@ -156,7 +160,7 @@ struct mips_index_s {
     // host bookkeeping of the captured call, restored on replay
     bool stage_ran[kStages] = {};
     int order[kStages] = {};
-    int n_order = 0, last_stage = -1, launches = 0, clusters = 0, dtype = 0;
+    int n_order = 0, last_stage = -1, launches = 0, clusters = 0, dtype = 0, n_kev = 0;
   };
   std::vector<Graph> graphs;
 };
@@ -184,7 +188,16 @@ mips_status begin_call(mips_index_t idx, cudaStream_t s) {
   idx->last_stage = -1;
   idx->n_order = 0;
   idx->launches = 0;
+  idx->n_kev = 0;
   MIPS_CUDA(record(idx, idx->ev[0], s));
+  return MIPS_OK;
+}
+
+// Start or end mark of one launch of the dominant kernel (the first four
+// marks of a call are kept).
+mips_status mark_kernel(mips_index_t idx, cudaStream_t s) {
+  if (idx->n_kev < 4) MIPS_CUDA(record(idx, idx->kev[idx->n_kev], s));
+  if (idx->n_kev < 4) ++idx->n_kev;
   return MIPS_OK;
 }
 
@@ -292,8 +305,10 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
                idx->ws.at<int>(o_workc), idx->ws.at<double>(o_sc), idx->ws.at<float>(o_tauf)};
   mips_status st;
   if (!use_tc) {
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_fp32_score_select(users, n_users, f, idx->items, idx->item_nrm, idx->n_items, K, so,
                                        idx->stats_dev, idx->err_dev, s));
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     idx->launches += 1;
     if ((st = end_stage(idx, ST_SCORE, s)) != MIPS_OK) return st;
   } else {
@@ -325,9 +340,11 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     }
     const int grid = (int)(n_work < idx->num_sms ? n_work : idx->num_sms);
     if (p.heap_global) p.heap_mem = idx->ws.at<float>(o_heap);
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &map_items, &map_items_tail, p, so, uaux,
                                      idx->item_aux, idx->stats_dev,
                                      idx->err_dev, grid, s));
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     idx->launches += 1;
     if ((st = end_stage(idx, ST_SCORE, s)) != MIPS_OK) return st;
   }
@@ -494,9 +511,11 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     SelectOut so{ws.at<float>(o_tau), ws.at<int>(o_n), ws.at<int32_t>(o_pos), ws.at<float>(o_ub), cap, 1, nullptr, 0,
                  ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc), ws.at<uint32_t>(o_work), ws.at<int>(o_workc),
                  ws.at<double>(o_sc), ws.at<float>(o_tauf)};
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(maximus_walk(users, f, idx->items, idx->item_nrm, nI, vals, ws.at<float>(o_bounds), user_perm,
                            ws.at<int>(o_off), ws.at<int>(o_toff), C, K, so, ws.at<int32_t>(o_vis), ws.at<int>(o_wc),
                            idx->stats_dev, idx->err_dev, idx->num_sms, s));
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     idx->launches += 1;
     if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
@@ -558,18 +577,22 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     const int64_t mw = max_work;
     p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1, nullptr};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(mx_tc_pass2(m, ws.at<int32_t>(o_assign), ws.at<float2>(o_uaux), ws.at<float>(o_bounds), so, K,
                           &user_perm, ws.at<int32_t>(o_vis), idx->stats_dev, s, &idx->launches));
     // second pass: uneven work items, claimed dynamically (counter in n_work[2])
     MIPS_CUDA(cudaMemsetAsync(m.n_work + 2, 0, sizeof(int), s));
     p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c, nullptr, 1,
                     m.n_work + 2};
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
                                      idx->err_dev, grid, s));
+    if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     idx->launches += 2;
     if ((st = end_stage(idx, ST_WALK, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_rescore(users, n_users, f, idx->items, idx->perm, idx->item_nrm, nI, K, so, out_idx, out_score,
@@ -743,6 +766,7 @@ mips_index_t mips::index_worker_clone(mips_index_t src) {
     }
   }
   for (int i = 0; i <= kStages && ok; ++i) ok = cudaEventCreate(&w->ev[i]) == cudaSuccess;
+  for (int i = 0; i < 4 && ok; ++i) ok = cudaEventCreate(&w->kev[i]) == cudaSuccess;
   ok = ok && cudaMalloc(&w->err_dev, sizeof(int)) == cudaSuccess && cudaMemset(w->err_dev, 0, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMalloc(&w->stats_dev, sizeof(DevStats)) == cudaSuccess;
   if (!ok) {
@@ -812,6 +836,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   idx->opt = o;
   BUILD_CUDA(cudaEventCreateWithFlags(&idx->done, cudaEventDisableTiming));
   for (int i = 0; i <= kStages; ++i) BUILD_CUDA(cudaEventCreate(&idx->ev[i]));
+  for (int i = 0; i < 4; ++i) BUILD_CUDA(cudaEventCreate(&idx->kev[i]));
   BUILD_CUDA(cudaMalloc(&idx->err_dev, sizeof(int)));
   BUILD_CUDA(cudaMemsetAsync(idx->err_dev, 0, sizeof(int), s));
   BUILD_CUDA(cudaMalloc(&idx->stats_dev, sizeof(DevStats)));
@@ -1070,6 +1095,7 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
     idx->n_order = g.n_order;
     idx->last_stage = g.last_stage;
     idx->launches = g.launches;
+    idx->n_kev = g.n_kev;
     idx->last_users = n_users;
     idx->last_clusters = g.clusters;
     idx->last_dtype = g.dtype;
@@ -1116,6 +1142,7 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
   g.n_order = idx->n_order;
   g.last_stage = idx->last_stage;
   g.launches = idx->launches;
+  g.n_kev = idx->n_kev;
   g.clusters = idx->last_clusters;
   g.dtype = idx->last_dtype;
   // keep a few; drop those the workspace has outgrown first
@@ -1282,6 +1309,11 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out) {
     MIPS_CUDA(cudaEventElapsedTime(&t, idx->ev[0], idx->ev[1 + idx->last_stage]));
     out->ms_total = t;
   }
+  out->ms_kernel = 0.0;
+  for (int i = 0; i + 1 < idx->n_kev; i += 2) {
+    MIPS_CUDA(cudaEventElapsedTime(&t, idx->kev[i], idx->kev[i + 1]));
+    out->ms_kernel += t;
+  }
   return MIPS_OK;
 }
 
@@ -1340,6 +1372,8 @@ void mips_free_index(mips_index_t idx) {
   if (idx->done) cudaEventDestroy(idx->done);
   for (int i = 0; i <= kStages; ++i)
     if (idx->ev[i]) cudaEventDestroy(idx->ev[i]);
+  for (int i = 0; i < 4; ++i)
+    if (idx->kev[i]) cudaEventDestroy(idx->kev[i]);
   delete idx;
 }
 

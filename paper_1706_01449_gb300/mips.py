@@ -86,7 +86,8 @@ class Stats(ctypes.Structure):
                 ("launches", ctypes.c_int), ("pad_", ctypes.c_int),
                 ("ms_prep", ctypes.c_double), ("ms_score", ctypes.c_double), ("ms_rescore", ctypes.c_double),
                 ("ms_kmeans", ctypes.c_double), ("ms_bounds", ctypes.c_double), ("ms_sort", ctypes.c_double),
-                ("ms_walk", ctypes.c_double), ("ms_total", ctypes.c_double), ("select_slow", ctypes.c_uint64)]
+                ("ms_walk", ctypes.c_double), ("ms_total", ctypes.c_double), ("select_slow", ctypes.c_uint64),
+                ("ms_kernel", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}

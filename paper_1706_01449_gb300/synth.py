@@ -82,19 +82,20 @@ def _rescale_rows(x: np.ndarray, norms: np.ndarray) -> np.ndarray:
 def gaussian_rows(n: int, f: int, seed: int, stream: int,
                   norm_stream: int | None = None,
                   lognormal: tuple[float, float] | None = None,
-                  chunk: int = 1 << 20) -> np.ndarray:
+                  chunk: int = 1 << 20, offset: int = 0) -> np.ndarray:
     """float32 [n][f]: N(0,1)/sqrt(d+1) entries, rows optionally rescaled
-    to LogNormal(mu, sigma) norms drawn from ``norm_stream``."""
+    to LogNormal(mu, sigma) norms drawn from ``norm_stream``.  The rows are
+    rows [offset, offset + n) of the same recipe's larger matrix."""
     out = np.empty((n, f), dtype=np.float32)
     dim_scale = 1.0 / np.sqrt(np.arange(1, f + 1, dtype=np.float64))
     rows_per = max(1, chunk // max(f, 1))
     for r0 in range(0, n, rows_per):
         r1 = min(n, r0 + rows_per)
-        z = normal(seed, stream, (r1 - r0) * f, r0 * f).reshape(r1 - r0, f)
+        z = normal(seed, stream, (r1 - r0) * f, (offset + r0) * f).reshape(r1 - r0, f)
         x = z * dim_scale[None, :]
         if lognormal is not None:
             mu, sigma = lognormal
-            rho = np.exp(mu + sigma * normal(seed, norm_stream, r1 - r0, r0))
+            rho = np.exp(mu + sigma * normal(seed, norm_stream, r1 - r0, offset + r0))
             x = _rescale_rows(x, rho)
         out[r0:r1] = x.astype(np.float32)
     return out
@@ -102,24 +103,25 @@ def gaussian_rows(n: int, f: int, seed: int, stream: int,
 
 def clustered_users(n: int, f: int, seed: int, n_dirs: int = 256,
                     noise: float = 0.2, lognormal=(0.0, 0.3),
-                    chunk: int = 1 << 20) -> np.ndarray:
+                    chunk: int = 1 << 20, offset: int = 0) -> np.ndarray:
     """float32 [n][f] users drawn from a mixture of ``n_dirs`` angular
-    clusters with uneven (LogNormal(0,1)-weighted) sizes."""
+    clusters with uneven (LogNormal(0,1)-weighted) sizes: rows
+    [offset, offset + n) of the recipe's larger matrix."""
     dirs = normal(seed, S_DIRS, n_dirs * f).reshape(n_dirs, f)
     dirs /= np.sqrt(np.einsum("ij,ij->i", dirs, dirs))[:, None]
     w = np.exp(normal(seed, S_DIR_WEIGHTS, n_dirs))
     cdf = np.cumsum(w / w.sum())
     cdf[-1] = 1.0
-    pick = np.searchsorted(cdf, uniform(seed, S_USER_DIR, n), side="right")
+    pick = np.searchsorted(cdf, uniform(seed, S_USER_DIR, n, offset), side="right")
     pick = np.minimum(pick, n_dirs - 1)
     out = np.empty((n, f), dtype=np.float32)
     rows_per = max(1, chunk // max(f, 1))
     mu, sigma = lognormal
     for r0 in range(0, n, rows_per):
         r1 = min(n, r0 + rows_per)
-        z = normal(seed, S_USERS, (r1 - r0) * f, r0 * f).reshape(r1 - r0, f)
+        z = normal(seed, S_USERS, (r1 - r0) * f, (offset + r0) * f).reshape(r1 - r0, f)
         x = dirs[pick[r0:r1]] + noise * z
-        rho = np.exp(mu + sigma * normal(seed, S_USER_NORMS, r1 - r0, r0))
+        rho = np.exp(mu + sigma * normal(seed, S_USER_NORMS, r1 - r0, offset + r0))
         out[r0:r1] = _rescale_rows(x, rho).astype(np.float32)
     return out
 
@@ -160,18 +162,20 @@ WORKLOADS = {
 }
 
 
-def make_users(spec: dict, seed: int, n: int | None = None, f: int | None = None) -> np.ndarray:
+def make_users(spec: dict, seed: int, n: int | None = None, f: int | None = None,
+               offset: int = 0) -> np.ndarray:
+    """The workload's users: rows [offset, offset + n) of its user recipe."""
     n = spec["n_users"] if n is None else n
     f = spec["f"] if f is None else f
     kind = spec["users"]
     if kind == "plain":
-        return gaussian_rows(n, f, seed, S_USERS)
+        return gaussian_rows(n, f, seed, S_USERS, offset=offset)
     if kind == "lognormal":
-        return gaussian_rows(n, f, seed, S_USERS, S_USER_NORMS, spec["user_norm"])
+        return gaussian_rows(n, f, seed, S_USERS, S_USER_NORMS, spec["user_norm"], offset=offset)
     if kind == "clustered":
-        return clustered_users(n, f, seed, lognormal=spec["user_norm"])
+        return clustered_users(n, f, seed, lognormal=spec["user_norm"], offset=offset)
     if kind == "serve":
-        return serving_users(n, f, seed)
+        return serving_users(n, f, seed, offset)
     raise ValueError(kind)
 
 

@@ -49,3 +49,42 @@ def test_reference_arm_prints_one_json_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+PEAKS = {"hbm_gbs": 6781.8, "bf16_tflops": 1923.0, "sm_max_mhz": 2070.0}
+
+
+def test_roofline_binds_on_the_slowest_ceiling():
+    b = load_bench()
+    # f = 10: 2 f FLOP per score is cheap, one issue slot per 32 scores binds
+    sc = 480189 * 17770
+    r = b.roofline("bf16", 10, sc, 1.0, 1e6, PEAKS, "measured", 152, 2070.0, "k x", ["tc_topk.cu"])
+    t_sel = sc / (152 * 4 * 32 * 2070e6) * 1e3
+    t_ten = 2 * 10 * sc / 1923e12 * 1e3
+    assert r["ceiling"] == "select_issue" and r["bound"] == "alu"
+    assert abs(r["ceilings_ms"]["select_issue"] - t_sel) < 1e-9 and abs(r["ceilings_ms"]["tensor"] - t_ten) < 1e-9
+    assert abs(r["frac"] - t_sel / 1.0) < 1e-9
+    # f = 100: the tensor ceiling binds; frac = achieved / peak
+    r = b.roofline("bf16", 100, sc, 2.0, 1e6, PEAKS, "measured", 152, 2070.0, "k x", ["tc_topk.cu"])
+    assert r["ceiling"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["frac"] - (2 * 100 * sc / 2e-3 / 1e12) / 1923.0) < 1e-9
+    # a byte-heavy case binds on HBM
+    r = b.roofline("bf16", 1, 1000, 1.0, 1e10, PEAKS, "measured", 152, 2070.0, "k x", ["tc_topk.cu"])
+    assert r["ceiling"] == "hbm" and r["bound"] == "hbm"
+    # FP32 CUDA-core form: the FMA peak from the SM count and clock
+    r = b.roofline("fp32", 50, sc, 30.0, 1e6, PEAKS, "measured", 152, 2070.0, "k x", ["fp32_topk.cu"])
+    assert r["ceiling"] == "alu_fp32_fma" and abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+
+
+def test_exact_sample_reports_differences():
+    b = load_bench()
+    idx = np.arange(12, dtype=np.int32).reshape(4, 3)
+    sc = np.linspace(1, 2, 12).reshape(4, 3)
+    r = b.exact_sample(np.vstack([idx, idx]), np.vstack([sc, sc]), idx, sc)
+    assert r == {"users": 4, "indices_equal": True, "rows_differing": 0, "max_rel_score_err": 0.0}
+    j = idx.copy()
+    j[2, 1] = 99
+    s2 = sc.copy()
+    s2[1, 0] *= 1 + 1e-7
+    r = b.exact_sample(j, s2, idx, sc)
+    assert not r["indices_equal"] and r["rows_differing"] == 1 and 0.9e-7 < r["max_rel_score_err"] < 1.1e-7
