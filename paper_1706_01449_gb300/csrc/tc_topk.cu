@@ -3,35 +3,40 @@
 // the |U| x |I| score matrix never leaves the SM), and the same machinery
 // walking Maximus's per-cluster item lists (Sec. IV, Algorithm 1).
 //
-// Persistent kernel, one CTA per SM, 12 warps, user tiles of 128 rows and
+// Persistent kernel, one CTA per SM, 10 warps, user tiles of 128 rows and
 // item tiles of 256 rows (an M = 128, N = 256 MMA runs at the tensor pipe's
-// full rate; N = 128 costs nearly the same time per instruction):
-//   warp 0      TMA producer: takes the CTA's next work item (user tile x
-//               range of item tiles), publishes it in a shared-memory ring
-//               for the other roles, loads the user tile, then the item
-//               tiles through an S-stage ring (whole tiles, or two 128-row
-//               halves when whole tiles do not fit shared memory; operand
-//               rows of 128-byte chunks plus a 32/64-byte tail chunk, each
-//               with its own tensor map and swizzle);
-//   warp 1      MMA issuer (one thread): D = A . B^T with tcgen05.mma
-//               kind::f16 (BF16 x BF16 -> FP32) into one of two TMEM
-//               accumulators of 128 lanes x 256 columns, so the MMAs of item
-//               tile j+1 overlap the select of tile j;
-//   warp 2      allocates / frees TMEM;
-//   warps 4-11  select: epilogue warp e reads TMEM lanes 32 * (e % 4) .. +31
+// full rate):
+//   warps 0-7   select: epilogue warp e reads TMEM lanes 32 * (e % 4) .. +31
 //               (a warp may only touch the lane quarter of its warp % 4) and
 //               columns 128 * (e / 4) .. +127 of each item tile, so every
 //               user is served by two threads, each with its own threshold,
 //               top-K of lower bounds and candidate sub-list; the two share
 //               their thresholds through shared memory (either one is a valid
 //               lower bound on the user's K-th score, so the larger filters
-//               both halves).
+//               both halves);
+//   warp 8      allocates / frees TMEM; its lane 0 is the TMA producer: it
+//               takes the CTA's next work item (user tile x
+//               range of item tiles), publishes it in a shared-memory ring
+//               for the other roles, loads the user tile, then the item
+//               tiles through an S-stage ring (whole tiles, or two 128-row
+//               halves when whole tiles do not fit shared memory; operand
+//               rows of 128-byte chunks plus a 32/64-byte tail chunk, each
+//               with its own tensor map and swizzle), and with each item
+//               tile a bulk copy of its bound columns (and, for list walks,
+//               its item positions) into a small ring the select warps read;
+//   warp 9      MMA issuer (one thread): D = A . B^T with tcgen05.mma
+//               kind::f16 (BF16 x BF16 -> FP32) into one of two TMEM
+//               accumulators of 128 lanes x 256 columns, so the MMAs of item
+//               tile j+1 overlap the select of tile j.
+// The select's common case is one max-reducing TMEM load per 64 scores
+// (tcgen05.ld.red: the values and each thread's maximum of them) and one
+// warp vote: the operands carry two bound columns, so every accumulator
+// entry is an upper bound H >= u^T i and a maximum below the threshold
+// clears 64 items at once.  Only 16-column groups holding a hit are looked
+// at item by item, from a second, narrow TMEM load.
 // Work items: without a work list (blocked multiply) user tile w against
 // every item tile; with one (item-chunked blocked multiply, Maximus walk)
 // as the list gives them, claimed round-robin or from a global counter.
-// Operands are K-major rows (prep.cu): the two bound columns make every
-// accumulator entry an upper bound H >= u^T i, so the common case costs one
-// maximum over 16 scores and a compare.
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel
 // raises DEV_ERR_TIMEOUT, every role leaves its loop, the MMA thread drains
@@ -47,15 +52,18 @@ namespace mips {
 
 namespace {
 
-constexpr int kWarps = 12;
-constexpr int kEpiWarp0 = 4;
-constexpr int kEpiWarps = 8;
+constexpr int kWarps = 10;
+constexpr int kEpiWarps = 8;   // warps 0-7 select
+constexpr int kProdWarp = 8;   // producer (lane 0) and TMEM allocation (whole warp)
+constexpr int kMmaWarp = 9;    // MMA issuer (lane 0)
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTileN = 256;    // items per tile (MMA N)
 constexpr int kTileM = 128;    // users per tile (MMA M)
 constexpr int kHalfN = 128;    // columns per epilogue thread and tile
 constexpr int kQueue = 16;     // hit-queue slots per thread
+constexpr int kAuxSlots = 4;   // item tiles whose bound columns / positions are staged at a time
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -107,11 +115,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return mbar_wait_slow(bar, parity, abort_flag, err);
 }
 
+// Wait (bounded) for a phase whose completion nothing else depends on any
+// more: used only to drain copies and MMAs before the CTA exits.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity) && globaltimer() - t0 < kWaitNs) {
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
           "r"(smem_u32(smem_dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Untiled bulk copy global -> shared (both addresses 16-byte aligned, bytes a
+// multiple of 16), completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(gmem_src)), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -141,47 +167,72 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 lanes x 32 bits, 64 consecutive columns: r[j] = column (col + j) of this
-// thread's lane.
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+#define MIPS_R8(r, o)                                                                                       \
+  "=r"(r[o + 0]), "=r"(r[o + 1]), "=r"(r[o + 2]), "=r"(r[o + 3]), "=r"(r[o + 4]), "=r"(r[o + 5]), "=r"(r[o + 6]), \
+      "=r"(r[o + 7])
+#define MIPS_R16(r, o) MIPS_R8(r, o), MIPS_R8(r, o + 8)
+#define MIPS_R64(r) MIPS_R16(r, 0), MIPS_R16(r, 16), MIPS_R16(r, 32), MIPS_R16(r, 48)
+
+// 32 lanes x 32 bits, 64 consecutive columns, reduced: this thread's maximum
+// of its lane's 64 columns (the values themselves are not used).
+__device__ __forceinline__ float tmem_ldmax64(uint32_t taddr) {
+  uint32_t r[64];
+  float m;
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
-        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
-        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
-        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
-        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
+      "%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,"
+      "%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, %64, [%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : MIPS_R64(r), "=f"(m)
+      : "r"(taddr)
+      : "memory");
+  return m;
 }
 
-__device__ __forceinline__ float max3(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
+// 16 consecutive columns: r[j] = column (col + j) of this thread's lane, and
+// their maximum.
+__device__ __forceinline__ float tmem_ldmax16(uint32_t taddr, uint32_t (&r)[16]) {
+  float m;
+  asm volatile(
+      "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, "
+      "[%17];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : MIPS_R16(r, 0), "=f"(m)
+      : "r"(taddr)
+      : "memory");
+  return m;
 }
 
-// maximum of 16 scores (a tree of three-input maxima)
-__device__ __forceinline__ float max16(const uint32_t* r) {
-  const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
-  const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
-  const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
-  const float m3 = max3(__uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
-  const float m4 = max3(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]));
-  return max3(max3(m0, m1, m2), m3, fmaxf(m4, __uint_as_float(r[15])));
+// 8 consecutive columns, no wait: the caller reads r only after
+// tmem_wait_ld8(r), whose operands tie the wait to these registers.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];" : MIPS_R8(r, 0) : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld8(uint32_t (&r)[8]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+               :
+               : "memory");
 }
 
-// A threshold published for the partner thread, tagged with its user tile
-// so that a value from another user is never taken.
+#undef MIPS_R64
+#undef MIPS_R16
+#undef MIPS_R8
+
+// A threshold published for the partner thread, tagged with its work item
+// so that a value from another work item is never taken.
 __device__ __forceinline__ unsigned long long pack_tau(float t, int ut) {
   return ((unsigned long long)(uint32_t)ut << 32) | (unsigned long long)__float_as_uint(t);
+}
+
+// float <-> unsigned with the same order (for atomicMax on thresholds)
+__device__ __forceinline__ unsigned tau_ord(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float tau_from_ord(unsigned o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
 // Per-thread select state (registers).  KR > 0: the K largest lower bounds
@@ -190,30 +241,42 @@ __device__ __forceinline__ unsigned long long pack_tau(float t, int ut) {
 template <int KR>
 struct TcUser {
   float tau;      // this thread's K-th largest lower bound so far
-  float tau_eff;  // max(tau, partner thread's tau): the filter threshold
+  float tau_eff;  // max(tau, partner thread's tau, merged seed lists): the filter threshold
   int n_cand;
-  int ut;         // current user tile (tag of the published threshold)
+  int ut;         // current work item (tag of the published threshold)
   float beta_u, nhat_u;  // bound columns of this user (prep.cu)
   float d[KR > 0 ? KR : 1];
 };
 
-// Warp-uniform parameters of the select.
+// Per-thread arrays in shared memory, one column per select thread (slot
+// 0..255), laid out back to back from `qbase`:
+//   hit queue values [16][256] floats, hit queue columns [16][256] ints,
+//   published thresholds [256] (64-bit: tag << 32 | float bits),
+//   seed-list tags [2][256] ints (work item whose first-tile list is
+//   published, -1: none), first-tile top-K lists [2][K][256] floats.
+constexpr int kQpOfs = kQueue * kEpiThreads;            // in 4-byte words from qbase
+constexpr int kTauOfs = 2 * kQueue * kEpiThreads;       // (8-byte aligned)
+constexpr int kSeedTagOfs = kTauOfs + 2 * kEpiThreads;
+constexpr int kSeedListOfs = kSeedTagOfs + 2 * kEpiThreads;
+
+// Parameters of one select thread (warp-uniform but for the slots).
 struct TcSel {
   float* heap;        // &heap_base[slot] (stride kEpiThreads), KR = 0 only
   int K;
   int cap;
   int32_t* cand_pos;  // this thread's candidate sub-list
   float* cand_ub;
-  float* qh;          // hit queue: qh[t * kEpiThreads]
-  int32_t* qp;
-  volatile unsigned long long* tau_mine;  // published thresholds: mine, partner's
-  const volatile unsigned long long* tau_partner;
-  unsigned* tau_glob;                     // this user's shared threshold (item-chunked scan) or null
-  volatile int* seed_mine;                // [2][256] user tile whose seed list is published
-  const volatile int* seed_partner;
-  float* seed_list;                       // [2][K][256] first-tile top-K lists
-  const float* seed_list_partner;
+  float* qbase;       // the per-thread arrays above
+  int slot, pslot;    // this thread's column and its partner's (the other half of the same user)
+  unsigned* tau_glob;  // this user's shared threshold (item-chunked scan) or null
   float g;            // accumulation-error factor of prep.cu
+  __device__ __forceinline__ float* qh() const { return qbase + slot; }  // qh()[t * kEpiThreads]
+  __device__ __forceinline__ int32_t* qp() const { return (int32_t*)qbase + kQpOfs + slot; }
+  __device__ __forceinline__ volatile unsigned long long* tau(int sl) const {
+    return (volatile unsigned long long*)(qbase + kTauOfs) + sl;
+  }
+  __device__ __forceinline__ volatile int* seed_tag(int sl) const { return (volatile int*)qbase + kSeedTagOfs + sl; }
+  __device__ __forceinline__ volatile float* seed_list(int sl) const { return qbase + kSeedListOfs + sl; }
 };
 
 template <int KR>
@@ -224,6 +287,15 @@ __device__ __forceinline__ void topk_init(TcUser<KR>& s, const TcSel& c) {
   } else {
     heap_init(c.heap, kEpiThreads, c.K);
   }
+}
+
+// The K-th largest kept value (static indices keep d in registers).
+template <int KR>
+__device__ __forceinline__ float topk_kth(const TcUser<KR>& s, int K) {
+  float t = s.d[0];
+#pragma unroll
+  for (int i = 0; i < KR; ++i) t = (i < K) ? s.d[i] : t;
+  return t;
 }
 
 // Insert lower bound L (> the current K-th largest) and return the new K-th
@@ -238,12 +310,25 @@ __device__ __forceinline__ float topk_insert(TcUser<KR>& s, const TcSel& c, floa
 #pragma unroll
     for (int i = 0; i < KR; ++i) s.d[i] = nd[i];
     if (c.K == KR) return nd[KR - 1];  // K fills the array (warp-uniform)
-    float t = nd[0];  // ends as nd[K - 1] (static indices keep d in registers)
-#pragma unroll
-    for (int i = 0; i < KR; ++i) t = (i < c.K) ? nd[i] : t;
-    return t;
+    return topk_kth(s, c.K);
   } else {
     return heap_replace_min(c.heap, kEpiThreads, c.K, L);
+  }
+}
+
+// Branch-free insertion of any L into the descending array d (the smallest
+// entry drops out; an L below all of them changes nothing): entry i becomes
+// max(d[i], min(d[i-1], L)), two instructions per entry and no divergence
+// between lanes.
+template <int KR>
+__device__ __forceinline__ void topk_push(TcUser<KR>& s, float L) {
+  float prev = s.d[0];
+  s.d[0] = fmaxf(prev, L);
+#pragma unroll
+  for (int i = 1; i < KR; ++i) {
+    const float cur = s.d[i];
+    s.d[i] = fmaxf(cur, fminf(prev, L));
+    prev = cur;
   }
 }
 
@@ -258,82 +343,25 @@ __device__ __forceinline__ float tc_lower(const TcUser<KR>& s, const TcSel& c, f
   return (H - slack) - fabsf(H) * 2.384185791015625e-07f;                             // 2^-22
 }
 
-// After the first-tile pass: this thread's K best lower bounds go to its
-// queue slots (shared memory), published with a tagged flag; it then waits a
-// bounded time for the partner's (the other half of the same user) and
-// takes the K-th largest of the union as its threshold.  The two halves
-// hold distinct items, so the union's K-th largest is a valid lower bound.
-// If the partner's list is not there within the bound, the thread goes on
-// with its own threshold, which is valid too.
-// The lists are double-buffered by user-tile parity: a partner that is one
-// user tile ahead cannot overwrite the list being read (the accumulator
-// handshake keeps the halves within one user tile of each other).
-template <int KR>
-__device__ __forceinline__ void seed_merge(TcUser<KR>& s, const TcSel& c, int ut, int par) {
-  if constexpr (KR > 0) {
-    float* mine = c.seed_list + par * c.K * kEpiThreads;
-#pragma unroll
-    for (int i = 0; i < KR; ++i)
-      if (i < c.K) mine[i * kEpiThreads] = s.d[i];
-    __threadfence_block();
-    c.seed_mine[par * kEpiThreads] = ut;
-    const float* pq = c.seed_list_partner + par * c.K * kEpiThreads;
-    const volatile int* pflag = c.seed_partner + par * kEpiThreads;
-    int spins = 0;
-    while (*pflag != ut && ++spins < 20000) {
-    }
-    if (*pflag == ut) {
-      __threadfence_block();
-      // K-th largest of two descending lists of K
-      int ia = 0, ib = 0;
-      float v = s.d[0];
-      for (int r = 0; r < c.K; ++r) {
-        float a = kNegInf;
-#pragma unroll
-        for (int i = 0; i < KR; ++i)
-          if (i == ia) a = s.d[i];
-        const float b = ((volatile const float*)pq)[ib * kEpiThreads];
-        if (a >= b) {
-          v = a;
-          ++ia;
-        } else {
-          v = b;
-          ++ib;
-        }
-      }
-      if (v > s.tau_eff) s.tau_eff = v;
-    }
-  }
-}
-
-// Publish this thread's threshold (tagged with its user tile) for the partner.
-// float <-> unsigned with the same order (for atomicMax on thresholds)
-__device__ __forceinline__ unsigned tau_ord(float x) {
-  const unsigned b = __float_as_uint(x);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float tau_from_ord(unsigned o) {
-  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
-}
-
+// Publish this thread's threshold (tagged with its work item) for the partner.
 template <int KR>
 __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) {
-  *c.tau_mine = pack_tau(s.tau, s.ut);
+  *c.tau(c.slot) = pack_tau(s.tau, s.ut);
   if (c.tau_glob) atomicMax(c.tau_glob, tau_ord(s.tau));  // every threshold is valid for the user
 }
 
 // One hit (H >= tau_eff when queued): threshold update from its lower bound,
 // then the candidate emission.  Lower bounds at or below the current filter
 // threshold cannot raise it and are not kept.  With emit_only (second pass
-// over a user tile's first item tile, whose lower bounds are already in the
-// top-K) only the emission is done, so no item is counted twice.  The
-// item's position is pos0 + col, or pos_tile[col] for a walk of a
-// cluster's sorted list (MX).
+// over a work item's first item tile, whose lower bounds already went
+// through the top-K) only the emission is done, so no item is counted twice.
+// The item's position is pos0 + col, or pos[col] for a walk of a cluster's
+// sorted list (MX).
 template <int KR, bool MX>
-__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int col, const float2* aux_tile,
-                                         int32_t pos0, const int32_t* pos_tile, bool emit_only) {
+__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int col, const float2* aux,
+                                         int32_t pos0, const int32_t* pos, bool emit_only) {
   if (H < s.tau_eff) return;  // the threshold rose since the hit was queued
-  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux_tile[col]);
+  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux[col]);
   if (L > s.tau_eff) {
     s.tau = topk_insert(s, c, L);
     if (s.tau > s.tau_eff) {
@@ -343,123 +371,140 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
   }
   if (H >= s.tau_eff) {
     if (s.n_cand < c.cap) {
-      c.cand_pos[s.n_cand] = MX ? pos_tile[col] : pos0 + col;
+      c.cand_pos[s.n_cand] = MX ? pos[col] : pos0 + col;
       c.cand_ub[s.n_cand] = H;
     }
     ++s.n_cand;
   }
 }
 
-// 16 scores r[0..15] of items pos0.. (valid: how many are real items).
-// Fast path: one maximum over the 16 and a compare.  Slow path (any lane of
-// the warp has a hit): this thread's hits are queued in shared memory, then
-// drained in order through one offer site.
+// Seed step for 8 columns col0.. of the first item tile: every lower bound
+// goes into the top-K (K = 1: the maximum; register top-K: the branch-free
+// network, so lanes never diverge; heap: only what passes its minimum).
+template <int KR>
+__device__ __forceinline__ void seed8(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[8], int col0, int valid,
+                                      const float2* aux) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float L = col0 + q < valid ? tc_lower(s, c, __uint_as_float(r[q]), aux[col0 + q]) : kNegInf;
+    if constexpr (KR == 1) {
+      s.d[0] = fmaxf(s.d[0], L);
+    } else if constexpr (KR > 1) {
+      topk_push(s, L);
+    } else {
+      if (L > s.tau) s.tau = heap_replace_min(c.heap, kEpiThreads, c.K, L);
+    }
+  }
+}
+
+// First pass over a fresh work item's first item tile (the items of largest
+// norm: the index stores items by norm, descending), so that the threshold
+// starts the scan near its final value instead of at -inf; nothing is
+// emitted.  TMEM is read 8 columns at a time with the next 8 in flight.
+// Inactive lanes (padding rows) keep tau = +inf.
+template <int KR>
+__device__ __forceinline__ void seed_tile(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid,
+                                          const float2* aux, bool active) {
+  uint32_t ra[8], rb[8];
+  tmem_ld8(taddr, ra);
+  tmem_wait_ld8(ra);
+#pragma unroll 1
+  for (int c8 = 0; c8 < kHalfN; c8 += 16) {
+    tmem_ld8(taddr + c8 + 8, rb);
+    seed8(s, c, ra, c8, valid, aux);
+    tmem_wait_ld8(rb);
+    if (c8 + 16 < kHalfN) tmem_ld8(taddr + c8 + 16, ra);
+    seed8(s, c, rb, c8 + 8, valid, aux);
+    if (c8 + 16 < kHalfN) tmem_wait_ld8(ra);
+  }
+  if constexpr (KR > 0) s.tau = active ? topk_kth(s, c.K) : __int_as_float(0x7f800000);
+}
+
+// After the seed: this thread's K best lower bounds go to its list slot for
+// the work item's parity, under a tag that is cleared while the list is
+// rewritten (so a reader that sees the same tag before and after reading
+// the list has read it whole).
+template <int KR>
+__device__ __forceinline__ void seed_publish(const TcUser<KR>& s, const TcSel& c, int wi, int par) {
+  if constexpr (KR > 0) {
+    volatile int* flag = c.seed_tag(c.slot) + par * kEpiThreads;
+    *flag = -1;
+    __threadfence_block();
+    volatile float* mine = c.seed_list(c.slot) + par * c.K * kEpiThreads;
+#pragma unroll
+    for (int i = 0; i < KR; ++i)
+      if (i < c.K) mine[i * kEpiThreads] = s.d[i];
+    __threadfence_block();
+    *flag = wi;
+  }
+}
+
+// Once the partner thread (the other half of the same user) has published
+// its first-tile list for this work item: the K-th largest of the union of
+// the two lists raises this thread's filter threshold (the halves hold
+// distinct items, so the union's K-th largest lower bound is a lower bound
+// on the user's K-th score).  Warp-uniform; returns true when there is
+// nothing more to wait for (merged, or the list was overwritten meanwhile).
+template <int KR>
+__device__ __forceinline__ bool seed_try_merge(TcUser<KR>& s, const TcSel& c, int wi, int par, bool active) {
+  if constexpr (KR > 0) {
+    const volatile int* pflag = c.seed_tag(c.pslot) + par * kEpiThreads;
+    if (!__all_sync(kFull, *pflag == wi)) return false;
+    __threadfence_block();
+    const volatile float* pq = c.seed_list(c.pslot) + par * c.K * kEpiThreads;
+    int ia = 0, ib = 0;
+    float v = kNegInf;
+    for (int r = 0; r < c.K; ++r) {
+      float a = kNegInf;
+#pragma unroll
+      for (int i = 0; i < KR; ++i)
+        if (i == ia) a = s.d[i];
+      const float b = pq[ib * kEpiThreads];
+      if (a >= b) {
+        v = a;
+        ++ia;
+      } else {
+        v = b;
+        ++ib;
+      }
+    }
+    __threadfence_block();
+    if (*pflag == wi && active && v > s.tau_eff) s.tau_eff = v;
+  }
+  return true;
+}
+
+// The 16-column groups of this thread's 128 columns whose 64-column half had
+// a hit somewhere in the warp (bit h of `halves`): each group is read again
+// with its maximum; lanes whose maximum reaches their threshold queue their
+// hits in shared memory and offer them in order through one offer site.
 template <int KR, bool MX>
-__device__ __forceinline__ void select16(TcUser<KR>& s, const TcSel& c, const uint32_t* r, int col0, int valid,
-                                         const float2* aux_tile, int32_t pos0, const int32_t* pos_tile,
-                                         unsigned long long& slow, bool emit_only) {
-  const float m0 = max3(__uint_as_float(r[0]), __uint_as_float(r[1]), __uint_as_float(r[2]));
-  const float m1 = max3(__uint_as_float(r[3]), __uint_as_float(r[4]), __uint_as_float(r[5]));
-  const float m2 = max3(__uint_as_float(r[6]), __uint_as_float(r[7]), __uint_as_float(r[8]));
-  const float m3 = max3(__uint_as_float(r[9]), __uint_as_float(r[10]), __uint_as_float(r[11]));
-  const float m4 = max3(__uint_as_float(r[12]), __uint_as_float(r[13]), __uint_as_float(r[14]));
-  const float mm = max3(max3(m0, m1, m2), m3, fmaxf(m4, __uint_as_float(r[15])));
-  const bool hit = mm >= s.tau_eff;
-  if (__any_sync(0xffffffffu, hit)) {  // warp-uniform: counts warp-level entries
-    ++slow;
+__device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid,
+                                            const float2* aux, int32_t pos0, const int32_t* pos, unsigned halves,
+                                            bool emit_only) {
+#pragma unroll 1
+  for (int gi = 0; gi < kHalfN / 16; ++gi) {
+    if (!((halves >> (gi >> 2)) & 1u)) continue;  // warp-uniform
+    uint32_t v[16];
+    const float mg = tmem_ldmax16(taddr + 16 * gi, v);
+    const bool hit = mg >= s.tau_eff;
+    if (!__any_sync(kFull, hit)) continue;
     int n = 0;
     if (hit) {
-      // only the groups of three whose maximum reached the threshold
       const float t = s.tau_eff;
-      const float gm[6] = {m0, m1, m2, m3, m4, __uint_as_float(r[15])};
+      const int col0 = 16 * gi;
 #pragma unroll
-      for (int gq = 0; gq < 6; ++gq) {
-        if (gm[gq] >= t) {
-#pragma unroll
-          for (int q = 3 * gq; q < (gq < 5 ? 3 * gq + 3 : 16); ++q) {
-            const float v = __uint_as_float(r[q]);
-            if (v >= t && q < valid) {
-              c.qh[n * kEpiThreads] = v;
-              c.qp[n * kEpiThreads] = col0 + q;
-              ++n;
-            }
-          }
+      for (int q = 0; q < 16; ++q) {
+        const float x = __uint_as_float(v[q]);
+        if (x >= t && col0 + q < valid) {
+          c.qh()[n * kEpiThreads] = x;
+          c.qp()[n * kEpiThreads] = col0 + q;
+          ++n;
         }
       }
     }
-    // one offer site for the queued hits (keeps the code small)
-    for (int t = 0; t < n; ++t)
-      tc_offer<KR, MX>(s, c, c.qh[t * kEpiThreads], c.qp[t * kEpiThreads], aux_tile, pos0, pos_tile, emit_only);
-  }
-}
-
-template <int KR, bool MX>
-__device__ __forceinline__ void select64(TcUser<KR>& s, const TcSel& c, uint32_t (&r)[64], int col0, int valid,
-                                         const float2* aux_tile, int32_t pos0, const int32_t* pos_tile,
-                                         unsigned long long& slow, bool emit_only) {
-  if (valid < 64) {
-#pragma unroll
-    for (int q = 0; q < 64; ++q)
-      if (q >= valid) r[q] = 0xff800000u;  // -inf
-  }
-  // fast path: one maximum over the 64 scores and one warp vote (the four
-  // groups of 16 are looked at only when some lane has a hit)
-  const float g0 = max16(r), g1 = max16(r + 16), g2 = max16(r + 32), g3 = max16(r + 48);
-  const float mm = max3(g0, g1, fmaxf(g2, g3));
-  if (!__any_sync(0xffffffffu, mm >= s.tau_eff)) return;
-#pragma unroll
-  for (int g = 0; g < 4; ++g)
-    select16<KR, MX>(s, c, r + 16 * g, col0 + 16 * g, valid - 16 * g, aux_tile, pos0, pos_tile, slow, emit_only);
-}
-
-// First pass over a user tile's first item tile (the items of largest norm:
-// the index stores items by norm, descending), so that the threshold starts
-// the scan near its final value instead of at -inf; nothing is emitted.
-// K = 1: the 64 scores form 8 groups of 8 and each group's largest lower
-// bound goes to the top-1 -- branch-free, and the result is the exact
-// maximum.  K > 1: every lower bound above the threshold is queued, then
-// inserted (group maxima would be cheaper but give a lower threshold,
-// which measured slower overall on large catalogues).
-template <int KR>
-__device__ __forceinline__ void seed64(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[64], int col0, int valid,
-                                       const float2* aux_tile) {
-  if constexpr (KR == 1) {
-#pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      float m = kNegInf;
-#pragma unroll
-      for (int q = 8 * g; q < 8 * g + 8; ++q) {
-        const float L = tc_lower(s, c, __uint_as_float(r[q]), aux_tile[col0 + q]);
-        m = fmaxf(m, q < valid ? L : kNegInf);
-      }
-      c.qh[g * kEpiThreads] = m;
-    }
-    // inserted from shared memory in a rolled loop (keeps the registers down)
-#pragma unroll 1
-    for (int g = 0; g < 8; ++g) {
-      const float m = c.qh[g * kEpiThreads];
-      if (m > s.tau) s.tau = topk_insert(s, c, m);
-    }
-  } else {
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      int n = 0;
-#pragma unroll
-      for (int q = 16 * g; q < 16 * g + 16; ++q) {
-        const float H = __uint_as_float(r[q]);
-        if (H > s.tau && q < valid) {  // L <= H: nothing at or below tau can enter
-          const float L = tc_lower(s, c, H, aux_tile[col0 + q]);
-          if (L > s.tau) {
-            c.qh[n * kEpiThreads] = L;
-            ++n;
-          }
-        }
-      }
-      for (int t = 0; t < n; ++t) {
-        const float L = c.qh[t * kEpiThreads];
-        if (L > s.tau) s.tau = topk_insert(s, c, L);
-      }
-    }
+    for (int k = 0; k < n; ++k)
+      tc_offer<KR, MX>(s, c, c.qh()[k * kEpiThreads], c.qp()[k * kEpiThreads], aux, pos0, pos, emit_only);
   }
 }
 
@@ -509,6 +554,7 @@ struct Smem {
   uint64_t b_empty[kMaxStages];
   uint64_t a_full, a_empty;
   uint64_t acc_full[2], acc_empty[2];
+  uint64_t aux_full[kAuxSlots], aux_empty[kAuxSlots];
   uint64_t drain;
   uint64_t wq_full[kWQ], wq_empty[kWQ];
   int wq[kWQ];
@@ -516,8 +562,14 @@ struct Smem {
   int abort_flag;
 };
 
-// MX: work items from p.work (Maximus walk of per-cluster sorted lists);
-// otherwise every user tile against every item tile (blocked multiply).
+// Bytes of one aux ring slot: an item tile's bound columns, then (list walks)
+// its item positions.
+constexpr uint32_t kAuxBytes = kTileN * sizeof(float2);
+constexpr uint32_t kPosBytes = kTileN * sizeof(int32_t);
+
+// MX: work items from p.work (Maximus walk of per-cluster sorted lists,
+// item-chunked blocked multiply); otherwise every user tile against every
+// item tile (blocked multiply).
 template <int KR, bool MX>
 __global__ void __launch_bounds__(kWarps * 32, 1)
     tc_score_select_kernel(const __grid_constant__ CUtensorMap map_users, const __grid_constant__ CUtensorMap map_users_t,
@@ -535,17 +587,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const uint32_t b_bytes = p.kc * b_chunk + sub_rows * p.tail_bytes;  // one ring stage
   unsigned char* a_tiles = base;                                              // [KC][a_chunk] + tail
   unsigned char* b_tiles = a_tiles + a_bytes;                                 // [S]([KC][b_chunk] + tail)
-  float* heap_smem = (float*)(b_tiles + (size_t)p.stages * b_bytes);          // [K][256] (KR = 0)
+  float2* aux_ring = (float2*)(b_tiles + (size_t)p.stages * b_bytes);        // [kAuxSlots][256]
+  int32_t* pos_ring = (int32_t*)(aux_ring + (size_t)kAuxSlots * kTileN);     // [kAuxSlots][256]
+  float* heap_smem = (float*)(pos_ring + (size_t)kAuxSlots * kTileN);        // [K][256] (KR = 0)
   const bool heap_in_smem = KR == 0 && !p.heap_global;
   float* heap_base = heap_in_smem ? heap_smem : p.heap_mem + (size_t)blockIdx.x * p.K * kEpiThreads;
-  float2* aux_base = (float2*)(heap_smem + (heap_in_smem ? (size_t)p.K * kEpiThreads : 0));  // [8 warps][128]
-  int32_t* posb_base = (int32_t*)(aux_base + (size_t)kEpiWarps * kHalfN);      // [8 warps][128]
-  float* qh_base = (float*)(posb_base + (size_t)kEpiWarps * kHalfN);          // [16][256]
+  float* qh_base = heap_smem + (heap_in_smem ? (size_t)p.K * kEpiThreads : 0);  // [16][256]
   int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
   unsigned long long* tau_sh = (unsigned long long*)(qp_base + (size_t)kQueue * kEpiThreads);  // [256]
   int* seed_sh = (int*)(tau_sh + kEpiThreads);                                                // [2][256]
   float* seed_lists = (float*)(seed_sh + 2 * kEpiThreads);  // [2][K][256] (KR > 0)
   Smem* ctl = (Smem*)(seed_lists + (KR > 0 ? (size_t)2 * p.K * kEpiThreads : 0));
+  static_assert(kSeedListOfs == 2 * kQueue * kEpiThreads + 2 * kEpiThreads + 2 * kEpiThreads, "layout");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   volatile int* abort_flag = &ctl->abort_flag;
@@ -564,6 +617,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       mbar_init(&ctl->acc_full[b], 1);
       mbar_init(&ctl->acc_empty[b], kEpiWarps);
     }
+    for (int a = 0; a < kAuxSlots; ++a) {
+      mbar_init(&ctl->aux_full[a], 1);
+      mbar_init(&ctl->aux_empty[a], kEpiWarps);
+    }
     mbar_init(&ctl->drain, 1);
     for (int w = 0; w < kWQ; ++w) {
       mbar_init(&ctl->wq_full[w], 1);
@@ -577,7 +634,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     seed_sh[i] = -1;
     seed_sh[kEpiThreads + i] = -1;
   }
-  if (warp == 2) {
+  if (warp == kProdWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem_base)),
                  "r"(kTmemCols)
                  : "memory");
@@ -588,17 +645,20 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   tc_fence_after();
   const uint32_t tmem = ctl->tmem_base;
 
-  if (warp == 0) {
+  if (warp == kProdWarp) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_users)) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_items)) : "memory");
       const int tail_x = p.kc * p.row_elems;  // element column of the tail chunk
-      long long g = 0;  // item tiles issued so far
-      int st = 0;        // ring stage of tile g
-      uint32_t ph = 0;   // ring pass parity of tile g
+      long long g = 0;   // item loads issued so far
+      long long at = 0;  // item tiles whose bound columns (and positions) were copied so far
+      long long na = 0;  // user tiles loaded so far
+      int st = 0;        // ring stage of load g
+      uint32_t ph = 0;   // ring pass parity of load g
       bool ok = true;
       const bool dyn = MX && p.work.next;
+      const uint32_t aux_tx = kAuxBytes + (MX ? kPosBytes : 0u);
       for (int lt = 0; ok; ++lt) {
         // take and publish the next work item
         const int slot = lt % kWQ;
@@ -617,7 +677,17 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full);
         if (p.tail_bytes)
           tma_load_2d(a_tiles + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full);
+        ++na;
         for (int j = wk.tb; j < wk.te && ok; ++j) {
+          // the tile's bound columns (and list positions) into aux slot at % kAuxSlots
+          const int as = (int)(at % kAuxSlots);
+          if (at >= kAuxSlots) ok = mbar_wait(&ctl->aux_empty[as], (uint32_t)((at / kAuxSlots - 1) & 1), abort_flag, err);
+          if (!ok) break;
+          const int64_t row0 = (int64_t)wk.b_row + (int64_t)j * kTileN;
+          mbar_expect_tx(&ctl->aux_full[as], aux_tx);
+          bulk_load(aux_ring + (size_t)as * kTileN, item_aux + row0, kAuxBytes, &ctl->aux_full[as]);
+          if constexpr (MX) bulk_load(pos_ring + (size_t)as * kTileN, p.work.item_pos + row0, kPosBytes, &ctl->aux_full[as]);
+          ++at;
           for (int h = 0; h < bs; ++h, ++g) {  // g: loads issued so far
             if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
             if (!ok) break;
@@ -634,16 +704,17 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           }
         }
       }
-      if (!ok) {  // drain the copies still in flight before the CTA exits
-        for (long long gg = (g > p.stages ? g - p.stages : 0); gg < g; ++gg) {
-          uint64_t* bar = &ctl->b_full[gg % p.stages];
-          const unsigned long long t0 = globaltimer();
-          while (!mbar_try_wait(bar, (uint32_t)((gg / p.stages) & 1)) && globaltimer() - t0 < kWaitNs) {
-          }
-        }
+      if (!ok) {  // drain the operand copies still in flight before the CTA exits
+        for (long long gg = (g > p.stages ? g - p.stages : 0); gg < g; ++gg)
+          mbar_drain(&ctl->b_full[gg % p.stages], (uint32_t)((gg / p.stages) & 1));
+        if (na > 0) mbar_drain(&ctl->a_full, (uint32_t)((na - 1) & 1));
       }
+      // the select warps wait for a tile's bound columns only when they need
+      // them: the last copies may still be landing, on either path
+      for (long long aa = (at > kAuxSlots ? at - kAuxSlots : 0); aa < at; ++aa)
+        mbar_drain(&ctl->aux_full[aa % kAuxSlots], (uint32_t)((aa / kAuxSlots) & 1));
     }
-  } else if (warp == 1) {
+  } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       // instruction descriptor: D = F32, A = B = BF16, both K-major, N, M
@@ -713,13 +784,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       }
       // all MMAs issued by this thread complete before TMEM is released
       mma_commit(&ctl->drain);
-      const unsigned long long t0 = globaltimer();
-      while (!mbar_try_wait(&ctl->drain, 0) && globaltimer() - t0 < kWaitNs) {
-      }
+      mbar_drain(&ctl->drain, 0);
     }
-  } else if (warp >= kEpiWarp0) {
+  } else {
     // ------------------------------------------------------------ select
-    const int e = warp - kEpiWarp0;
+    const int e = warp;
     const int q = e % 4, c2 = e / 4;       // lane quarter, column half
     const int row = 32 * q + lane;         // user row within the tile
     const int slot = c2 * kTileM + row;    // this thread's index among the 256
@@ -728,55 +797,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     c.heap = heap_base + slot;
     c.K = p.K;
     c.cap = o.cap;
-    c.qh = qh_base + slot;
-    c.qp = qp_base + slot;
-    c.tau_mine = tau_sh + slot;
-    c.tau_partner = tau_sh + (c2 ^ 1) * kTileM + row;
-    c.seed_mine = seed_sh + slot;
-    c.seed_partner = seed_sh + (c2 ^ 1) * kTileM + row;
-    c.seed_list = seed_lists + slot;
-    c.seed_list_partner = seed_lists + (c2 ^ 1) * kTileM + row;
+    c.qbase = qh_base;
+    c.slot = slot;
+    c.pslot = (c2 ^ 1) * kTileM + row;
     c.g = p.g;
-    long long g = 0;
+    long long g = 0;  // item tiles processed: the accumulator and aux-ring sequence
     bool ok = true;
     unsigned long long emitted = 0, slow = 0;
-    // this warp's copy of the bound columns and item positions of its 128
-    // items of the current tile, prefetched one tile ahead into registers
-    // (4 entries per lane); the tile after the last of a work item is the
-    // first of the CTA's next work item
-    float2* aux_tile = aux_base + (size_t)e * kHalfN;
-    int32_t* pos_tile = posb_base + (size_t)e * kHalfN;
-    float2 pre[4];
-    int32_t prep[4];
-    auto prefetch = [&](int64_t brow0) {  // B row of this warp's first column
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int64_t br = brow0 + lane * 4 + t;
-        pre[t] = item_aux[br];
-        if constexpr (MX) prep[t] = p.work.item_pos[br];
-      }
-    };
-    // the index of the CTA's lt-th work item (waits for the producer to
-    // publish it; warp-uniform)
-    auto peek_work = [&](int lt_, int* wi_out) {
-      bool okp = mbar_wait(&ctl->wq_full[lt_ % kWQ], (uint32_t)((lt_ / kWQ) & 1), abort_flag, err);
-      okp = __all_sync(0xffffffffu, okp);
-      *wi_out = okp ? *(volatile int*)&ctl->wq[lt_ % kWQ] : n_work;
-      return okp;
-    };
-    {
-      int w0i = n_work;
-      ok = peek_work(0, &w0i);
-      if (ok && w0i < n_work) {
-        const WorkItem w0 = get_work<MX>(p, w0i, n_it);
-        prefetch((int64_t)w0.b_row + (int64_t)w0.tb * kTileN + c2 * kHalfN);
-      }
-    }
     for (int lt = 0; ok; ++lt) {  // work items of this CTA
-      int wi = n_work;
-      ok = peek_work(lt, &wi);
+      const int wslot = lt % kWQ;
+      ok = __all_sync(kFull, mbar_wait(&ctl->wq_full[wslot], (uint32_t)((lt / kWQ) & 1), abort_flag, err));
+      const int wi = ok ? *(volatile int*)&ctl->wq[wslot] : n_work;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&ctl->wq_empty[lt % kWQ]);
+      if (lane == 0) mbar_arrive(&ctl->wq_empty[wslot]);
       if (!ok || wi >= n_work) break;
       const WorkItem wk = get_work<MX>(p, wi, n_it);
       const int64_t u = MX ? (int64_t)p.work.row_user[wk.a_row + row] : (int64_t)wk.a_row + row;
@@ -804,9 +837,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if constexpr (KR > 0) {
 #pragma unroll
             for (int i = 0; i < KR; ++i) s.d[i] = i < p.K ? src[i] : kNegInf;
-            s.tau = s.d[0];
-#pragma unroll
-            for (int i = 0; i < KR; ++i) s.tau = (i < p.K) ? s.d[i] : s.tau;
+            s.tau = topk_kth(s, p.K);
           } else {  // the row is descending: reversed, it is a min-heap
             for (int i = 0; i < p.K; ++i) c.heap[i * kEpiThreads] = src[p.K - 1 - i];
             s.tau = c.heap[0];
@@ -815,35 +846,22 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           tc_publish(s, c);
         }
       }
+      // a fresh work item merges the two halves' first-tile lists once both exist
+      bool merged = restoring || KR == 0;
+      const int par = lt & 1;
       for (int j = wk.tb; j < wk.te; ++j, ++g) {
         const int b = (int)(g & 1);
-        ok = mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), abort_flag, err);
-        // lanes leave together: the tcgen05.ld below needs the whole warp
-        ok = __all_sync(0xffffffffu, ok);
+        // lanes leave together: TMEM loads are warp-collective
+        ok = __all_sync(kFull, mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), abort_flag, err));
         if (!ok) break;
         tc_fence_after();
-        __syncwarp();  // the previous tile's offers are done with aux_tile / pos_tile
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          aux_tile[lane * 4 + t] = pre[t];
-          if constexpr (MX) pos_tile[lane * 4 + t] = prep[t];
-        }
-        __syncwarp();
-        if constexpr (MX) {
-          if (j + 1 < wk.te) {
-            prefetch((int64_t)wk.b_row + (int64_t)(j + 1) * kTileN + c2 * kHalfN);
-          } else {  // the first tile of the next work item, once published
-            int wni = n_work;
-            if (peek_work(lt + 1, &wni) && wni < n_work) {
-              const WorkItem wn = get_work<MX>(p, wni, n_it);
-              prefetch((int64_t)wn.b_row + (int64_t)wn.tb * kTileN + c2 * kHalfN);
-            }
-          }
-        } else {  // next tile (wraps to the first of the next user tile)
-          prefetch((int64_t)((j + 1 < n_it) ? j + 1 : 0) * kTileN + c2 * kHalfN);
-        }
+        const int as = (int)(g % kAuxSlots);
+        const uint32_t aph = (uint32_t)((g / kAuxSlots) & 1);
+        const float2* aux = aux_ring + (size_t)as * kTileN + c2 * kHalfN;
+        const int32_t* pos = pos_ring + (size_t)as * kTileN + c2 * kHalfN;
+        bool aux_ready = false;
         {  // the partner's threshold, if it is for this work item
-          const unsigned long long pt = *c.tau_partner;
+          const unsigned long long pt = *c.tau(c.pslot);
           if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
           // and the one shared by the user's other item chunks (zero bits: none yet, NaN, ignored)
           if constexpr (MX)
@@ -852,31 +870,42 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTileN + c2 * kHalfN);
         const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
-        uint32_t r[64];
         const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
-        if (first) {  // warp-uniform: tcgen05.ld is a warp-collective instruction
-          // (inactive lanes hold tau = +inf and insert nothing)
-#pragma unroll 1
-          for (int h = 0; h < 2; ++h) {
-            tmem_ld64(taddr + 64 * h, r);
-            seed64(s, c, r, 64 * h, valid - 64 * h, aux_tile);
-          }
+        if (first) {
+          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, abort_flag, err));
+          if (!ok) break;
+          aux_ready = true;
+          seed_tile(s, c, taddr, valid, aux, active);
           if (active) {
-            s.tau_eff = s.tau;
+            s.tau_eff = fmaxf(s.tau_eff, s.tau);
             tc_publish(s, c);
-            if constexpr (KR > 0) seed_merge(s, c, wi, lt & 1);
           }
+          seed_publish(s, c, wi, par);
         }
-        // the two 64-column halves run through one copy of the select code
-        // (a second inlined copy costs more in instruction-cache misses)
+        if (!merged) merged = seed_try_merge(s, c, wi, par, active);
+        // common case: the maxima of the two 64-column halves and two votes
+        // (one load site in a rolled loop: two unrolled 64-register loads
+        // make the compiler keep both destination sets apart)
+        unsigned halves = 0;
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          tmem_ld64(taddr + 64 * h, r);
-          select64<KR, MX>(s, c, r, 64 * h, valid - 64 * h, aux_tile, rank0, pos_tile, slow, first);
+          const float m = tmem_ldmax64(taddr + 64 * h);
+          halves |= __any_sync(kFull, m >= s.tau_eff) ? (1u << h) : 0u;
+        }
+        if (halves) {
+          slow += __popc(halves);
+          if (!aux_ready) {
+            ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, abort_flag, err));
+            if (!ok) break;
+          }
+          select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves, first);
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->acc_empty[b]);
+        if (lane == 0) {
+          mbar_arrive(&ctl->acc_empty[b]);
+          mbar_arrive(&ctl->aux_empty[as]);
+        }
       }
       if (!ok) break;
       if (active) {
@@ -899,15 +928,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) emitted += __shfl_xor_sync(0xffffffffu, emitted, off);
+    for (int off = 16; off > 0; off >>= 1) emitted += __shfl_xor_sync(kFull, emitted, off);
     if (lane == 0 && emitted) atomicAdd(&stats->cand_emitted, emitted);
-    if (lane == 0 && slow) atomicAdd(&stats->select_slow, slow);  // warp-level slow-path entries
+    if (lane == 0 && slow) atomicAdd(&stats->select_slow, slow);  // warp x 64-column halves with a hit
   }
 
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 2) {
+  if (warp == kProdWarp) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
@@ -921,7 +950,7 @@ size_t tc_smem_bytes(const TcParams& p) {
   const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
   const size_t b_bytes = (size_t)p.kc * b_chunk + sub_rows * p.tail_bytes;
   return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +
-         (sizeof(float2) + sizeof(int32_t)) * kEpiWarps * kHalfN + 2 * sizeof(float) * kQueue * kEpiThreads +
+         (sizeof(float2) + sizeof(int32_t)) * kAuxSlots * kTileN + 2 * sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
          (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
 }
