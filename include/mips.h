@@ -224,7 +224,11 @@ typedef struct {
   int method;              /* 0 = blocked multiply (mips_topk), 1 = Maximus */
   int slots;               /* batches in flight at once (1..8), one stream each */
   int64_t max_batch_users; /* users per batch; a larger request runs alone */
-  int64_t mem_budget;      /* device bytes the batches in flight may hold (0 = unlimited) */
+  int64_t mem_budget;      /* device bytes the batches in flight may hold (0 = unlimited): a batch is
+                            * admitted only if its bytes (its call's workspace, computed by that call's
+                            * own layout, plus its buffers) fit beside those in flight, or nothing is
+                            * in flight; while the slots hold more than this, a slot frees its
+                            * workspace and buffers after each batch */
 } mips_server_options;
 
 typedef struct {
@@ -235,6 +239,11 @@ typedef struct {
   int64_t batch_users;  /* users in that batch */
   int batch_K;          /* K the batch ran with */
   int slot;             /* stream slot of the batch */
+  int64_t batch_bytes;    /* device bytes its batch was admitted with: the workspace its call lays out
+                           * plus the batch's user rows and results */
+  int64_t batch_ws_bytes; /* workspace bytes that call actually took (equal to the admitted workspace) */
+  int64_t inflight_bytes; /* admitted bytes of every batch in flight when its batch started, its own included:
+                           * never above mem_budget when mem_budget is at least one batch */
 } mips_request_info;
 
 /* Creates the server (its threads, streams, worker handles).  The index
@@ -339,10 +348,13 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
  *
  * Scratch comes from one static device array of 32 MiB per GPU, reserved
  * when the library's code is loaded on that GPU and held until the process
- * exits.  A call needs 8 n_items + n_users (16 + 20 (4K + 96)) bytes of it
- * plus 2 KiB (K = 10: about 12,000 users against 17,770 items); larger
- * calls return MIPS_ERR_ARG (split the users).  Limits as mips_topk:
- * 1 <= f <= 128, 1 <= K <= min(n_items, 128).
+ * exits.  A call needs 8 n_items + n_users (20 + 20 cap) bytes of it plus
+ * at most 4 KiB of counters and alignment padding, where cap = max(4K + 96,
+ * K (2 + ln(n_items / K)) + 96) is the candidate slots per user (K = 10:
+ * about 8,700 users against 17,770 items); larger calls return
+ * MIPS_ERR_ARG (split the users).  A user whose candidates overflow its
+ * slots is scored exhaustively (still exact, slower).  Limits as
+ * mips_topk: 1 <= f <= 128, 1 <= K <= min(n_items, 128).
  *
  * All calls share that array and it keeps the last call's contents (each
  * call clears the counters that must start at zero).  Calls that overlap on

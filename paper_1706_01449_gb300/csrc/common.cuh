@@ -118,6 +118,41 @@ __device__ __forceinline__ double dot_f64_seq(const float* u, const float* v, in
   return s;
 }
 
+// ---------------------------------------------------------------------------
+// Norm bounds that hold at any magnitude.  A plain FP32 sum of squares loses
+// every term below 2^-149 and most bits of those below 2^-126, so the norm of
+// a row of tiny entries can come out 0.  The row is therefore scaled by an
+// exact power of two 2^k that puts its largest |entry| in [1/2, 1) (then the
+// largest square is at least 1/4 and the sum's relative error bound holds),
+// and the bound is scaled back by 2^-k rounding upward.
+// ---------------------------------------------------------------------------
+// 2^e for e in [-126, 127] (exact).
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
+
+// k with amax 2^k in [1/2, 1), for finite amax > 0 (k in [-128, 149]).
+__device__ __forceinline__ int norm_scale_exp(float amax) {
+  int ex;
+  frexpf(amax, &ex);
+  return -ex;
+}
+
+// x 2^k for k in [-128, 149]: exact unless the result falls below 2^-126
+// (then the absolute error is below 2^-149).
+__device__ __forceinline__ float scale_pow2(float x, int k) {
+  const int k1 = k / 2;
+  return (x * exp2i(k1)) * exp2i(k - k1);
+}
+
+// y 2^-k rounded upward (an upper bound stays an upper bound).
+__device__ __forceinline__ float unscale_pow2_ru(float y, int k) {
+  const int k1 = -k / 2;
+  return __fmul_ru(__fmul_ru(y, exp2i(k1)), exp2i(-k - k1));
+}
+
+// Squared norms below this are treated as unreliable (subnormal terms) by
+// the bound kernels, which then fall back to no pruning.
+#define kTinySq 7.8886090522101181e-31f  // 2^-100
+
 // Upper bound on |computed - exact| for the FP32 fused score with f terms,
 // relative to ||u|| ||i||: recursive FMA summation error gamma_f (Higham,
 // "Accuracy and Stability of Numerical Algorithms", 2nd ed., Sec. 3.1) with

@@ -42,6 +42,10 @@ __host__ __device__ inline uint32_t float_desc_key(float x) {
   return ~asc;
 }
 
+// Multiprocessor count of the current device (queried once per device);
+// launch sizes of the grid-stride helper kernels scale with it.
+int sm_count();
+
 // Round n up to a multiple of m.
 inline int64_t round_up(int64_t n, int64_t m) { return (n + m - 1) / m * m; }
 
@@ -194,6 +198,16 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
 mips_index_t index_worker_clone(mips_index_t src);
 int index_f(mips_index_t idx);
 int64_t index_n_items(mips_index_t idx);
+// Workspace bytes a mips_topk (method 0) or mips_topk_maximus (method 1)
+// call on n_users users with this K takes: the calls' own layout, run
+// without device work (the index must be idle on the host side).
+size_t call_workspace_bytes(mips_index_t idx, int64_t n_users, int K, int method);
+// Bytes of workspace the last call took, and the capacity the index holds.
+size_t index_workspace_used(mips_index_t idx);
+size_t index_workspace_held(mips_index_t idx);
+// Free the index's workspace (stream-ordered on s; the next call allocates
+// again).
+cudaError_t index_release_workspace(mips_index_t idx, cudaStream_t s);
 
 // Set the calling thread's message returned by mips_last_error().
 void set_last_error_message(const char* msg);

@@ -204,7 +204,10 @@ __global__ void normalize_rows_kernel(float* __restrict__ cent, int C, int f) {
 // ---------------------------------------------------------------- bounds
 // cos_b[j] (as order-preserving bits, initialised to +1): a lower bound of
 // the smallest cosine between a member of cluster j and c_j.  Zero users are
-// left out; a zero centroid gives -1 (theta_b = pi).
+// left out, and so are users whose FP32 ||u||^2 is below 2^-100, where
+// subnormal squares make the computed cosine unreliable (the rescore scores
+// those users exhaustively whatever the walk did); a centroid that small
+// gives -1 (theta_b = pi).
 __global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, int f, const int32_t* __restrict__ assign,
                             const float* __restrict__ cent, uint32_t* __restrict__ cosb_ord) {
   const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -218,9 +221,9 @@ __global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, in
     su = __fmaf_rn(ur[k], ur[k], su);
     sc = __fmaf_rn(cr[k], cr[k], sc);
   }
-  if (su == 0.f) return;
+  if (su < kTinySq) return;
   float c;
-  if (sc == 0.f) {
+  if (sc < kTinySq) {
     c = -1.f;
   } else {
     // each factor carries a relative error below (f + 2) 2^-24; |cos| <= 1
@@ -242,12 +245,14 @@ __host__ __device__ __forceinline__ size_t cb_items_floats(int f) {  // rounded 
   return ((size_t)f * (kCbItems + 1) + 3) & ~(size_t)3;
 }
 
+// ni: the item's norm bound from row_norm_ub_kernel (power-of-two scaled
+// sums, valid at any magnitude; 0 only for the zero item).
 __device__ __forceinline__ float cbound_value(float d, float sc, float si, float ni, float y, int f) {
   float g;
-  if (si == 0.f) {
+  if (ni == 0.f) {
     g = 0.f;  // zero item: bound 0 = its score
-  } else if (sc == 0.f || y <= -1.f) {
-    g = 1.f;  // theta_b = pi: no pruning
+  } else if (sc < kTinySq || si < kTinySq || y <= -1.f) {
+    g = 1.f;  // theta_b = pi, or a cosine FP32 cannot evaluate reliably: no pruning
   } else {
     float x = __fdiv_rn(d, __fsqrt_rn(sc) * __fsqrt_rn(si)) + (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
     x = fminf(x, 1.f);
@@ -764,7 +769,7 @@ __global__ void mx_visited_kernel(const int32_t* __restrict__ user_row, int64_t 
 }
 
 unsigned copy_blocks(int C) {  // blocks per cluster of the list copies: about 64 per SM in all
-  return (unsigned)std::max(1, 152 * 64 / std::max(C, 1));
+  return (unsigned)std::max(1, sm_count() * 64 / std::max(C, 1));
 }
 
 int bits_for(int64_t x) {  // bits to hold 0..x
@@ -979,7 +984,7 @@ cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, co
   cudaError_t e = launch_kmeans_assign(users, n_users, f, cent_fit, hn2_fit, C_fit, assign, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int) * C_fit, s);
   if (e != cudaSuccess) return e;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, 152 * 8));
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, (int64_t)sm_count() * 8));
   cluster_used_kernel<<<g, 256, 0, s>>>(assign, n_users, used);
   cluster_pack_kernel<<<1, 1024, 0, s>>>(used, C_fit, cent_fit, f, C_eff, remap, cent);
   cluster_remap_kernel<<<g, 256, 0, s>>>(assign, n_users, remap);
@@ -997,7 +1002,7 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
   }
   cudaError_t e = cudaMemsetAsync(absmax, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  absmax_kernel<<<152 * 4, 256, 0, s>>>(users, n_users * f, absmax);
+  absmax_kernel<<<sm_count() * 4, 256, 0, s>>>(users, n_users * f, absmax);
   *launches += 2;
   kmeans_scale_kernel<<<1, 32, 0, s>>>(absmax, n_users, scale);
   *launches += 1;
@@ -1013,7 +1018,7 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
       const size_t smem = (size_t)C * f * 8 + (size_t)C * 4;
       e = cudaFuncSetAttribute(kmeans_accum_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users * f + 255) / 256, 152 * 8));
+      const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users * f + 255) / 256, (int64_t)sm_count() * 8));
       kmeans_accum_smem_kernel<<<dim3(bx, 1), 256, smem, s>>>(users, n_users, f, assign, C, C, scale, sums, counts);
     } else {  // many clusters: the global adds spread over C * f addresses
       kmeans_accum_kernel<<<(unsigned)((n_users * f + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, C, scale,
@@ -1052,7 +1057,7 @@ cudaError_t maximus_group(const int32_t* assign, int64_t n_users, int C, uint32_
   if (e != cudaSuccess) return e;
   {
     const int use_smem = C <= 8192;
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, 152 * 4));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, (int64_t)sm_count() * 4));
     cluster_count_kernel<<<blocks, 256, use_smem ? sizeof(int) * C : 0, s>>>(assign, n_users, C, use_smem, counts);
   }
   cluster_offsets_kernel<<<1, 32, 0, s>>>(counts, C, offsets, tile_off);

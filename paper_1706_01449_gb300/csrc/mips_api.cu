@@ -241,10 +241,12 @@ int tc_cap(int K, int64_t n, bool chunked) {
 
 // Blocked multiply (Sec. III-B) over the index's items with fused select,
 // then the exact rescore.
+// size_only: lay out the workspace, store the bytes it needs there and
+// return before any device work (no pointer argument is used).
 mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
-                    double* out_score, cudaStream_t s) {
+                    double* out_score, cudaStream_t s, size_t* size_only = nullptr) {
   const int f = idx->f;
-  idx->mx.C = 0;  // the workspace is reused: earlier Maximus views are gone
+  if (!size_only) idx->mx.C = 0;  // the workspace is reused: earlier Maximus views are gone
   // candidate pass: tcgen05 BF16 when the index has BF16 operands and the
   // tiling fits shared memory for this K, else the FP32 CUDA-core kernel
   TcParams p{};
@@ -297,6 +299,11 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     o_cpos = idx->ws.take(sizeof(int32_t) * idx->n_items_pad);
     o_ctau = idx->ws.take(sizeof(unsigned) * n_users);
   }
+  if (size_only) {
+    *size_only = idx->ws.used;
+    idx->ws.reset();
+    return MIPS_OK;
+  }
   MIPS_CUDA(idx->ws.ensure(idx->ws.used, s));
   SelectOut so{idx->ws.at<float>(o_tau), idx->ws.at<int>(o_n), idx->ws.at<int32_t>(o_pos),
                idx->ws.at<float>(o_ub), cap, lists,
@@ -332,7 +339,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
       idx->launches += 1;
       p.mode = 1;
       p.work = TcWork{cw, cw + nw, cw + 2 * nw, cw + 3 * nw, idx->ws.at<int>(o_cnw), idx->ws.at<int32_t>(o_crow),
-                      idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0, nullptr};
+                      idx->ws.at<int32_t>(o_cpos), cw + 4 * nw, 0, nullptr, idx->n_items};
       // the chunks of a user share their thresholds (zero bits = none yet)
       so.tau_glob = idx->ws.at<unsigned>(o_ctau);
       MIPS_CUDA(cudaMemsetAsync(so.tau_glob, 0, sizeof(unsigned) * n_users, s));
@@ -378,7 +385,7 @@ void affine_sample(int64_t n, uint64_t seed, uint64_t* a_out, uint64_t* b_out) {
 // Maximus (Sec. IV, Algorithm 1): k-means, theta_b + CBound, per-cluster
 // sort and user grouping, grouped walk, exact rescore.
 mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
-                        double* out_score, cudaStream_t s) {
+                        double* out_score, cudaStream_t s, size_t* size_only = nullptr) {
   const int f = idx->f;
   const int64_t nI = idx->n_items;
   // with fitted centroids only the clusters that receive users are kept
@@ -468,6 +475,11 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     o_wk1 = ws.take(sizeof(uint32_t) * max_work);
     o_wv0 = ws.take(sizeof(int32_t) * max_work);
     o_wv1 = ws.take(sizeof(int32_t) * max_work);
+  }
+  if (size_only) {  // (run_bmm's sizing mode)
+    *size_only = ws.used;
+    ws.reset();
+    return MIPS_OK;
   }
   MIPS_CUDA(ws.ensure(ws.used, s));
 
@@ -575,7 +587,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     p.mode = 1;
     if (p.heap_global) p.heap_mem = ws.at<float>(o_heapm);
     const int64_t mw = max_work;
-    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1, nullptr};
+    p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1, nullptr,
+                    nI};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
@@ -587,7 +600,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     // second pass: uneven work items, claimed dynamically (counter in n_work[2])
     MIPS_CUDA(cudaMemsetAsync(m.n_work + 2, 0, sizeof(int), s));
     p.work = TcWork{m.w2, m.w2 + mw, m.w2 + 2 * mw, m.w2 + 3 * mw, m.n_work + 1, m.row_user, m.pos_c, nullptr, 1,
-                    m.n_work + 2};
+                    m.n_work + 2, nI};
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
@@ -778,6 +791,29 @@ mips_index_t mips::index_worker_clone(mips_index_t src) {
 
 int mips::index_f(mips_index_t idx) { return idx->f; }
 int64_t mips::index_n_items(mips_index_t idx) { return idx->n_items; }
+
+size_t mips::call_workspace_bytes(mips_index_t idx, int64_t n_users, int K, int method) {
+  size_t bytes = 0;
+  if (method == 0)
+    run_bmm(idx, nullptr, n_users, K, nullptr, nullptr, nullptr, &bytes);
+  else
+    run_maximus(idx, nullptr, n_users, K, nullptr, nullptr, nullptr, &bytes);
+  return bytes;
+}
+
+size_t mips::index_workspace_used(mips_index_t idx) { return idx->ws.used; }
+size_t mips::index_workspace_held(mips_index_t idx) { return idx->ws.cap; }
+
+cudaError_t mips::index_release_workspace(mips_index_t idx, cudaStream_t s) {
+  if (!idx->ws.base) return cudaSuccess;
+  cudaError_t e = cudaFreeAsync(idx->ws.base, s);
+  idx->ws.base = nullptr;
+  idx->ws.cap = 0;
+  idx->ws.used = 0;
+  ++idx->ws.gen;  // graphs captured over it are stale
+  idx->mx.C = 0;
+  return e;
+}
 
 extern "C" {
 

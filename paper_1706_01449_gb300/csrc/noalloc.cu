@@ -13,13 +13,20 @@
 // Limits and sharing (also stated in include/mips.h):
 //   * the scratch is kNoAllocScratchBytes (32 MiB) on every GPU that loads
 //     the library, held until the process exits;
-//   * a call needs 8 n_items + n_users (16 + 20 (4K + 96)) bytes plus 2 KiB of
-//     headers and is rejected with MIPS_ERR_ARG beyond that;
+//   * a call needs 8 n_items + n_users (20 + 20 cap) bytes plus at most 4 KiB
+//     of counters and alignment padding, cap = max(4K + 96, K (2 + ln(n_items
+//     / K)) + 96) candidate slots per user (the FP32 blocked multiply's list
+//     capacity: the expected number of K-th-largest records of a stream of
+//     n_items scores, with room to spare), and is rejected with MIPS_ERR_ARG
+//     beyond that; a user whose candidates still overflow its list is scored
+//     exhaustively by the rescore (exact, slower);
 //   * every call uses the same array: calls that overlap on the GPU (two
 //     streams, two host threads) race and corrupt each other's results, so
 //     callers must serialise them;
 //   * the array keeps the last call's contents; the parts that must start
 //     at zero (counters, error word) are cleared by each call.
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <mutex>
@@ -65,6 +72,12 @@ __global__ void iota_kernel(int32_t* p, int64_t n) {
 
 size_t up256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Candidate slots per user (see the size rule above).
+int list_cap(int K, int64_t n) {
+  const double r = n > K ? std::log((double)n / K) : 0.0;
+  return std::max(4 * K + 96, (int)std::min<int64_t>((int64_t)std::ceil(K * (2.0 + r)) + 96, n + 96));
+}
+
 // message for mips_last_error(), formatted locally then handed over
 mips_status report(mips_status st, const char* fmt, ...) {
   char buf[256];
@@ -91,7 +104,7 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
   if (f < 1 || f > 128 || n_items < 1 || n_items >= (1ll << 31) || n_users < 1 || n_users >= (1ll << 31) || K < 1 ||
       K > 128 || K > n_items)
     return report(MIPS_ERR_ARG, "size out of range (1<=f<=128, 1<=K<=min(n_items,128), n>=1)");
-  const int cap = 4 * K + 96;
+  const int cap = list_cap(K, n_items);
   const size_t slots = (size_t)n_users * cap;
   const size_t need = up256(sizeof(DevStats)) + up256(sizeof(int)) * 3 + up256(4 * (size_t)n_items) * 2 +
                       up256(4 * (size_t)n_users) * 3 + up256(8 * (size_t)n_users) + up256(4 * slots) * 3 + up256(8 * slots);

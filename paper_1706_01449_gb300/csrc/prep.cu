@@ -35,12 +35,22 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // FP32 sum of squares of f terms has relative error below f 2^-24; the
 // square root halves it.  This factor lifts the computed norm above the
-// exact one with room to spare.
+// exact one with room to spare.  The sums are taken over rows scaled by a
+// power of two (common.cuh: the largest |entry| in [1/2, 1)), so no term
+// that matters is subnormal; `floor` covers the absolute error of those
+// that are (below 2^-149 per entry and per square).
 __device__ __forceinline__ float norm_ub(float sumsq, int f) {
   return __fsqrt_rn(sumsq) * (1.0f + (float)(f + 2) * 1.1920929e-07f);
 }
+__device__ __forceinline__ float tiny_floor(int f) { return (float)f * 1.1210388e-44f; }  // f 2^-146
 
 __global__ void row_norm_ub_kernel(const float* __restrict__ x, int64_t n, int f,
                                    float* __restrict__ out, int* err) {
@@ -48,12 +58,35 @@ __global__ void row_norm_ub_kernel(const float* __restrict__ x, int64_t n, int f
   int lane = threadIdx.x & 31;
   if (row >= n) return;
   const float* r = x + row * f;
+  float amax = 0.f;
+  bool bad = false;
+  for (int k = lane; k < f; k += 32) {
+    amax = fmaxf(amax, fabsf(r[k]));
+    bad |= !isfinite(r[k]);
+  }
+  amax = warp_max(amax);
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) {
+      atomicOr(err, DEV_ERR_NONFINITE);
+      out[row] = __int_as_float(0x7f800000);
+    }
+    return;
+  }
+  if (amax == 0.f) {  // the zero row: its norm is 0
+    if (lane == 0) out[row] = 0.f;
+    return;
+  }
+  const int e = norm_scale_exp(amax);
   float ss = 0.f;
-  for (int k = lane; k < f; k += 32) ss = __fmaf_rn(r[k], r[k], ss);
+  for (int k = lane; k < f; k += 32) {
+    const float y = scale_pow2(r[k], e);
+    ss = __fmaf_rn(y, y, ss);
+  }
   ss = warp_sum(ss);
   if (lane == 0) {
-    if (!isfinite(ss)) atomicOr(err, DEV_ERR_NONFINITE);
-    out[row] = norm_ub(ss, f);
+    const float nb = unscale_pow2_ru(norm_ub(ss + tiny_floor(f), f), e);
+    if (!isfinite(nb)) atomicOr(err, DEV_ERR_NONFINITE);
+    out[row] = nb;
   }
 }
 
@@ -70,6 +103,14 @@ __device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row,
     for (int k = lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
     return;
   }
+  float amax = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (lane + 32 * j < f) amax = fmaxf(amax, fabsf(v[j]));
+  amax = warp_max(amax);
+  // sums over the row scaled by 2^e (largest |entry| in [1/2, 1)); a
+  // non-finite or zero row keeps e = 0 (the non-finite check below flags it)
+  const int e = (amax > 0.f && isfinite(amax)) ? norm_scale_exp(amax) : 0;
   float ss_x = 0.f, ss_t = 0.f, ss_d = 0.f;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -79,9 +120,10 @@ __device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row,
       const __nv_bfloat16 q = __float2bfloat16_rn(x);
       const float t = __bfloat162float(q);
       const float d = __fsub_rn(x, t);  // exact: t is x rounded to 8 significant bits
-      ss_x = __fmaf_rn(x, x, ss_x);
-      ss_t = __fmaf_rn(t, t, ss_t);
-      ss_d = __fmaf_rn(d, d, ss_d);
+      const float xs = scale_pow2(x, e), ts = scale_pow2(t, e), ds = scale_pow2(d, e);
+      ss_x = __fmaf_rn(xs, xs, ss_x);
+      ss_t = __fmaf_rn(ts, ts, ss_t);
+      ss_d = __fmaf_rn(ds, ds, ss_d);
       o[k] = q;
     }
   }
@@ -89,8 +131,14 @@ __device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row,
   ss_t = warp_sum(ss_t);
   ss_d = warp_sum(ss_d);
   const float g = (float)(fp + 4) * 9.5367432e-07f + (float)f * 8.8817842e-16f;  // 2^-20, 2^-50
-  float nhat = fmaxf(norm_ub(ss_x, f), norm_ub(ss_t, f));
-  float errn = norm_ub(ss_d, f);
+  // the zero row keeps 0 bounds (its scores are exactly 0); otherwise the
+  // largest scaled square is at least 1/4, and the floor covers subnormal
+  // squares of small entries and of the rounding errors d
+  float nhat = 0.f, errn = 0.f;
+  if (amax > 0.f) {
+    nhat = unscale_pow2_ru(fmaxf(norm_ub(ss_x + tiny_floor(f), f), norm_ub(ss_t + tiny_floor(f), f)), e);
+    errn = unscale_pow2_ru(norm_ub(ss_d + tiny_floor(f), f), e);
+  }
   __nv_bfloat16 nhat_b = __float2bfloat16_ru(nhat);
   __nv_bfloat16 eb_b = __float2bfloat16_ru(__fmul_ru(__fmaf_ru(g, nhat, errn), 1.0f + g));
   if (lane == 0) {
@@ -190,10 +238,27 @@ void launch_sample_keys(int64_t n, uint64_t a, uint64_t b, int64_t ns, uint32_t*
   sample_keys_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b, ns, keys, ids);
 }
 
+int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= 64) {
+    int n = 1;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
 void launch_bmm_chunks(int n_ut, int nch, int tpc, int n_it, int64_t n_users, int64_t n_items_pad, int* work5,
                        int* n_work, int32_t* row_user, int32_t* item_pos, cudaStream_t s) {
   const int64_t nw = (int64_t)n_ut * nch;
-  bmm_chunk_work_kernel<<<152 * 2, 256, 0, s>>>(n_ut, nch, tpc, n_it, n_users, n_items_pad, work5, work5 + nw,
+  bmm_chunk_work_kernel<<<sm_count() * 2, 256, 0, s>>>(n_ut, nch, tpc, n_it, n_users, n_items_pad, work5, work5 + nw,
                                                 work5 + 2 * nw, work5 + 3 * nw, work5 + 4 * nw, n_work, row_user,
                                                 item_pos);
 }

@@ -520,7 +520,7 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
   if (e != cudaSuccess) return e;
   rescore_collect_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, K, o, out_idx,
                                                                             out_score, stats);
-  rescore_dot_kernel<<<152 * 8, 256, 0, s>>>(users, f, items_sorted, o);
+  rescore_dot_kernel<<<sm_count() * 8, 256, 0, s>>>(users, f, items_sorted, o);
   // threads per block so that the per-thread lists of K + 1 keys fit in 96 KiB
   int T = 128;
   while (T > 32 && (size_t)T * (K + 1) * 12 > 96 * 1024) T -= 32;
@@ -530,7 +530,7 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
   rescore_select_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
                                                                            item_nrm_ub, K, o, out_idx, out_score,
                                                                            stats, err);
-  rescore_warp_kernel<<<152 * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,
+  rescore_warp_kernel<<<sm_count() * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,
                                                              o.ovf_list, o.ovf_count, out_idx, out_score, stats,
                                                              err);
   return cudaGetLastError();

@@ -38,6 +38,7 @@ struct Request {
   double t_submit = 0, t_start = 0, t_done = 0;
   int64_t batch = -1, batch_users = 0;
   int batch_K = 0, slot = -1;
+  size_t batch_bytes = 0, batch_ws = 0, inflight = 0;
   bool done = false;
   mips_status status = MIPS_OK;
   std::string error;
@@ -55,13 +56,16 @@ struct Slot {
   float* d_users = nullptr;
   int32_t* d_idx = nullptr;
   double* d_score = nullptr;
-  int64_t cap_users = 0, cap_out = 0;  // rows x f floats, rows x K outputs
+  int64_t cap_users = 0, cap_out = 0;    // pinned host capacity: rows x f floats, rows x K outputs
+  int64_t dcap_users = 0, dcap_out = 0;  // device capacity (freed under a memory budget)
   // the batch in flight
   bool busy = false, launched = false;
   std::vector<RequestP> reqs;
   int64_t batch = -1, n = 0;
   int K = 0;
-  size_t bytes = 0;
+  size_t bytes = 0;     // admitted: the call's workspace plus this batch's user and result buffers
+  size_t ws_used = 0;   // workspace the call took
+  size_t inflight = 0;  // admitted bytes of all batches in flight when this one started
   mips_status status = MIPS_OK;
   std::string error;
 };
@@ -104,10 +108,18 @@ struct mips_server_s {
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
-  size_t batch_bytes(int64_t n, int K) const {
-    // device buffers of the batch plus the call's per-user workspace
-    // (two candidate sub-lists of up to 4K + 64 entries, 20 bytes each)
-    return (size_t)n * (size_t)f * 4 + (size_t)n * K * 12 + (size_t)n * 2 * (4 * K + 64) * 20;
+  // Device bytes a batch of n users at this K holds while in flight: the
+  // workspace its call lays out (computed by the call's own layout code on
+  // the idle worker that will run it) plus its user rows and results.
+  size_t batch_bytes(mips_index_t worker, int64_t n, int K) const {
+    return call_workspace_bytes(worker, n, K, opt.method) + (size_t)n * (size_t)f * 4 + (size_t)n * K * 12;
+  }
+  // Device bytes the slots hold now (workspaces and batch buffers).
+  size_t held_bytes() const {
+    size_t b = 0;
+    for (const Slot& sl : slots)
+      b += index_workspace_held(sl.worker) + (size_t)sl.dcap_users * f * 4 + (size_t)sl.dcap_out * 12;
+    return b;
   }
   bool free_slot(int* which) const {
     for (size_t i = 0; i < slots.size(); ++i)
@@ -143,18 +155,25 @@ cudaError_t grow_dev(T*& p, size_t count, cudaStream_t s) {  // stream-ordered: 
 mips_status mips_server_s::launch(Slot& sl) {
   cudaError_t e = cudaSuccess;
   if (sl.n > sl.cap_users) {
-    if ((e = grow_host(sl.h_users, (size_t)sl.n * f)) != cudaSuccess ||
-        (e = grow_dev(sl.d_users, (size_t)sl.n * f, sl.stream)) != cudaSuccess)
-      return cuda_fail(e, "server staging allocation");
+    if ((e = grow_host(sl.h_users, (size_t)sl.n * f)) != cudaSuccess) return cuda_fail(e, "server staging allocation");
     sl.cap_users = sl.n;
+  }
+  if (sl.n > sl.dcap_users) {
+    if ((e = grow_dev(sl.d_users, (size_t)sl.n * f, sl.stream)) != cudaSuccess)
+      return cuda_fail(e, "server staging allocation");
+    sl.dcap_users = sl.n;
   }
   const int64_t outs = sl.n * sl.K;
   if (outs > sl.cap_out) {
-    if ((e = grow_host(sl.h_idx, outs)) != cudaSuccess || (e = grow_host(sl.h_score, outs)) != cudaSuccess ||
-        (e = grow_dev(sl.d_idx, outs, sl.stream)) != cudaSuccess ||
-        (e = grow_dev(sl.d_score, outs, sl.stream)) != cudaSuccess)
+    if ((e = grow_host(sl.h_idx, outs)) != cudaSuccess || (e = grow_host(sl.h_score, outs)) != cudaSuccess)
       return cuda_fail(e, "server output allocation");
     sl.cap_out = outs;
+  }
+  if (outs > sl.dcap_out) {
+    if ((e = grow_dev(sl.d_idx, outs, sl.stream)) != cudaSuccess ||
+        (e = grow_dev(sl.d_score, outs, sl.stream)) != cudaSuccess)
+      return cuda_fail(e, "server output allocation");
+    sl.dcap_out = outs;
   }
   int64_t row = 0;
   for (const RequestP& r : sl.reqs) {
@@ -168,6 +187,7 @@ mips_status mips_server_s::launch(Slot& sl) {
                        ? mips_topk(sl.worker, sl.d_users, sl.n, sl.K, sl.d_idx, sl.d_score, sl.stream)
                        : mips_topk_maximus(sl.worker, sl.d_users, sl.n, sl.K, sl.d_idx, sl.d_score, sl.stream);
   if (st != MIPS_OK) return st;
+  sl.ws_used = index_workspace_used(sl.worker);
   if ((e = cudaMemcpyAsync(sl.h_idx, sl.d_idx, sizeof(int32_t) * outs, cudaMemcpyDeviceToHost, sl.stream)) !=
           cudaSuccess ||
       (e = cudaMemcpyAsync(sl.h_score, sl.d_score, sizeof(double) * outs, cudaMemcpyDeviceToHost, sl.stream)) !=
@@ -198,7 +218,7 @@ void mips_server_s::scheduler() {
       n += r->n;
       K = std::max(K, r->K);
     }
-    const size_t bytes = batch_bytes(n, K);
+    const size_t bytes = batch_bytes(slots[which].worker, n, K);
     if (opt.mem_budget > 0 && inflight_bytes > 0 && inflight_bytes + bytes > (size_t)opt.mem_budget) {
       // admission by memory: wait for a batch in flight to finish
       cv_sched.wait(lk, [&] { return stop || inflight_bytes + bytes <= (size_t)opt.mem_budget || inflight_bytes == 0; });
@@ -214,6 +234,7 @@ void mips_server_s::scheduler() {
     sl.bytes = bytes;
     sl.batch = next_batch++;
     inflight_bytes += bytes;
+    sl.inflight = inflight_bytes;
     const double t = now();
     for (const RequestP& r : take) r->t_start = t;
     lk.unlock();
@@ -271,6 +292,9 @@ void mips_server_s::completer() {
         r->batch_users = sl.n;
         r->batch_K = sl.K;
         r->slot = (int)i;
+        r->batch_bytes = sl.bytes;
+        r->batch_ws = sl.ws_used;
+        r->inflight = sl.inflight;
         r->status = st;
         r->error = sl.error;
         r->done = true;
@@ -279,6 +303,20 @@ void mips_server_s::completer() {
       sl.busy = false;
       sl.launched = false;
       inflight_bytes -= sl.bytes;
+      // with a budget, an idle slot gives its workspace and buffers back
+      // while the slots hold more than the budget (its next batch
+      // allocates what that batch needs)
+      if (opt.mem_budget > 0 && held_bytes() > (size_t)opt.mem_budget) {
+        index_release_workspace(sl.worker, sl.stream);
+        if (sl.d_users) cudaFreeAsync(sl.d_users, sl.stream);
+        if (sl.d_idx) cudaFreeAsync(sl.d_idx, sl.stream);
+        if (sl.d_score) cudaFreeAsync(sl.d_score, sl.stream);
+        sl.d_users = nullptr;
+        sl.d_idx = nullptr;
+        sl.d_score = nullptr;
+        sl.dcap_users = 0;
+        sl.dcap_out = 0;
+      }
       progressed = true;
     }
     if (progressed) {
@@ -370,6 +408,9 @@ mips_status mips_server_wait(mips_server_t srv, int64_t request_id, double timeo
     info->batch_users = r->batch_users;
     info->batch_K = r->batch_K;
     info->slot = r->slot;
+    info->batch_bytes = (int64_t)r->batch_bytes;
+    info->batch_ws_bytes = (int64_t)r->batch_ws;
+    info->inflight_bytes = (int64_t)r->inflight;
   }
   if (r->status != MIPS_OK) return fail(r->status, "%s", r->error.c_str());
   return MIPS_OK;

@@ -173,11 +173,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 #define MIPS_R16(r, o) MIPS_R8(r, o), MIPS_R8(r, o + 8)
 #define MIPS_R64(r) MIPS_R16(r, 0), MIPS_R16(r, 16), MIPS_R16(r, 32), MIPS_R16(r, 48)
 
+// The TMEM loads are warp-collective (.sync.aligned): every lane must issue
+// the same load together, so each wrapper first reconverges the warp (the
+// select's offer loops before a load diverge lane by lane).
+
 // 32 lanes x 32 bits, 64 consecutive columns, reduced: this thread's maximum
 // of its lane's 64 columns (the values themselves are not used).
 __device__ __forceinline__ float tmem_ldmax64(uint32_t taddr) {
   uint32_t r[64];
   float m;
+  __syncwarp();
   asm volatile(
       "tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 "
       "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,"
@@ -194,6 +199,7 @@ __device__ __forceinline__ float tmem_ldmax64(uint32_t taddr) {
 // their maximum.
 __device__ __forceinline__ float tmem_ldmax16(uint32_t taddr, uint32_t (&r)[16]) {
   float m;
+  __syncwarp();
   asm volatile(
       "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, %16, "
       "[%17];\n\t"
@@ -207,6 +213,7 @@ __device__ __forceinline__ float tmem_ldmax16(uint32_t taddr, uint32_t (&r)[16])
 // 8 consecutive columns, no wait: the caller reads r only after
 // tmem_wait_ld8(r), whose operands tie the wait to these registers.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  __syncwarp();
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];" : MIPS_R8(r, 0) : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld8(uint32_t (&r)[8]) {
@@ -266,6 +273,8 @@ struct TcSel {
   int cap;
   int32_t* cand_pos;  // this thread's candidate sub-list
   float* cand_ub;
+  int64_t n_items;    // positions emitted must lie in [0, n_items)
+  int* err;
   float* qbase;       // the per-thread arrays above
   int slot, pslot;    // this thread's column and its partner's (the other half of the same user)
   unsigned* tau_glob;  // this user's shared threshold (item-chunked scan) or null
@@ -370,8 +379,13 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
     }
   }
   if (H >= s.tau_eff) {
+    const int32_t ip = MX ? pos[col] : pos0 + col;
+    if (ip < 0 || ip >= c.n_items) {  // never for consistent lists: flag it rather than emit it
+      atomicOr(c.err, DEV_ERR_INTERNAL);
+      return;
+    }
     if (s.n_cand < c.cap) {
-      c.cand_pos[s.n_cand] = MX ? pos[col] : pos0 + col;
+      c.cand_pos[s.n_cand] = ip;
       c.cand_ub[s.n_cand] = H;
     }
     ++s.n_cand;
@@ -679,9 +693,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           tma_load_2d(a_tiles + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full);
         ++na;
         for (int j = wk.tb; j < wk.te && ok; ++j) {
-          // the tile's bound columns (and list positions) into aux slot at % kAuxSlots
+          // the tile's bound columns (and list positions) into aux slot at % kAuxSlots,
+          // once the select warps are done with the slot's last tile AND that
+          // tile's copy has landed: the select warps wait for a copy only when
+          // they read it, so nothing else orders it before this one (re-arming
+          // the barrier while its previous phase still waits for bytes would
+          // be an arrival too many, and the two copies would overlap)
           const int as = (int)(at % kAuxSlots);
-          if (at >= kAuxSlots) ok = mbar_wait(&ctl->aux_empty[as], (uint32_t)((at / kAuxSlots - 1) & 1), abort_flag, err);
+          if (at >= kAuxSlots) {
+            const uint32_t prev = (uint32_t)((at / kAuxSlots - 1) & 1);
+            ok = mbar_wait(&ctl->aux_empty[as], prev, abort_flag, err) &&
+                 mbar_wait(&ctl->aux_full[as], prev, abort_flag, err);
+          }
           if (!ok) break;
           const int64_t row0 = (int64_t)wk.b_row + (int64_t)j * kTileN;
           mbar_expect_tx(&ctl->aux_full[as], aux_tx);
@@ -797,6 +820,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     c.heap = heap_base + slot;
     c.K = p.K;
     c.cap = o.cap;
+    c.n_items = MX ? p.work.n_items_pos : p.n_items;
+    c.err = err;
     c.qbase = qh_base;
     c.slot = slot;
     c.pslot = (c2 ^ 1) * kTileM + row;

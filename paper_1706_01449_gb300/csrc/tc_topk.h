@@ -30,6 +30,7 @@ struct TcWork {
   const int* l_base;        // first sub-list of each work item (null: 0)
   int restore;
   int* next;                // zeroed work counter: CTAs claim items dynamically (null: round-robin)
+  int64_t n_items_pos;      // item positions in item_pos lie in [0, n_items_pos)
 };
 
 struct TcParams {

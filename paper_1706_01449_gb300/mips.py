@@ -74,7 +74,8 @@ class RequestInfo(ctypes.Structure):
     """mips_request_info: a served request's timestamps and the batch it ran in."""
     _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
                 ("batch", ctypes.c_int64), ("batch_users", ctypes.c_int64), ("batch_K", ctypes.c_int),
-                ("slot", ctypes.c_int)]
+                ("slot", ctypes.c_int), ("batch_bytes", ctypes.c_int64), ("batch_ws_bytes", ctypes.c_int64),
+                ("inflight_bytes", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):

@@ -2,10 +2,14 @@
 and K submitted at once are batched (several requests per batch, mixed K
 inside a batch, batches in flight on different stream slots at the same
 time), and every request's result is bit-identical to the same request
-run alone, and exact against the oracle."""
+run alone, and exact against the oracle (every request).  Memory
+admission: a batch's admitted bytes are exactly the workspace its call
+took plus its buffers, and with a budget the batches in flight never hold
+more than the budget."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1706_01449_gb300 import mips, synth
 from parity_util import check_against_oracle
 
@@ -39,8 +43,8 @@ def test_mixed_requests_alone_equals_in_the_mix(method):
         assert (gi == ai).all() and (gs == asc).all()
         assert info["batch_K"] >= K and info["batch_users"] >= U.shape[0]
         assert info["t_submit"] <= info["t_start"] <= info["t_done"]
-    for (U, K), (gi, gs, _) in list(zip(reqs, got))[:4]:
-        check_against_oracle(U, I, K, gi, gs)
+    for (U, K), (gi, gs, _) in zip(reqs, got):
+        check_against_oracle(U, I, K, gi, gs, ref=oracle.topk(U, I, K))
     infos = [g[2] for g in got]
     # several requests per batch, and mixed K inside one batch (5 and 10,
     # 50 and 100 share a K class)
@@ -76,4 +80,36 @@ def test_memory_budget_admission_and_errors():
     with pytest.raises(mips.MipsError):
         srv.wait(10 ** 9, timeout=0.01)
     srv.close()
+    index.close()
+
+
+def test_admission_bytes_are_the_calls_workspace_and_budget_holds():
+    f = 32
+    I = synth.gaussian_rows(20000, f, 13, synth.S_ITEMS, synth.S_ITEM_NORMS, (0.0, 0.5))
+    index = mips.build_index(torch.from_numpy(I).cuda(), dtype="bf16")
+    reqs = _requests(24, f, 9, max_users=400, ks=(1, 10, 100))
+
+    def run(**kw):
+        srv = mips.Server(index, slots=3, max_batch_users=512, **kw)
+        ids = [srv.submit(U, K) for U, K in reqs]
+        got = [srv.wait(i, timeout=120) for i in ids]
+        srv.close()
+        return got
+
+    free = run()
+    for (U, K), (gi, gs, info) in zip(reqs, free):
+        io = info["batch_users"] * (f * 4 + info["batch_K"] * 12)
+        # the admitted workspace is what the call laid out and took
+        assert info["batch_ws_bytes"] > 0 and info["batch_bytes"] == info["batch_ws_bytes"] + io
+        check_against_oracle(U, I, K, gi, gs, ref=oracle.topk(U, I, K))
+    biggest = max(g[2]["batch_bytes"] for g in free)
+    budget = int(biggest * 1.5)  # room for one batch, not always two
+    capped = run(mem_budget=budget)
+    # admission: a batch starts only if everything in flight fits the
+    # budget, or it runs alone
+    for g in capped:
+        assert g[2]["inflight_bytes"] <= max(budget, g[2]["batch_bytes"])
+        assert g[2]["batch_bytes"] == g[2]["batch_ws_bytes"] + g[2]["batch_users"] * (f * 4 + g[2]["batch_K"] * 12)
+    for (gi, gs, _), (fi, fs, _) in zip(capped, free):
+        assert (gi == fi).all() and (gs == fs).all()
     index.close()
