@@ -1,7 +1,7 @@
 """Benchmark: exact batch top-K MIPS throughput (users/sec) on GB300.
 
 Default workload: the KDD shape -- 1,000,000 clustered users x 624,961
-items, f = 51, K = 10 -- searched with Maximus (Sec. IV, Algorithm 1) with
+items, f = 51, K = 10 -- searched with Maximus (Sec. III, Algorithm 1) with
 its cluster count |C| and item block B picked by the library's autotuner.
 One step = one Maximus call over all users (user quantisation, k-means,
 theta_b + CBound, per-cluster lists, the two-pass tensor-core walk, the
@@ -10,7 +10,7 @@ with users and items already resident in HBM.  The step's value is the
 line's `value`.
 
 In the same run, on the same inputs, `legs` times the other forms the
-metric compares: the BF16 blocked multiply with fused select (Sec. III-B,
+metric compares: the BF16 blocked multiply with fused select (Sec. II-C,
 graph replays) and the plain FP32 CUDA-core blocked multiply (plain calls),
 each with its users/sec and its own roofline.  `e2e` is the default form
 through the host-buffer entry point (pinned host users in, host results
@@ -82,7 +82,7 @@ def parse(argv=None):
                    help="Maximus / selector: spherical k-means (unit-length centroids)")
     p.add_argument("--fit-frac", type=float, default=0.0,
                    help="Maximus / selector: fit the centroids once on this fraction of the users before the "
-                        "warm-up (Sec. IV-E dynamic users); timed steps then only assign users")
+                        "warm-up (Sec. III-E dynamic users); timed steps then only assign users")
     return p.parse_args(argv)
 
 

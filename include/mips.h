@@ -2,7 +2,7 @@
  * mips.h -- C ABI of libmips: exact batch top-K maximum inner product
  * search on one GB300 GPU (sm_103a).
  *
- * The operation (Sec. III-A, "Problem Statement: Batch Exact MIPS"): given
+ * The operation (Sec. II-B, "Problem Statement: Batch Exact MIPS"): given
  * user vectors U (|U| x f) and item vectors I (|I| x f), return for every
  * user u the K items i with the largest u^T i.
  *
@@ -67,12 +67,12 @@ typedef enum {
 
 typedef struct {
   int dtype;          /* mips_dtype of the candidate pass (default MIPS_BF16) */
-  int kmeans_iters;   /* Lloyd iterations for Maximus (Sec. IV-E: i = 3) */
+  int kmeans_iters;   /* Lloyd iterations for Maximus (Sec. III-D: i = 3) */
   int block_items;    /* Maximus item block B; 0 = library default */
-  double sample_frac; /* Optimus user sample fraction (Sec. V: 0.005) */
+  double sample_frac; /* Optimus user sample fraction (Sec. IV: 0.005) */
   int autotune;       /* reserved */
   uint64_t seed;      /* seed of the k-means initial centroids and samples */
-  int kmeans_spherical; /* 1: spherical k-means (Sec. IV-A): unit-length centroids, largest cosine */
+  int kmeans_spherical; /* 1: spherical k-means (Sec. III-A): unit-length centroids, largest cosine */
 } mips_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -81,7 +81,7 @@ void mips_default_options(mips_options* opt);
 /*
  * Build an index over n_items item vectors of dimension f
  * (items_dev: device FP32 [n_items][f]; read during the call only).
- * clusters = |C| for Maximus (Sec. IV-A; Algorithm 1 input "# clusters"),
+ * clusters = |C| for Maximus (Sec. III-A; Algorithm 1 input "# clusters"),
  * fixed here and used by mips_topk_maximus.  The index copies the items
  * (FP32 master + quantised copies + per-item bounds); the caller may free
  * items_dev once the stream has passed this call.
@@ -95,7 +95,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
                              const mips_options* opt, void* stream, mips_index_t* out);
 
 /*
- * Blocked matrix multiply with fused top-K selection (Sec. III-B, "BMM"):
+ * Blocked matrix multiply with fused top-K selection (Sec. II-C, "BMM"):
  * every user against every item, nothing pruned.
  * users_dev: device FP32 [n_users][f]; out_idx_dev: device int32
  * [n_users][K]; out_score_dev: device double [n_users][K].
@@ -105,7 +105,7 @@ mips_status mips_topk(mips_index_t idx, const float* users_dev, int64_t n_users,
                       int32_t* out_idx_dev, double* out_score_dev, void* stream);
 
 /*
- * The Maximus index (Sec. IV, Algorithm 1): cluster these users with
+ * The Maximus index (Sec. III, Algorithm 1): cluster these users with
  * k-means into the index's |C| clusters, compute theta_b per cluster and
  * the per-cluster item lists ordered by CBound (Eq. appx_bound), then walk
  * each cluster's list in blocks for all of its users, stopping when no
@@ -116,7 +116,7 @@ mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t 
                               int32_t* out_idx_dev, double* out_score_dev, void* stream);
 
 /*
- * Dynamic users (Sec. IV-E, "Practical Usage"): run k-means (the index's
+ * Dynamic users (Sec. III-E, "Practical Usage"): run k-means (the index's
  * kmeans_iters Lloyd iterations, initial centroids a seeded draw of users)
  * on these users (device FP32 [n_users][f], read during the call only) and
  * keep the min(|C|, n_users) centroids in the index.  Afterwards every
@@ -133,7 +133,7 @@ mips_status mips_topk_maximus(mips_index_t idx, const float* users_dev, int64_t 
  */
 mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t n_users, void* stream);
 
-/* Report of one Optimus decision (Sec. V, "Overhead of Optimizer"). */
+/* Report of one Optimus decision (Sec. IV, "Overhead of Optimizer"). */
 typedef struct {
   int choice;           /* 0 = blocked multiply, 1 = Maximus */
   double t_build;       /* C_I: seconds of Maximus construction on the sample */
@@ -145,7 +145,7 @@ typedef struct {
 } mips_select_report;
 
 /*
- * Optimus (Sec. V): time a random user sample on both paths, extrapolate
+ * Optimus (Sec. IV): time a random user sample on both paths, extrapolate
  * to all users, finish the remaining users with the faster one and reuse
  * the sample's results.  Full results land in out_idx_dev/out_score_dev.
  * This call synchronises the stream (it reads the sample's timings).
@@ -169,7 +169,7 @@ typedef struct {
 
 /*
  * Autotuner for Maximus: picks the cluster count |C| and the item block B
- * (Sec. IV-A, IV-D) for these users by timing Maximus on a seeded user
+ * (Sec. III-A, III-D) for these users by timing Maximus on a seeded user
  * sample (n_users / 8 users, at least two waves of 128-user tiles per SM)
  * for |C| in {16, ..., 1024} (at most n_users / 32) and B in {1024, 4096,
  * 16384}.  The sample runs with |C| scaled by sample / n_users, so that it
@@ -215,7 +215,7 @@ mips_status mips_topk_graph(mips_index_t idx, const float* users_dev, int64_t n_
  * scatters each batch's results to its requests' host buffers.  Results
  * are those of mips_topk / mips_topk_maximus on the request alone
  * (exact, so independent of the batch).  No counterpart in the paper,
- * which scores offline batches (Sec. III-B); this is the serving form of
+ * which scores offline batches (Sec. II-C); this is the serving form of
  * its user batching.
  */
 typedef struct mips_server_s* mips_server_t;

@@ -6,7 +6,7 @@ arithmetic lives in ``mips_oracle.c`` (plain C, FP64, OpenMP over users);
 this module builds it with gcc on first use and wraps it with ctypes.
 
 Functions and the passages they follow:
-  * ``topk``       -- the problem (Sec. III-A) by brute force (Sec. III-B):
+  * ``topk``       -- the problem (Sec. II-B) by brute force (Sec. II-C):
                       sequential FP64 dots, full sort per user, ties to the
                       smaller item index.
   * ``dot``        -- one FP64 inner product u^T i.

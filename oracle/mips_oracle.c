@@ -8,11 +8,11 @@
  *
  * Everything here is the plain definition, written for a reader to check
  * against the paper by eye:
- *   - the problem (Sec. III-A "Problem Statement: Batch Exact MIPS"): for
+ *   - the problem (Sec. II-B "Problem Statement: Batch Exact MIPS"): for
  *     every user u, the K items i maximising u^T i;
- *   - brute force (Sec. III-B): one inner product per (u, i) pair, then a
+ *   - brute force (Sec. II-C): one inner product per (u, i) pair, then a
  *     selection of the K best;
- *   - the Maximus index (Sec. IV, Algorithm 1): k-means user clusters,
+ *   - the Maximus index (Sec. III, Algorithm 1): k-means user clusters,
  *     theta_b = max angle between a cluster's users and its centroid, the
  *     CBound of Eq. (appx_bound), per-cluster lists sorted by CBound, and
  *     QueryIndex's walk that stops once the bound falls below the K-th
@@ -73,7 +73,7 @@ static int cmp_rank(const void* pa, const void* pb) {
   return 0;
 }
 
-/* u^T i: sequential double sum over k = 0..f-1 (Sec. III-A). */
+/* u^T i: sequential double sum over k = 0..f-1 (Sec. II-B). */
 double oracle_dot(const float* u, const float* i, int f) {
   double s = 0.0;
   for (int k = 0; k < f; ++k) s += (double)u[k] * (double)i[k];
@@ -105,7 +105,7 @@ static int set_threads(int nthreads) {
 }
 
 /*
- * Brute force (Sec. III-B): score every item, sort all of them by the
+ * Brute force (Sec. II-C): score every item, sort all of them by the
  * ranking rule, keep the first K.  Outputs are row-major [n_users][K].
  * Returns the number of threads used.
  */
@@ -134,7 +134,7 @@ int oracle_topk(const float* U, int64_t n_users, const float* I, int64_t n_items
 }
 
 /* ---------------------------------------------------------------------
- * k-means (Sec. IV-A "Clustering Users"; Algorithm 1, ConstructIndex).
+ * k-means (Sec. III-A "Clustering Users"; Algorithm 1, ConstructIndex).
  * ------------------------------------------------------------------- */
 static double sqdist_fd(const float* u, const double* c, int f) {
   double s = 0.0;

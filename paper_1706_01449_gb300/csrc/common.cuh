@@ -1,7 +1,7 @@
 // Device helpers shared by the fused score+select kernels and the rescore.
 //
 // Per-user select state (the on-chip replacement for the per-user min-heap
-// of the paper's BMM, Sec. III-B): each user is owned by one thread, which
+// of the paper's BMM, Sec. II-C): each user is owned by one thread, which
 // keeps
 //   * tau   -- the K-th largest LOWER bound on u^T i seen so far (register);
 //   * a min-heap of those K lower bounds in shared memory (column layout:

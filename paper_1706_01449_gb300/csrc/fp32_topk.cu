@@ -1,5 +1,5 @@
 // Fused FP32 blocked multiply + top-K candidate select on CUDA cores
-// (Sec. III-B "Blocked Matrix Multiply", the paper's BMM: every user against
+// (Sec. II-C "Blocked Matrix Multiply", the paper's BMM: every user against
 // every item, here with the per-user selection fused so the |U| x |I| score
 // matrix never leaves the chip).
 //

@@ -1,4 +1,4 @@
-// Maximus (Sec. IV, Algorithm 1) on the GPU: k-means user clusters,
+// Maximus (Sec. III, Algorithm 1) on the GPU: k-means user clusters,
 // theta_b per cluster, CBound (Eq. appx_bound) for every (cluster, item),
 // per-cluster item lists sorted by CBound, users grouped by cluster, and a
 // grouped walk of each cluster's list that stops once no remaining item can
@@ -185,7 +185,7 @@ __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ sums
   cent[t] = (float)(s * (double)scale[1] / (double)n);
 }
 
-// Spherical k-means (Sec. IV-A: the clustering that minimises the user-
+// Spherical k-means (Sec. III-A: the clustering that minimises the user-
 // centroid angles; the paper itself runs plain k-means as the faster one):
 // centroids scaled to unit length after the draw and after every update, so
 // the assignment step picks the largest cosine (||c_j||^2 / 2 is the same for
@@ -914,7 +914,7 @@ cudaError_t launch_kmeans_assign(const float* users, int64_t n_users, int f, con
   return cudaSuccess;
 }
 
-// Dynamic users (Sec. IV-E, practical usage): a call's users are assigned to
+// Dynamic users (Sec. III-E, practical usage): a call's users are assigned to
 // centroids fitted earlier, and only the clusters that receive users are
 // kept.  used[j] marks cluster j.
 __global__ void cluster_used_kernel(const int32_t* __restrict__ assign, int64_t n, int* __restrict__ used) {

@@ -239,7 +239,7 @@ int tc_cap(int K, int64_t n, bool chunked) {
   return std::max(base, (int)std::min<int64_t>(grow, n + 64));
 }
 
-// Blocked multiply (Sec. III-B) over the index's items with fused select,
+// Blocked multiply (Sec. II-C) over the index's items with fused select,
 // then the exact rescore.
 // size_only: lay out the workspace, store the bytes it needs there and
 // return before any device work (no pointer argument is used).
@@ -382,7 +382,7 @@ void affine_sample(int64_t n, uint64_t seed, uint64_t* a_out, uint64_t* b_out) {
   *b_out = n > 0 ? mix(seed ^ 1ull) % (uint64_t)n : 0;
 }
 
-// Maximus (Sec. IV, Algorithm 1): k-means, theta_b + CBound, per-cluster
+// Maximus (Sec. III, Algorithm 1): k-means, theta_b + CBound, per-cluster
 // sort and user grouping, grouped walk, exact rescore.
 mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
                         double* out_score, cudaStream_t s, size_t* size_only = nullptr) {
@@ -484,7 +484,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   MIPS_CUDA(ws.ensure(ws.used, s));
 
   if (fitted) {
-    // dynamic users (Sec. IV-E): one assignment step to the fitted centroids
+    // dynamic users (Sec. III-E): one assignment step to the fitted centroids
     MIPS_CUDA(maximus_assign_fitted(users, n_users, f, idx->fit_cent, C_fit, ws.at<float>(o_fhn2),
                                     ws.at<int32_t>(o_assign), ws.at<int>(o_used), ws.at<int>(o_remap),
                                     ws.at<float>(o_cent), C, s, &idx->launches));
@@ -634,7 +634,7 @@ double elapsed_ms(cudaEvent_t a, cudaEvent_t b) {
   return t;
 }
 
-// Optimus (Sec. V): time a user sample on both paths, extrapolate, finish
+// Optimus (Sec. IV): time a user sample on both paths, extrapolate, finish
 // the other users with the faster one, reuse the sample's results.
 mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, int K, int32_t* out_idx,
                        double* out_score, cudaStream_t s, mips_select_report* rep) {

@@ -1,6 +1,6 @@
 // Input preparation: row-norm upper bounds, BF16 operand rows with bound
-// columns, row gathers.  The exact answer is Sec. III-A's top-K of u^T i per
-// user; the blocked multiply (Sec. III-B) scores in BF16 here, and the bound
+// columns, row gathers.  The exact answer is Sec. II-B's top-K of u^T i per
+// user; the blocked multiply (Sec. II-C) scores in BF16 here, and the bound
 // columns keep every true top-K item above the select's threshold.
 //
 // BF16 operand layout (K-major rows of fp = round_up(f + 2, 16) bf16):

@@ -1,5 +1,5 @@
 // Serving runtime: a request queue over one index with continuous batching
-// (mips_server_* in include/mips.h).  Host code only.  Sec. III-A notes that
+// (mips_server_* in include/mips.h).  Host code only.  Sec. II-B notes that
 // the index also serves a subset of users at a time, as in a model-serving
 // system that collects requests; each batch here is such a subset and gets
 // the same exact top-K as the batch problem.

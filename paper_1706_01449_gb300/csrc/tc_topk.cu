@@ -1,7 +1,7 @@
 // Fused BF16 blocked multiply + top-K candidate select on tcgen05 tensor
-// cores (the paper's BMM, Sec. III-B, with the per-user selection fused so
+// cores (the paper's BMM, Sec. II-C, with the per-user selection fused so
 // the |U| x |I| score matrix never leaves the SM), and the same machinery
-// walking Maximus's per-cluster item lists (Sec. IV, Algorithm 1).
+// walking Maximus's per-cluster item lists (Sec. III, Algorithm 1).
 //
 // Persistent kernel, one CTA per SM, 10 warps, user tiles of 128 rows and
 // item tiles of 256 rows (an M = 128, N = 256 MMA runs at the tensor pipe's

@@ -258,7 +258,7 @@ def topk_maximus(index: Index, users, K: int, out_idx=None, out_score=None, stre
 
 def fit_clusters(index: Index, users, stream=None):
     """mips_fit_clusters: k-means on these users; later Maximus calls on the
-    index assign their users to the fitted centroids (Sec. IV-E, dynamic
+    index assign their users to the fitted centroids (Sec. III-E, dynamic
     users).  users=None drops the fitted centroids.  Asynchronous."""
     lib = load()
     if users is None:

@@ -1,7 +1,7 @@
 """Multi-rank plumbing (one process per GPU).
 
 Users are independent and the index is read-only (the paper partitions
-users over index replicas, Sec. VI's multi-core runs), so the user matrix is
+users over index replicas, Sec. V's multi-core runs), so the user matrix is
 split into contiguous row ranges, one per rank; every rank holds the same
 items and computes the exact top-K of its own rows with no collective on the
 data path.  The only collectives are a barrier around a timed region, the

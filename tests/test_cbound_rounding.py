@@ -6,7 +6,7 @@ d / (sqrt(su) sqrt(sc)) - (2f + 8) 2^-23 with FMA-summed d, su, sc (a lower
 bound of the true smallest cosine).  CBound(i) = ||i|| g with
 g = cos(theta_ic - theta_b) from the angle-difference identity, computed
 from x = cos(theta_ic) + (2f + 8) 2^-23 and y = cos(theta_b) plus 2^-20 and
-a final outward factor (Eq. appx_bound; the upper-bound lemma of Sec. IV-B).
+a final outward factor (Eq. appx_bound; the upper-bound lemma of Sec. III-B).
 The lemma must hold as computed: u^T i <= ||u|| CBound(i) for every member
 u and every item i -- checked on members spread over a cone and items at,
 inside and outside its edge, aligned and opposite to the centroid."""

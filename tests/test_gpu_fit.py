@@ -1,4 +1,4 @@
-"""GPU checks of fitted centroids (mips_fit_clusters; Sec. IV-E, practical
+"""GPU checks of fitted centroids (mips_fit_clusters; Sec. III-E, practical
 usage: cluster an initial set of users once, then only assign later users
 to the extant centroids):
   * Maximus results stay equal to the brute-force oracle when k-means ran on

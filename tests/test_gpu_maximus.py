@@ -1,4 +1,4 @@
-"""GPU checks of the Maximus path (mips_topk_maximus, Sec. IV / Algorithm 1)
+"""GPU checks of the Maximus path (mips_topk_maximus, Sec. III / Algorithm 1)
 through the C ABI:
   * results equal the brute-force oracle and mips_topk (Theorem "exact");
   * the GPU's CBound values are upper bounds: ||u|| CBound >= u^T i for every
@@ -120,7 +120,7 @@ def test_kmeans_invariants():
 
 @pytest.mark.parametrize("dtype", ["fp32", "bf16"])
 def test_spherical_kmeans(dtype):
-    """kmeans_spherical (Sec. IV-A): exact results; every centroid is the unit
+    """kmeans_spherical (Sec. III-A): exact results; every centroid is the unit
     vector along its members' mean (of the last assignment step)."""
     U, I = clustered(2500, 900, 12, seed=8)
     K, C = 10, 12

@@ -1,7 +1,7 @@
-"""GPU checks of the Optimus selector (mips_select, Sec. V): the result equals
+"""GPU checks of the Optimus selector (mips_select, Sec. IV): the result equals
 the oracle whatever path it picks, the sample has the requested size (with
 the two-waves-per-SM floor), the report's estimates follow the overhead
-formula of Sec. V (C_I + n Q_I against n M_I) and the choice is the smaller
+formula of Sec. IV (C_I + n Q_I against n M_I) and the choice is the smaller
 estimate."""
 import math
 

@@ -1,7 +1,7 @@
 """Pins for the CPU oracle: checks against what the paper and mathematics
 fix, independent of the oracle's own code.
 
-* Brute force (Sec. III-A/B): exact rational arithmetic on tiny inputs,
+* Brute force (Sec. II-B/C): exact rational arithmetic on tiny inputs,
   integer closed forms, hand-worked fixture (tests/golden), one-hot and
   Cauchy-Schwarz cases, tie rule, zero user, power-of-two and positive
   scaling (ranking invariance noted under Eq. max), item permutation.
