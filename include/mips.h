@@ -369,6 +369,21 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
 mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const float* users_dev, int64_t n_users,
                               int f, int K, int32_t* out_idx_dev, double* out_score_dev, void* stream);
 
+/*
+ * Test hook of the bounded device waits (no counterpart in the paper; it
+ * exists for the library's own tests).  Every wait inside the tensor-core
+ * score kernel gives up after a limit, raises a timeout, lets the other
+ * roles drain their copies and MMAs, frees the tensor memory and exits, so
+ * the context stays usable.  After this call, the next blocked-multiply
+ * launch of that kernel in this process (a BF16 mips_topk call) publishes
+ * no work item: its MMA thread and select warps wait for one until wait_ns
+ * nanoseconds pass, and the call's mips_sync reports MIPS_ERR_TIMEOUT (the
+ * call's rescore then finds empty candidate lists).  One launch only;
+ * later launches are unaffected.  Errors: MIPS_ERR_ARG unless
+ * 1e5 <= wait_ns <= 1e9.
+ */
+mips_status mips_test_expire_next_wait(int64_t wait_ns);
+
 /* Release the index and everything it allocated.  NULL is a no-op. */
 void mips_free_index(mips_index_t idx);
 

@@ -2,6 +2,7 @@
 // index object, its workspace arena, and the dispatch of each call to its
 // kernels.  No C++ exception crosses the boundary.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -193,6 +194,9 @@ mips_status begin_call(mips_index_t idx, cudaStream_t s) {
   return MIPS_OK;
 }
 
+// Set by mips_test_expire_next_wait, taken by the next tensor-core launch.
+std::atomic<long long> g_test_expire_ns{0};
+
 // Start or end mark of one launch of the dominant kernel (the first four
 // marks of a call are kept).
 mips_status mark_kernel(mips_index_t idx, cudaStream_t s) {
@@ -347,6 +351,13 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
     }
     const int grid = (int)(n_work < idx->num_sms ? n_work : idx->num_sms);
     if (p.heap_global) p.heap_mem = idx->ws.at<float>(o_heap);
+    // counts start at 0: a launch that gives up on a bounded wait leaves
+    // unfinished lists, which the rescore then reads as empty
+    MIPS_CUDA(cudaMemsetAsync(so.n_cand, 0, sizeof(int) * nl, s));
+    if (const long long t = g_test_expire_ns.exchange(0)) {
+      p.wait_ns = (unsigned long long)t;
+      p.test_withhold = 1;
+    }
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_users, &map_users_tail, &map_items, &map_items_tail, p, so, uaux,
                                      idx->item_aux, idx->stats_dev,
@@ -590,6 +601,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     p.work = TcWork{m.w1, m.w1 + mw, m.w1 + 2 * mw, m.w1 + 3 * mw, m.n_work, m.row_user, m.pos_c, nullptr, 1, nullptr,
                     nI};
     const int grid = (int)(max_work < idx->num_sms ? max_work : idx->num_sms);
+    MIPS_CUDA(cudaMemsetAsync(so.n_cand, 0, sizeof(int) * nl, s));  // (as in run_bmm)
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(launch_tc_score_select(&map_a, &map_at, &map_b, &map_bt, p, so, ws.at<float2>(o_uaux), m.aux_c,
                                      idx->stats_dev,
@@ -818,6 +830,13 @@ cudaError_t mips::index_release_workspace(mips_index_t idx, cudaStream_t s) {
 extern "C" {
 
 int mips_version(void) { return 100; }
+
+mips_status mips_test_expire_next_wait(int64_t wait_ns) {
+  if (wait_ns < 100000 || wait_ns > 1000000000) return fail(MIPS_ERR_ARG, "wait_ns out of [1e5, 1e9]: %lld",
+                                                            (long long)wait_ns);
+  g_test_expire_ns.store(wait_ns);
+  return MIPS_OK;
+}
 
 const char* mips_last_error(void) { return g_err.c_str(); }
 

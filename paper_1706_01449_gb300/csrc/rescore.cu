@@ -296,13 +296,22 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // (B) thread per valid candidate: its compensated dot product
 // ---------------------------------------------------------------------------
+// (a position outside [0, n_items) is never written by the score kernels;
+// if one is read -- a score kernel that gave up on a bounded wait leaves its
+// lists unfinished -- it is flagged and skipped rather than dereferenced)
 __global__ void __launch_bounds__(256)
-    rescore_dot_kernel(const float* __restrict__ users, int f, const float* __restrict__ items, SelectOut o) {
+    rescore_dot_kernel(const float* __restrict__ users, int f, const float* __restrict__ items, int64_t n_items,
+                       SelectOut o, int* err) {
   const int count = *o.work_count;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
     const uint32_t slot = o.work[w];
     const int64_t u = (int64_t)(slot / (uint32_t)o.cap) / o.lists;
     const int32_t pos = o.cand_pos[slot];
+    if (pos < 0 || pos >= n_items) {
+      atomicOr(err, DEV_ERR_INTERNAL);
+      o.cand_sc[slot] = 0.0;
+      continue;
+    }
     o.cand_sc[slot] = score_dot2(users + u * f, items + (int64_t)pos * f, f);
   }
 }
@@ -313,7 +322,8 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(128)
     rescore_select_kernel(const float* __restrict__ users, int64_t n_users, int f,
                           const float* __restrict__ items, const int32_t* __restrict__ perm,
-                          const float* __restrict__ item_nrm, int K, SelectOut o, int32_t* __restrict__ out_idx,
+                          const float* __restrict__ item_nrm, int64_t n_items, int K, SelectOut o,
+                          int32_t* __restrict__ out_idx,
                           double* __restrict__ out_score, DevStats* stats, int* err) {
   extern __shared__ unsigned char smem_raw[];
   const int T = blockDim.x, t = threadIdx.x;
@@ -343,6 +353,10 @@ __global__ void __launch_bounds__(128)
           for (int c = 0; c < nl; ++c) {
             if (o.cand_ub[row + c] < tau) continue;
             const int32_t pos = o.cand_pos[row + c];
+            if (pos < 0 || pos >= n_items) {  // (as in the dot kernel)
+              atomicOr(err, DEV_ERR_INTERNAL);
+              continue;
+            }
             const double v =
                 mode == 0 ? o.cand_sc[row + c] : score_f64(ur, items + (int64_t)pos * f, f);
             nmax = fmaxf(nmax, item_nrm[pos]);
@@ -520,7 +534,7 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
   if (e != cudaSuccess) return e;
   rescore_collect_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, K, o, out_idx,
                                                                             out_score, stats);
-  rescore_dot_kernel<<<sm_count() * 8, 256, 0, s>>>(users, f, items_sorted, o);
+  rescore_dot_kernel<<<sm_count() * 8, 256, 0, s>>>(users, f, items_sorted, n_items, o, err);
   // threads per block so that the per-thread lists of K + 1 keys fit in 96 KiB
   int T = 128;
   while (T > 32 && (size_t)T * (K + 1) * 12 > 96 * 1024) T -= 32;
@@ -528,7 +542,7 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
   e = cudaFuncSetAttribute(rescore_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   rescore_select_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
-                                                                           item_nrm_ub, K, o, out_idx, out_score,
+                                                                           item_nrm_ub, n_items, K, o, out_idx, out_score,
                                                                            stats, err);
   rescore_warp_kernel<<<sm_count() * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,
                                                              o.ovf_list, o.ovf_count, out_idx, out_score, stats,

@@ -95,24 +95,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// What a bounded wait needs: the CTA's abort flag, the error word, and the
+// wait limit (1 s; shorter only when a test asks for it).
+struct Guard {
+  volatile int* abort_flag;
+  int* err;
+  unsigned long long wait_ns;
+};
+
 // Bounded wait for the phase with the given parity.  Returns false when the
 // CTA is aborting (this or another role timed out).
-__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, Guard gd) {
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitNs) {
-      *abort_flag = 1;
-      atomicOr(err, DEV_ERR_TIMEOUT);
+    if (*gd.abort_flag) return false;
+    if (globaltimer() - t0 > gd.wait_ns) {
+      *gd.abort_flag = 1;
+      atomicOr(gd.err, DEV_ERR_TIMEOUT);
       return false;
     }
   }
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const Guard& gd) {
   if (mbar_try_wait(bar, parity)) return true;
-  return mbar_wait_slow(bar, parity, abort_flag, err);
+  return mbar_wait_slow(bar, parity, gd);
 }
 
 // Wait (bounded) for a phase whose completion nothing else depends on any
@@ -615,7 +623,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   static_assert(kSeedListOfs == 2 * kQueue * kEpiThreads + 2 * kEpiThreads + 2 * kEpiThreads, "layout");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
-  volatile int* abort_flag = &ctl->abort_flag;
+  const Guard gd{&ctl->abort_flag, err, p.wait_ns > 0 ? p.wait_ns : kWaitNs};
   const int n_it = (int)((p.n_items + kTileN - 1) / kTileN);
   const int n_work = MX ? *p.work.n_work : (int)((p.n_users + kTileM - 1) / kTileM);
   constexpr uint32_t kTmemCols = 2 * kTileN;  // two accumulators
@@ -673,10 +681,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       bool ok = true;
       const bool dyn = MX && p.work.next;
       const uint32_t aux_tx = kAuxBytes + (MX ? kPosBytes : 0u);
+      // a test of the bounded waits: publish no work item at all, so that
+      // the MMA thread and the select warps wait for one until the limit
+      if (p.test_withhold) ok = false;
       for (int lt = 0; ok; ++lt) {
         // take and publish the next work item
         const int slot = lt % kWQ;
-        if (lt >= kWQ) ok = mbar_wait(&ctl->wq_empty[slot], (uint32_t)((lt / kWQ - 1) & 1), abort_flag, err);
+        if (lt >= kWQ) ok = mbar_wait(&ctl->wq_empty[slot], (uint32_t)((lt / kWQ - 1) & 1), gd);
         if (!ok) break;
         int wi = dyn ? atomicAdd(p.work.next, 1) : (int)blockIdx.x + lt * (int)gridDim.x;
         if (wi > n_work) wi = n_work;
@@ -684,7 +695,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         mbar_arrive(&ctl->wq_full[slot]);
         if (wi >= n_work) break;
         const WorkItem wk = get_work<MX>(p, wi, n_it);
-        if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, abort_flag, err);
+        if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, gd);
         if (!ok) break;
         mbar_expect_tx(&ctl->a_full, a_bytes);
         for (int c = 0; c < p.kc; ++c)
@@ -702,8 +713,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           const int as = (int)(at % kAuxSlots);
           if (at >= kAuxSlots) {
             const uint32_t prev = (uint32_t)((at / kAuxSlots - 1) & 1);
-            ok = mbar_wait(&ctl->aux_empty[as], prev, abort_flag, err) &&
-                 mbar_wait(&ctl->aux_full[as], prev, abort_flag, err);
+            ok = mbar_wait(&ctl->aux_empty[as], prev, gd) &&
+                 mbar_wait(&ctl->aux_full[as], prev, gd);
           }
           if (!ok) break;
           const int64_t row0 = (int64_t)wk.b_row + (int64_t)j * kTileN;
@@ -712,7 +723,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if constexpr (MX) bulk_load(pos_ring + (size_t)as * kTileN, p.work.item_pos + row0, kPosBytes, &ctl->aux_full[as]);
           ++at;
           for (int h = 0; h < bs; ++h, ++g) {  // g: loads issued so far
-            if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, abort_flag, err);
+            if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, gd);
             if (!ok) break;
             mbar_expect_tx(&ctl->b_full[st], b_bytes);
             unsigned char* dst = b_tiles + (size_t)st * b_bytes;
@@ -765,19 +776,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       bool ok = true;
       for (int lt = 0; ok; ++lt) {
         const int slot = lt % kWQ;
-        ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), abort_flag, err);
+        ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), gd);
         if (!ok) break;
         const int wi = *(volatile int*)&ctl->wq[slot];
         mbar_arrive(&ctl->wq_empty[slot]);
         if (wi >= n_work) break;
         const WorkItem wk = get_work<MX>(p, wi, n_it);
-        ok = mbar_wait(&ctl->a_full, lt & 1, abort_flag, err);
+        ok = mbar_wait(&ctl->a_full, lt & 1, gd);
         if (!ok) break;
         tc_fence_after();
         for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
           for (int h = 0; h < bs && ok; ++h) {
-            ok = mbar_wait(&ctl->b_full[st], ph, abort_flag, err);
-            if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, abort_flag, err);
+            ok = mbar_wait(&ctl->b_full[st], ph, gd);
+            if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, gd);
             if (!ok) break;
             tc_fence_after();
             // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
@@ -831,7 +842,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     unsigned long long emitted = 0, slow = 0;
     for (int lt = 0; ok; ++lt) {  // work items of this CTA
       const int wslot = lt % kWQ;
-      ok = __all_sync(kFull, mbar_wait(&ctl->wq_full[wslot], (uint32_t)((lt / kWQ) & 1), abort_flag, err));
+      ok = __all_sync(kFull, mbar_wait(&ctl->wq_full[wslot], (uint32_t)((lt / kWQ) & 1), gd));
       const int wi = ok ? *(volatile int*)&ctl->wq[wslot] : n_work;
       __syncwarp();
       if (lane == 0) mbar_arrive(&ctl->wq_empty[wslot]);
@@ -877,7 +888,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       for (int j = wk.tb; j < wk.te; ++j, ++g) {
         const int b = (int)(g & 1);
         // lanes leave together: TMEM loads are warp-collective
-        ok = __all_sync(kFull, mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), abort_flag, err));
+        ok = __all_sync(kFull, mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), gd));
         if (!ok) break;
         tc_fence_after();
         const int as = (int)(g % kAuxSlots);
@@ -897,7 +908,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
         if (first) {
-          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, abort_flag, err));
+          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
           if (!ok) break;
           aux_ready = true;
           seed_tile(s, c, taddr, valid, aux, active);
@@ -920,7 +931,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         if (halves) {
           slow += __popc(halves);
           if (!aux_ready) {
-            ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, abort_flag, err));
+            ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
             if (!ok) break;
           }
           select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves, first);

@@ -49,7 +49,9 @@ struct TcParams {
   int stages;     // item-tile ring depth
   float g;
   int mode;       // 0: blocked multiply, 1: work list
-  TcWork work;        // accumulation-error factor used by prep.cu for this fp
+  TcWork work;
+  unsigned long long wait_ns;  // limit of every bounded wait (0: 1 s)
+  int test_withhold;           // tests of the bounded waits: the producer publishes no work item
 };
 
 // Operand row length (BF16 elements) for dimension f: f + 2 bound columns,

@@ -29,7 +29,7 @@ EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_m
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
            "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph",
            "mips_autotune", "mips_server_create", "mips_server_submit", "mips_server_wait",
-           "mips_server_destroy", "mips_fit_clusters")
+           "mips_server_destroy", "mips_fit_clusters", "mips_test_expire_next_wait")
 
 
 class MipsError(RuntimeError):
@@ -146,6 +146,8 @@ def load():
     lib.mips_last_error.restype = ctypes.c_char_p
     lib.mips_topk_noalloc.argtypes = [P, i64, P, i64, i32, i32, P, P, P]
     lib.mips_topk_noalloc.restype = st
+    lib.mips_test_expire_next_wait.argtypes = [i64]
+    lib.mips_test_expire_next_wait.restype = st
     lib.mips_version.argtypes = []
     lib.mips_version.restype = i32
     _lib = lib
@@ -375,6 +377,13 @@ def topk_noalloc(items, users, K: int, out_idx, out_score, stream=None):
                                     ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
                                     _stream_ptr(stream)))
     return out_idx, out_score
+
+
+def test_expire_next_wait(wait_ns: int):
+    """Tests of the bounded device waits: the next tensor-core score launch
+    publishes no work item, so its waits run out after wait_ns ns and the
+    call's sync raises MIPS_ERR_TIMEOUT (one launch only)."""
+    _check(load().mips_test_expire_next_wait(int(wait_ns)))
 
 
 def free_index(index: Index):

@@ -97,3 +97,9 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(mips, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         mips.load()
+
+
+def test_wait_expiry_hook_checks_its_limit():
+    lib = mips.load()
+    assert lib.mips_test_expire_next_wait(10) == mips.MIPS_ERR_ARG
+    assert lib.mips_test_expire_next_wait(5_000_000_000) == mips.MIPS_ERR_ARG
