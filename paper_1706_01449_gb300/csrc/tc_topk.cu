@@ -160,14 +160,30 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo, uint3
          ((uint64_t)1 << 46) | ((uint64_t)layout << 61);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// One MMA; ACC (compile time): 0 overwrites the accumulator, 1 adds to it.
+template <int ACC>
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC)
       : "memory");
+}
+
+// K steps (K = 16 each) of one operand row, at most: two full 64-element
+// chunks and a 32-element tail (f = 128 needs 8 + 1).
+constexpr int kMaxSteps = 10;
+
+// The N MMAs of one item load, fully unrolled: a single thread issues them
+// back to back, so a loop, a branch or a computed predicate per MMA would
+// add issue time the tensor pipe waits for.  boff: the load's ring stage.
+template <int N>
+__device__ __forceinline__ void mma_steps(uint32_t d, const uint64_t (&a_d)[kMaxSteps],
+                                          const uint64_t (&b_d)[kMaxSteps], uint64_t boff, uint32_t idesc) {
+  mma_bf16<0>(d, a_d[0], b_d[0] + boff, idesc);
+#pragma unroll
+  for (int s = 1; s < N; ++s) mma_bf16<1>(d, a_d[s], b_d[s] + boff, idesc);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -751,6 +767,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
+      bool ok_init = true;
       // instruction descriptor: D = F32, A = B = BF16, both K-major, N, M
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(sub_rows >> 3) << 17) |
                              ((uint32_t)(kTileM >> 4) << 24);
@@ -768,12 +785,25 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       const int tsteps = p.tail_bytes / 32;
       const uint64_t a_tdesc = smem_desc(smem_u32(a_tiles + (size_t)p.kc * a_chunk), tsbo, p.tail_swizzle);
       const uint64_t b_tdesc0 = smem_desc(smem_u32(b_tiles + (size_t)p.kc * b_chunk), tsbo, p.tail_swizzle);
+      // the descriptors of every K step, once (B relative to ring stage 0)
+      const int nfull = p.kc * ksteps, nst = nfull + tsteps;
+      uint64_t a_d[kMaxSteps], b_d[kMaxSteps];
+#pragma unroll
+      for (int i = 0; i < kMaxSteps; ++i) {
+        const int c = i / ksteps, k = i - c * ksteps, tk = i - nfull;
+        a_d[i] = i < nfull ? a_desc0 + (uint64_t)(c * a16 + 2 * k) : a_tdesc + (uint64_t)(2 * tk);
+        b_d[i] = i < nfull ? b_desc0 + (uint64_t)(c * b16 + 2 * k) : b_tdesc0 + (uint64_t)(2 * tk);
+      }
+      if (nst < 1 || nst > kMaxSteps) {  // (tc_plan never makes such rows)
+        atomicOr(err, DEV_ERR_INTERNAL);
+        ok_init = false;
+      }
       long long g = 0;
       int st = 0;
       uint32_t ph = 0;   // ring pass parity
       int b = 0;         // accumulator of tile g
       uint32_t aph = 0;  // accumulator pass parity
-      bool ok = true;
+      bool ok = ok_init;
       for (int lt = 0; ok; ++lt) {
         const int slot = lt % kWQ;
         ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), gd);
@@ -793,16 +823,19 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             tc_fence_after();
             // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
             const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
-            const uint64_t bst = b_desc0 + (uint64_t)(st * stage16);
-            for (int c = 0; c < p.kc; ++c) {
-              const uint64_t ad = a_desc0 + (uint64_t)(c * a16);
-              const uint64_t bd = bst + (uint64_t)(c * b16);
-              for (int k = 0; k < ksteps; ++k)
-                mma_bf16(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (c | k) != 0);
+            const uint64_t boff = (uint64_t)(st * stage16);
+            switch (nst) {
+              case 1: mma_steps<1>(d, a_d, b_d, boff, idesc); break;
+              case 2: mma_steps<2>(d, a_d, b_d, boff, idesc); break;
+              case 3: mma_steps<3>(d, a_d, b_d, boff, idesc); break;
+              case 4: mma_steps<4>(d, a_d, b_d, boff, idesc); break;
+              case 5: mma_steps<5>(d, a_d, b_d, boff, idesc); break;
+              case 6: mma_steps<6>(d, a_d, b_d, boff, idesc); break;
+              case 7: mma_steps<7>(d, a_d, b_d, boff, idesc); break;
+              case 8: mma_steps<8>(d, a_d, b_d, boff, idesc); break;
+              case 9: mma_steps<9>(d, a_d, b_d, boff, idesc); break;
+              default: mma_steps<10>(d, a_d, b_d, boff, idesc); break;
             }
-            const uint64_t btd = b_tdesc0 + (uint64_t)(st * stage16);
-            for (int k = 0; k < tsteps; ++k)
-              mma_bf16(d, a_tdesc + (uint64_t)(2 * k), btd + (uint64_t)(2 * k), idesc, 1u);
             mma_commit(&ctl->b_empty[st]);
             if (++st == p.stages) {
               st = 0;
