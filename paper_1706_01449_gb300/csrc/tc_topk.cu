@@ -60,7 +60,7 @@ constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTileN = 256;    // items per tile (MMA N)
 constexpr int kTileM = 128;    // users per tile (MMA M)
 constexpr int kHalfN = 128;    // columns per epilogue thread and tile
-constexpr int kQueue = 16;     // hit-queue slots per thread
+constexpr int kQueue = 16;     // staging slots per thread: one 16-column group of scores
 constexpr int kAuxSlots = 4;   // item tiles whose bound columns / positions are staged at a time
 constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
 constexpr unsigned kFull = 0xffffffffu;
@@ -281,12 +281,11 @@ struct TcUser {
 
 // Per-thread arrays in shared memory, one column per select thread (slot
 // 0..255), laid out back to back from `qbase`:
-//   hit queue values [16][256] floats, hit queue columns [16][256] ints,
+//   staged scores of a hit group [16][256] floats,
 //   published thresholds [256] (64-bit: tag << 32 | float bits),
 //   seed-list tags [2][256] ints (work item whose first-tile list is
 //   published, -1: none), first-tile top-K lists [2][K][256] floats.
-constexpr int kQpOfs = kQueue * kEpiThreads;            // in 4-byte words from qbase
-constexpr int kTauOfs = 2 * kQueue * kEpiThreads;       // (8-byte aligned)
+constexpr int kTauOfs = kQueue * kEpiThreads;  // in 4-byte words from qbase (8-byte aligned)
 constexpr int kSeedTagOfs = kTauOfs + 2 * kEpiThreads;
 constexpr int kSeedListOfs = kSeedTagOfs + 2 * kEpiThreads;
 
@@ -304,7 +303,6 @@ struct TcSel {
   unsigned* tau_glob;  // this user's shared threshold (item-chunked scan) or null
   float g;            // accumulation-error factor of prep.cu
   __device__ __forceinline__ float* qh() const { return qbase + slot; }  // qh()[t * kEpiThreads]
-  __device__ __forceinline__ int32_t* qp() const { return (int32_t*)qbase + kQpOfs + slot; }
   __device__ __forceinline__ volatile unsigned long long* tau(int sl) const {
     return (volatile unsigned long long*)(qbase + kTauOfs) + sl;
   }
@@ -383,18 +381,23 @@ __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) 
   if (c.tau_glob) atomicMax(c.tau_glob, tau_ord(s.tau));  // every threshold is valid for the user
 }
 
-// One hit (H >= tau_eff when queued): threshold update from its lower bound,
+// One hit: column col of the tile, whose staged upper bound H reached the
+// threshold when it was staged.  Threshold update from its lower bound,
 // then the candidate emission.  Lower bounds at or below the current filter
 // threshold cannot raise it and are not kept.  With emit_only (second pass
 // over a work item's first item tile, whose lower bounds already went
 // through the top-K) only the emission is done, so no item is counted twice.
 // The item's position is pos0 + col, or pos[col] for a walk of a cluster's
-// sorted list (MX).
+// sorted list (MX).  The three loads (H, the item's bound columns, its
+// position) do not depend on one another and are issued first.
 template <int KR, bool MX>
-__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H, int col, const float2* aux,
+__device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, const float* Hp, int col, const float2* aux,
                                          int32_t pos0, const int32_t* pos, bool emit_only) {
-  if (H < s.tau_eff) return;  // the threshold rose since the hit was queued
-  const float L = emit_only ? kNegInf : tc_lower(s, c, H, aux[col]);
+  const float H = *Hp;
+  const float2 ia = aux[col];
+  const int32_t ip = MX ? pos[col] : pos0 + col;
+  if (H < s.tau_eff) return;  // the threshold rose since the hit was staged
+  const float L = emit_only ? kNegInf : tc_lower(s, c, H, ia);
   if (L > s.tau_eff) {
     s.tau = topk_insert(s, c, L);
     if (s.tau > s.tau_eff) {
@@ -403,7 +406,6 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
     }
   }
   if (H >= s.tau_eff) {
-    const int32_t ip = MX ? pos[col] : pos0 + col;
     if (ip < 0 || ip >= c.n_items) {  // never for consistent lists: flag it rather than emit it
       atomicOr(c.err, DEV_ERR_INTERNAL);
       return;
@@ -416,22 +418,49 @@ __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, float H,
   }
 }
 
-// Seed step for 8 columns col0.. of the first item tile: every lower bound
-// goes into the top-K (K = 1: the maximum; register top-K: the branch-free
-// network, so lanes never diverge; heap: only what passes its minimum).
+// Seed step of the heap-held top-K for 8 columns col0.. of the first item
+// tile: every lower bound that passes the heap's minimum goes in.
 template <int KR>
-__device__ __forceinline__ void seed8(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[8], int col0, int valid,
-                                      const float2* aux) {
+__device__ __forceinline__ void seed8_heap(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[8], int col0,
+                                           int valid, const float2* aux) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
     const float L = col0 + q < valid ? tc_lower(s, c, __uint_as_float(r[q]), aux[col0 + q]) : kNegInf;
-    if constexpr (KR == 1) {
-      s.d[0] = fmaxf(s.d[0], L);
-    } else if constexpr (KR > 1) {
-      topk_push(s, L);
-    } else {
-      if (L > s.tau) s.tau = heap_replace_min(c.heap, kEpiThreads, c.K, L);
-    }
+    if (L > s.tau) s.tau = heap_replace_min(c.heap, kEpiThreads, c.K, L);
+  }
+}
+
+// The two largest of 8 values (hi >= lo): pairwise maxima and minima, then
+// three merges of (max, second) pairs.
+__device__ __forceinline__ void top2_of8(const float (&x)[8], float& hi, float& lo) {
+  float a[4], b[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    a[p] = fmaxf(x[2 * p], x[2 * p + 1]);
+    b[p] = fminf(x[2 * p], x[2 * p + 1]);
+  }
+  const float h01 = fmaxf(a[0], a[1]), l01 = fmaxf(fminf(a[0], a[1]), fmaxf(b[0], b[1]));
+  const float h23 = fmaxf(a[2], a[3]), l23 = fmaxf(fminf(a[2], a[3]), fmaxf(b[2], b[3]));
+  hi = fmaxf(h01, h23);
+  lo = fmaxf(fminf(h01, h23), fmaxf(l01, l23));
+}
+
+// Register top-K seed step for 8 columns: each column's lower bound, then
+// the group's two largest go into the top-K (K = 1: its largest).
+template <int KR>
+__device__ __forceinline__ void seed8_reg(TcUser<KR>& s, const TcSel& c, const uint32_t (&r)[8], int col0,
+                                          int valid, const float2* aux) {
+  float L[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    L[q] = col0 + q < valid ? tc_lower(s, c, __uint_as_float(r[q]), aux[col0 + q]) : kNegInf;
+  float hi, lo;
+  top2_of8(L, hi, lo);
+  if constexpr (KR == 1) {
+    s.d[0] = fmaxf(s.d[0], hi);
+  } else {
+    topk_push(s, hi);
+    topk_push(s, lo);
   }
 }
 
@@ -439,6 +468,11 @@ __device__ __forceinline__ void seed8(TcUser<KR>& s, const TcSel& c, const uint3
 // norm: the index stores items by norm, descending), so that the threshold
 // starts the scan near its final value instead of at -inf; nothing is
 // emitted.  TMEM is read 8 columns at a time with the next 8 in flight.
+// Register top-K: only the two largest lower bounds of each 8-column group
+// are kept.  They belong to distinct items and the K-th largest of a subset
+// is at most the K-th largest of the whole, so the K-th kept value is a
+// valid threshold; it equals the tile's K-th largest lower bound unless some
+// group holds three of the K largest.  Heap: every lower bound.
 // Inactive lanes (padding rows) keep tau = +inf.
 template <int KR>
 __device__ __forceinline__ void seed_tile(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid,
@@ -449,10 +483,12 @@ __device__ __forceinline__ void seed_tile(TcUser<KR>& s, const TcSel& c, uint32_
 #pragma unroll 1
   for (int c8 = 0; c8 < kHalfN; c8 += 16) {
     tmem_ld8(taddr + c8 + 8, rb);
-    seed8(s, c, ra, c8, valid, aux);
+    if constexpr (KR > 0) seed8_reg(s, c, ra, c8, valid, aux);
+    else seed8_heap(s, c, ra, c8, valid, aux);
     tmem_wait_ld8(rb);
     if (c8 + 16 < kHalfN) tmem_ld8(taddr + c8 + 16, ra);
-    seed8(s, c, rb, c8 + 8, valid, aux);
+    if constexpr (KR > 0) seed8_reg(s, c, rb, c8 + 8, valid, aux);
+    else seed8_heap(s, c, rb, c8 + 8, valid, aux);
     if (c8 + 16 < kHalfN) tmem_wait_ld8(ra);
   }
   if constexpr (KR > 0) s.tau = active ? topk_kth(s, c.K) : __int_as_float(0x7f800000);
@@ -514,12 +550,15 @@ __device__ __forceinline__ bool seed_try_merge(TcUser<KR>& s, const TcSel& c, in
 
 // The 16-column groups of this thread's 128 columns whose 64-column half had
 // a hit somewhere in the warp (bit h of `halves`): each group is read again
-// with its maximum; lanes whose maximum reaches their threshold queue their
-// hits in shared memory and offer them in order through one offer site.
+// with its maximum; a lane whose maximum reaches its threshold stages the
+// group's 16 scores in shared memory (independent stores) and marks its hits
+// in a bit mask, then offers them in column order (the index of a hit is its
+// bit; no queue counter to wait on).
 template <int KR, bool MX>
 __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid,
                                             const float2* aux, int32_t pos0, const int32_t* pos, unsigned halves,
                                             bool emit_only) {
+  float* const stage = c.qh();
 #pragma unroll 1
   for (int gi = 0; gi < kHalfN / 16; ++gi) {
     if (!((halves >> (gi >> 2)) & 1u)) continue;  // warp-uniform
@@ -527,22 +566,23 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
     const float mg = tmem_ldmax16(taddr + 16 * gi, v);
     const bool hit = mg >= s.tau_eff;
     if (!__any_sync(kFull, hit)) continue;
-    int n = 0;
+    const int col0 = 16 * gi;
+    unsigned mask = 0;
     if (hit) {
       const float t = s.tau_eff;
-      const int col0 = 16 * gi;
+      const int nv = valid - col0;  // columns of the group below `valid`
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const float x = __uint_as_float(v[q]);
-        if (x >= t && col0 + q < valid) {
-          c.qh()[n * kEpiThreads] = x;
-          c.qp()[n * kEpiThreads] = col0 + q;
-          ++n;
-        }
+        stage[q * kEpiThreads] = x;
+        mask |= (x >= t && q < nv) ? (1u << q) : 0u;
       }
     }
-    for (int k = 0; k < n; ++k)
-      tc_offer<KR, MX>(s, c, c.qh()[k * kEpiThreads], c.qp()[k * kEpiThreads], aux, pos0, pos, emit_only);
+    while (mask) {
+      const int q = __ffs(mask) - 1;
+      mask &= mask - 1;
+      tc_offer<KR, MX>(s, c, stage + q * kEpiThreads, col0 + q, aux, pos0, pos, emit_only);
+    }
   }
 }
 
@@ -631,12 +671,11 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const bool heap_in_smem = KR == 0 && !p.heap_global;
   float* heap_base = heap_in_smem ? heap_smem : p.heap_mem + (size_t)blockIdx.x * p.K * kEpiThreads;
   float* qh_base = heap_smem + (heap_in_smem ? (size_t)p.K * kEpiThreads : 0);  // [16][256]
-  int32_t* qp_base = (int32_t*)(qh_base + (size_t)kQueue * kEpiThreads);     // [16][256]
-  unsigned long long* tau_sh = (unsigned long long*)(qp_base + (size_t)kQueue * kEpiThreads);  // [256]
+  unsigned long long* tau_sh = (unsigned long long*)(qh_base + (size_t)kQueue * kEpiThreads);  // [256]
   int* seed_sh = (int*)(tau_sh + kEpiThreads);                                                // [2][256]
   float* seed_lists = (float*)(seed_sh + 2 * kEpiThreads);  // [2][K][256] (KR > 0)
   Smem* ctl = (Smem*)(seed_lists + (KR > 0 ? (size_t)2 * p.K * kEpiThreads : 0));
-  static_assert(kSeedListOfs == 2 * kQueue * kEpiThreads + 2 * kEpiThreads + 2 * kEpiThreads, "layout");
+  static_assert(kSeedListOfs == kQueue * kEpiThreads + 2 * kEpiThreads + 2 * kEpiThreads, "layout");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   const Guard gd{&ctl->abort_flag, err, p.wait_ns > 0 ? p.wait_ns : kWaitNs};
@@ -1019,7 +1058,7 @@ size_t tc_smem_bytes(const TcParams& p) {
   const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
   const size_t b_bytes = (size_t)p.kc * b_chunk + sub_rows * p.tail_bytes;
   return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +
-         (sizeof(float2) + sizeof(int32_t)) * kAuxSlots * kTileN + 2 * sizeof(float) * kQueue * kEpiThreads +
+         (sizeof(float2) + sizeof(int32_t)) * kAuxSlots * kTileN + sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
          (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
 }
