@@ -325,7 +325,8 @@ mips_status mips_get_stats(mips_index_t idx, mips_stats* out);
  * (float [C][f]), "cos_b" (float [C], lower bound of cos theta_b),
  * "bound_sorted" (float [C][n_items], CBound upper bounds in list order),
  * "list" (int32 [C][n_items], sorted item positions in list order),
- * "visited" (int32 [n_users], items scored per user).  *dev_ptr and
+ * "visited" (int32 [n_users], items scored per user), and after
+ * mips_fit_clusters "fit_centroids" (float [C_fit][f]).  *dev_ptr and
  * *bytes describe the array; it stays valid until the next call on idx.
  */
 mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev_ptr,

@@ -126,16 +126,38 @@ cudaError_t radix_sort_pairs(uint32_t*& keys, int32_t*& vals, uint32_t*& keys_al
 cudaError_t make_float_desc_keys(const float* x, int64_t n, uint32_t* keys, int32_t* iota, int64_t seg_len,
                                  cudaStream_t s);
 
+// ---- tensor-core k-means assignment (kmeans_tc.cu) ------------------------
+// BF16 operand row length: f + 1 (the bias column) in whole 64-element chunks.
+int km_tc_row_len(int f);
+size_t km_tc_smem_bytes(int f, int C);
+// Whether C centroids of dimension f stay resident in max_smem bytes.
+bool km_tc_fits(int f, int C, int max_smem);
+// users_km [n_users][km_tc_row_len(f)] = [u, 1, 0 ..] in BF16.
+cudaError_t km_tc_users(const float* users, int64_t n_users, int f, uint16_t* users_km, cudaStream_t s);
+// One assignment step: cent_km [C][row len] is written from cent and hn2
+// (= ||c_j||^2 / 2), then assign[u] = argmax_j of the BF16 u . c_j - hn2_j.
+cudaError_t km_tc_assign(const uint16_t* users_km, int64_t n_users, int f, const float* cent, const float* hn2, int C,
+                         uint16_t* cent_km, int32_t* assign, int* err, int max_smem, cudaStream_t s);
+
+// Buffers of the tensor-core assignment; users_km null: the CUDA-core kernel.
+struct KmTc {
+  uint16_t* users_km = nullptr;  // [n_users][km_tc_row_len(f)]
+  uint16_t* cent_km = nullptr;   // [C][km_tc_row_len(f)]
+  int* err = nullptr;
+  int max_smem = 0;
+};
+
 // ---- Maximus (maximus.cu) -------------------------------------------------
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
-                           uint32_t* absmax, float* scale, bool spherical, cudaStream_t s, int* launches);
+                           uint32_t* absmax, float* scale, bool spherical, const KmTc& tc, cudaStream_t s,
+                           int* launches);
 // Assignment of the call's users to fitted centroids (cent_fit [C_fit][f]),
 // then the used clusters packed into slots 0.. of cent [C_eff][f] and the
 // assignment renumbered to those slots (C_eff >= the number of used clusters).
 cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, const float* cent_fit, int C_fit,
                                   float* hn2_fit, int32_t* assign, int* used, int* remap, float* cent, int C_eff,
-                                  cudaStream_t s, int* launches);
+                                  const KmTc& tc, cudaStream_t s, int* launches);
 cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int32_t* assign, const float* cent, int C,
                            const float* items, const float* item_nrm, int64_t n_items, uint32_t* cosb_ord,
                            uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches);

@@ -173,6 +173,61 @@ __global__ void kmeans_accum_smem_kernel(const float* __restrict__ users, int64_
     if (km_cnt[e]) atomicAdd(&counts[j0 + e], km_cnt[e]);
 }
 
+// The same sums with warp-private partial sums: warp w of the block owns
+// rows [C][f] (and counts [C]) of shared memory, lane l adds dimensions l,
+// l + 32, .. of each of the warp's users to its cluster's row with plain
+// adds (one lane per address, users in order), then the block sums its
+// warps' copies and adds each (cluster, dimension) to the global sums once.
+// Integer sums: the same result as kmeans_accum_kernel in any order.
+__global__ void kmeans_accum_warp_kernel(const float* __restrict__ users, int64_t n_users, int f,
+                                         const int32_t* __restrict__ assign, int C, const float* __restrict__ scale,
+                                         unsigned long long* __restrict__ sums, unsigned int* __restrict__ counts) {
+  extern __shared__ unsigned long long kw_acc[];  // [warps][C][f]
+  const int nwb = blockDim.x / 32;
+  const int64_t cf = (int64_t)C * f;
+  unsigned int* kw_cnt = (unsigned int*)(kw_acc + nwb * cf);  // [warps][C]
+  for (int64_t e = threadIdx.x; e < nwb * cf; e += blockDim.x) kw_acc[e] = 0ull;
+  for (int e = threadIdx.x; e < nwb * C; e += blockDim.x) kw_cnt[e] = 0u;
+  __syncthreads();
+  const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
+  unsigned long long* acc = kw_acc + w * cf;
+  unsigned int* cnt = kw_cnt + w * C;
+  const float sc = scale[0];
+  // each warp takes 8 consecutive users at a time: their cluster ids and
+  // row values are loaded before any add, so the loads overlap
+  constexpr int kU = 8;
+  const int64_t step = (int64_t)gridDim.x * nwb * kU;
+  for (int64_t u0 = ((int64_t)blockIdx.x * nwb + w) * kU; u0 < n_users; u0 += step) {
+    int j[kU];
+#pragma unroll
+    for (int r = 0; r < kU; ++r) j[r] = u0 + r < n_users ? assign[u0 + r] : -1;
+    for (int k = lane; k < f; k += 32) {
+      float x[kU];
+#pragma unroll
+      for (int r = 0; r < kU; ++r) x[r] = j[r] >= 0 ? users[(u0 + r) * f + k] : 0.f;
+#pragma unroll
+      for (int r = 0; r < kU; ++r)
+        if (j[r] >= 0) acc[(int64_t)j[r] * f + k] += (unsigned long long)__float2ll_rn(x[r] * sc);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < kU; ++r)
+        if (j[r] >= 0) cnt[j[r]] += 1u;
+    }
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < cf; e += blockDim.x) {
+    unsigned long long t = 0ull;
+    for (int ww = 0; ww < nwb; ++ww) t += kw_acc[ww * cf + e];
+    if (t) atomicAdd(&sums[e], t);
+  }
+  for (int e = threadIdx.x; e < C; e += blockDim.x) {
+    unsigned int t = 0u;
+    for (int ww = 0; ww < nwb; ++ww) t += kw_cnt[ww * C + e];
+    if (t) atomicAdd(&counts[e], t);
+  }
+}
+
 // Update step, part 2: mean of the members; an empty cluster keeps its centroid.
 __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ sums, const unsigned int* __restrict__ counts,
                                     int C, int f, const float* __restrict__ scale, float* __restrict__ cent) {
@@ -979,9 +1034,17 @@ __global__ void cluster_remap_kernel(int32_t* __restrict__ assign, int64_t n, co
 
 cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, const float* cent_fit, int C_fit,
                                   float* hn2_fit, int32_t* assign, int* used, int* remap, float* cent, int C_eff,
-                                  cudaStream_t s, int* launches) {
+                                  const KmTc& tc, cudaStream_t s, int* launches) {
   half_norm2_kernel<<<(C_fit + 127) / 128, 128, 0, s>>>(cent_fit, C_fit, f, hn2_fit);
-  cudaError_t e = launch_kmeans_assign(users, n_users, f, cent_fit, hn2_fit, C_fit, assign, s);
+  cudaError_t e;
+  if (tc.users_km) {
+    e = km_tc_users(users, n_users, f, tc.users_km, s);
+    if (e == cudaSuccess)
+      e = km_tc_assign(tc.users_km, n_users, f, cent_fit, hn2_fit, C_fit, tc.cent_km, assign, tc.err, tc.max_smem, s);
+    *launches += 3;
+  } else {
+    e = launch_kmeans_assign(users, n_users, f, cent_fit, hn2_fit, C_fit, assign, s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(used, 0, sizeof(int) * C_fit, s);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users + 255) / 256, (int64_t)sm_count() * 8));
@@ -994,7 +1057,8 @@ cudaError_t maximus_assign_fitted(const float* users, int64_t n_users, int f, co
 
 cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, int iters, const int64_t* init_ids_dev,
                            float* cent, float* hn2, int32_t* assign, unsigned long long* sums, unsigned int* counts,
-                           uint32_t* absmax, float* scale, bool spherical, cudaStream_t s, int* launches) {
+                           uint32_t* absmax, float* scale, bool spherical, const KmTc& tc, cudaStream_t s,
+                           int* launches) {
   gather_rows_i64<<<(unsigned)((C * f + 255) / 256), 256, 0, s>>>(users, init_ids_dev, C, f, cent);
   if (spherical) {
     normalize_rows_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f);
@@ -1006,14 +1070,39 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
   *launches += 2;
   kmeans_scale_kernel<<<1, 32, 0, s>>>(absmax, n_users, scale);
   *launches += 1;
+  if (tc.users_km) {  // the users' BF16 operand rows, once
+    e = km_tc_users(users, n_users, f, tc.users_km, s);
+    if (e != cudaSuccess) return e;
+    *launches += 1;
+  }
   for (int it = 0; it < iters; ++it) {
     half_norm2_kernel<<<(C + 127) / 128, 128, 0, s>>>(cent, C, f, hn2);
-    e = launch_kmeans_assign(users, n_users, f, cent, hn2, C, assign, s);
+    if (tc.users_km) {
+      e = km_tc_assign(tc.users_km, n_users, f, cent, hn2, C, tc.cent_km, assign, tc.err, tc.max_smem, s);
+      *launches += 1;
+    } else {
+      e = launch_kmeans_assign(users, n_users, f, cent, hn2, C, assign, s);
+    }
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * C * f, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned int) * C, s);
     if (e != cudaSuccess) return e;
-    if ((size_t)C * f * 8 + (size_t)C * 4 <= 96 * 1024) {
+    // warp-private partial sums of 8, 4 or 2 warps per block, when they fit
+    int max_smem = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t per_warp = (size_t)C * f * 8 + (size_t)C * 4;
+    int nwb = 8;
+    while (nwb >= 2 && (size_t)nwb * per_warp > (size_t)max_smem) nwb /= 2;
+    if (nwb >= 2) {
+      const size_t smem = (size_t)nwb * per_warp;
+      e = cudaFuncSetAttribute(kmeans_accum_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int per_sm = std::max<int>(1, (int)((size_t)max_smem / smem));
+      const unsigned bx = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>((n_users + 8 * nwb - 1) / (8 * nwb), (int64_t)sm_count() * std::min(per_sm, 4)));
+      kmeans_accum_warp_kernel<<<bx, nwb * 32, smem, s>>>(users, n_users, f, assign, C, scale, sums, counts);
+    } else if ((size_t)C * f * 8 + (size_t)C * 4 <= 96 * 1024) {
       // all partial sums fit one block's shared memory
       const size_t smem = (size_t)C * f * 8 + (size_t)C * 4;
       e = cudaFuncSetAttribute(kmeans_accum_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -427,6 +427,13 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int C_fit = fitted ? idx->fit_C : 0;
   size_t o_fhn2 = ws.take(sizeof(float) * C_fit), o_used = ws.take(sizeof(int) * C_fit),
          o_remap = ws.take(sizeof(int) * C_fit);
+  // k-means assignment on tcgen05 (BF16 operands) when every centroid stays
+  // resident in shared memory
+  const int C_km = fitted ? C_fit : C;
+  const bool km_tc = idx->opt.dtype == MIPS_BF16 && km_tc_fits(f, C_km, idx->max_smem);
+  const int fk = km_tc_row_len(f);
+  const size_t o_ukm = km_tc ? ws.take(sizeof(uint16_t) * n_users * fk) : 0;
+  const size_t o_ckm = km_tc ? ws.take(sizeof(uint16_t) * (size_t)C_km * fk) : 0;
   const int64_t n_rows_max = round_up(n_users, 128) + 128ll * C;  // A rows of the tensor-core walk
   const int64_t max_work = n_rows_max / 128;
   size_t tmp_bytes = radix_sort_temp_bytes(nI, C);
@@ -493,12 +500,19 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     return MIPS_OK;
   }
   MIPS_CUDA(ws.ensure(ws.used, s));
+  KmTc kt;
+  if (km_tc) {
+    kt.users_km = ws.at<uint16_t>(o_ukm);
+    kt.cent_km = ws.at<uint16_t>(o_ckm);
+    kt.err = idx->err_dev;
+    kt.max_smem = idx->max_smem;
+  }
 
   if (fitted) {
     // dynamic users (Sec. III-E): one assignment step to the fitted centroids
     MIPS_CUDA(maximus_assign_fitted(users, n_users, f, idx->fit_cent, C_fit, ws.at<float>(o_fhn2),
                                     ws.at<int32_t>(o_assign), ws.at<int>(o_used), ws.at<int>(o_remap),
-                                    ws.at<float>(o_cent), C, s, &idx->launches));
+                                    ws.at<float>(o_cent), C, kt, s, &idx->launches));
   } else {
     // k-means initial centroids: a seeded draw of C distinct users (on the
     // device, so that a captured call holds no host data)
@@ -507,7 +521,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     MIPS_CUDA(maximus_kmeans(users, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
                              ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
                              ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
-                             ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, s, &idx->launches));
+                             ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, kt, s, &idx->launches));
   }
   mips_status st;
   if ((st = end_stage(idx, ST_KMEANS, s)) != MIPS_OK) return st;
@@ -988,14 +1002,25 @@ mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t 
   size_t o_bits = ws.take(sizeof(uint32_t) * ((n_users + 31) / 32));
   size_t o_assign = ws.take(sizeof(int32_t) * n_users), o_sums = ws.take(sizeof(unsigned long long) * C * f);
   size_t o_cnt = ws.take(sizeof(unsigned) * C), o_amax = ws.take(16), o_scale = ws.take(16);
+  const bool km_tc = idx->opt.dtype == MIPS_BF16 && km_tc_fits(f, C, idx->max_smem);
+  const int fk = km_tc_row_len(f);
+  const size_t o_ukm = km_tc ? ws.take(sizeof(uint16_t) * n_users * fk) : 0;
+  const size_t o_ckm = km_tc ? ws.take(sizeof(uint16_t) * (size_t)C * fk) : 0;
   MIPS_CUDA(ws.ensure(ws.used, s));
+  KmTc kt;
+  if (km_tc) {
+    kt.users_km = ws.at<uint16_t>(o_ukm);
+    kt.cent_km = ws.at<uint16_t>(o_ckm);
+    kt.err = idx->err_dev;
+    kt.max_smem = idx->max_smem;
+  }
   idx->mx.C = 0;  // the workspace is reused: earlier Maximus views are gone
   MIPS_CUDA(draw_init_ids(n_users, C, idx->opt.seed, ws.at<uint32_t>(o_bits), ws.at<int64_t>(o_ids), s));
   idx->launches += 1;
   MIPS_CUDA(maximus_kmeans(users_dev, n_users, f, C, idx->opt.kmeans_iters, ws.at<int64_t>(o_ids),
                            ws.at<float>(o_cent), ws.at<float>(o_hn2), ws.at<int32_t>(o_assign),
                            ws.at<unsigned long long>(o_sums), ws.at<unsigned>(o_cnt), ws.at<uint32_t>(o_amax),
-                           ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, s, &idx->launches));
+                           ws.at<float>(o_scale), idx->opt.kmeans_spherical != 0, kt, s, &idx->launches));
   if (idx->fit_cap < (int64_t)C * f) {  // (every call on this index is ordered after idx->done)
     if (idx->has_done) MIPS_CUDA(cudaEventSynchronize(idx->done));
     if (idx->fit_cent) MIPS_CUDA(cudaFree(idx->fit_cent));
@@ -1380,6 +1405,9 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
   } else if (!strcmp(name, "item_nrm")) {
     *dev_ptr = idx->item_nrm;
     *bytes = sizeof(float) * idx->n_items;
+  } else if (idx->fit_C > 0 && !strcmp(name, "fit_centroids")) {
+    *dev_ptr = idx->fit_cent;
+    *bytes = sizeof(float) * (int64_t)idx->fit_C * idx->f;
   } else if (idx->mx.C > 0 && !strcmp(name, "assign")) {
     *dev_ptr = idx->mx.assign;
     *bytes = sizeof(int32_t) * idx->mx.n_users;
