@@ -58,7 +58,7 @@ def parse(argv=None):
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--dtype", default="auto", choices=["auto", "bf16", "fp32"])
+    p.add_argument("--dtype", default="auto", choices=["auto", "bf16", "fp8", "fp32"])
     p.add_argument("--method", default="maximus", choices=["bmm", "maximus", "select"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--f", type=int, default=0, help="dimension (Netflix shape: 10, 50 or 100; default 50; others: their own f)")
@@ -66,7 +66,7 @@ def parse(argv=None):
     p.add_argument("--clusters", type=int, default=64, help="|C| when the autotuner is off")
     p.add_argument("--no-autotune", action="store_true",
                    help="Maximus / selector: keep --clusters and the default block instead of mips_autotune")
-    p.add_argument("--legs", default="bmm,fp32",
+    p.add_argument("--legs", default="bmm,fp32,fp8",
                    help="extra forms timed after the main steps on the same inputs: comma list of bmm (BF16 "
                         "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply); 'none' for none")
     p.add_argument("--leg-steps", type=int, default=3)
@@ -177,8 +177,9 @@ def traffic_for(kernel_key, src_hash):
 def roofline(dtype, f, scores, kernel_ms, hbm_bytes, peaks, peak_src, sm_count, clock_mhz, kernel_key, src_files):
     """The kernel's roofline: the slowest of three ceilings over its device time.
 
-    * tensor (BF16: 2 f FLOP per score at the measured BF16 burst peak) or,
-      for the FP32 CUDA-core form, FP32 FMA (SMs x 128 FMA/clk x 2 x clock);
+    * tensor (BF16: 2 f FLOP per score at the measured BF16 burst peak;
+      FP8 E4M3: at twice it, the nominal FP8 / BF16 ratio) or, for the FP32
+      CUDA-core form, FP32 FMA (SMs x 128 FMA/clk x 2 x clock);
     * HBM: the algorithmic bytes at the measured copy bandwidth;
     * select issue: one warp instruction slot per 32 scores on every SM
       sub-partition (SMs x 4 x 32 scores/clk), the algorithmic minimum of
@@ -193,6 +194,10 @@ def roofline(dtype, f, scores, kernel_ms, hbm_bytes, peaks, peak_src, sm_count, 
         pk = peaks["bf16_tflops"]
         ceil["tensor"] = {"time_ms": flops / (pk * 1e12) * 1e3, "achieved": flops / s / 1e12, "peak": pk,
                           "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 burst"}
+    elif dtype == "fp8":  # the measured BF16 burst x the nominal FP8 / BF16 ratio (4.5 / 2.25)
+        pk = 2.0 * peaks["bf16_tflops"]
+        ceil["tensor"] = {"time_ms": flops / (pk * 1e12) * 1e3, "achieved": flops / s / 1e12, "peak": pk,
+                          "unit": "TFLOP/s", "peak_source": f"{peak_src} bf16 burst x 2 (nominal fp8 ratio)"}
     else:
         pk = sm_count * 128 * 2 * clk / 1e12
         ceil["alu_fp32_fma"] = {"time_ms": flops / (pk * 1e12) * 1e3, "achieved": flops / s / 1e12, "peak": pk,
@@ -390,10 +395,10 @@ def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk,
     (the pairs it scored).  Algorithmic bytes: user rows and item rows once
     in the operand dtype, candidate lists out (8 bytes each)."""
     scores = stats["pairs_scored"] if walked else nU * nI
-    b = 2 if dtype == "bf16" else 4
+    b = {"bf16": 2, "fp8": 1}.get(dtype, 4)
     hbm = nU * f * b + nI * f * b + 8 * stats["cand_emitted"]
     kms = stats["ms_kernel"] or (stats["ms_walk"] if walked else stats["ms_score"])
-    kern = "tc_score_select" if dtype == "bf16" else ("fp32_score_select" if not walked else "maximus_walk")
+    kern = "tc_score_select" if dtype in ("bf16", "fp8") else ("fp32_score_select" if not walked else "maximus_walk")
     key = f"{kern}{' walk' if walked else ''} {dtype} {workload} f={f} K={K}"
     src = ["tc_topk.cu"] if dtype == "bf16" else ["fp32_topk.cu" if not walked else "maximus.cu"]
     return roofline(dtype, f, scores, kms, hbm, peaks, peak_src, sm, clk, key, src)
@@ -561,17 +566,21 @@ def main(argv=None):
     for leg in leg_names:
         if leg == args.method and dtype == "bf16":
             continue
-        if leg not in ("bmm", "maximus", "fp32"):
+        if leg not in ("bmm", "maximus", "fp32", "fp8"):
             raise SystemExit(f"unknown leg {leg}")
         oi = torch.empty_like(out_idx)
         osc = torch.empty_like(out_sc)
         if leg == "fp32":
             idx_l = mips.build_index(I_d, clusters=args.clusters, dtype="fp32")
             l_method, l_dtype, l_graph, n_warm = "bmm", "fp32", False, 1
+        elif leg == "fp8":  # the main method on an FP8 E4M3 index of the same items
+            idx_l = mips.build_index(I_d, clusters=args.clusters, dtype="fp8")
+            l_method = "maximus" if args.method == "select" else args.method
+            l_dtype, l_graph, n_warm = "fp8", use_graph, 2
         else:
             idx_l = index
             l_method, l_dtype, l_graph, n_warm = leg, dtype, use_graph, 2
-        if leg == "maximus" and not args.no_autotune:
+        if l_method == "maximus" and leg != "fp32" and not args.no_autotune:
             mips.autotune(idx_l, U_d, K, stream=stream)
         lstep = make_step(idx_l, l_method, oi, osc, l_graph)
         lms, lkms, _, lst = timed_steps(lstep, n_warm, args.leg_steps, stream, flush, idx_l, mips)
@@ -580,7 +589,9 @@ def main(argv=None):
         l_walk = l_method == "maximus"
         lrl = score_roofline(l_dtype, l_walk, f, nU, nI, K, lst, peaks, peak_src, sm, clk, args.workload)
         legs[leg] = {"value": nU / (statistics.mean(lms) / 1e3), "unit": "users/s", "ms_per_step": statistics.mean(lms),
-                     "steps": args.leg_steps, "warmup": n_warm, "candidate_pass": l_dtype,
+                     "steps": args.leg_steps, "warmup": n_warm, "candidate_pass": l_dtype, "method": l_method,
+                     "candidates_per_user": lst.get("cand_emitted", 0) / nU, "rescored_per_user":
+                         lst.get("cand_rescored", 0) / nU, "users_overflow": lst.get("users_overflow", 0),
                      "launch": "cuda graph replay" if l_graph else "plain calls",
                      "same_result_as_main": bool(torch.equal(oi, out_idx) and torch.equal(osc, out_sc)),
                      "stages_ms_last_step": {k: lst[k] for k in ("ms_prep", "ms_score", "ms_rescore", "ms_kmeans",
@@ -601,7 +612,7 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": value, "unit": "users/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if dtype == "bf16" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"bf16": "bf16", "fp8": "fp8_e4m3"}.get(dtype, "f32"),
         "data": "synthetic",
         "config": {"workload": f"{args.workload} f={f} K={K}" + (f" first {nU} users" if args.users else ""),
                    "n_users": nU, "n_items": nI, "f": f, "K": K,

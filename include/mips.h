@@ -62,7 +62,9 @@ typedef enum {
 typedef enum {
   MIPS_FP32 = 0,     /* FP32 CUDA-core dot products */
   MIPS_BF16 = 1,     /* BF16 operands on tcgen05 tensor cores, FP32 accumulate */
-  MIPS_FP8_E4M3 = 2  /* reserved */
+  MIPS_FP8_E4M3 = 2  /* FP8 E4M3 operands on tcgen05 (kind::f8f6f4), FP32 accumulate: users scaled
+                      * per row, items by one scale, bound columns rounded up (the same exact
+                      * top-K, a looser candidate filter than BF16) */
 } mips_dtype;
 
 typedef struct {
@@ -87,8 +89,7 @@ void mips_default_options(mips_options* opt);
  * items_dev once the stream has passed this call.
  * Limits: 1 <= f <= 128, 1 <= n_items < 2^31, 1 <= clusters <= 4096;
  * options: 0 <= kmeans_iters <= 100, block_items >= 0, 0 < sample_frac <= 1,
- * kmeans_spherical 0 or 1 (else MIPS_ERR_ARG); dtype MIPS_FP32 or MIPS_BF16
- * (MIPS_FP8_E4M3: MIPS_ERR_UNIMPLEMENTED).
+ * kmeans_spherical 0 or 1, dtype one of mips_dtype (else MIPS_ERR_ARG).
  * *out receives the handle; free it with mips_free_index.
  */
 mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int clusters,

@@ -56,6 +56,11 @@ void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* er
 // role 0 = users (A operand), role 1 = items (B operand).
 void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void* out_bf16,
                        int64_t n_rows_out, float2* aux, int* err, cudaStream_t s);
+// E4M3 operand rows (prep.cu): role 0 users (row_scale[row] = their scale),
+// role 1 items (scale *item_scale, from launch_fp8_item_scale).
+void launch_quant_fp8(const float* x, int64_t n, int f, int fp, int role, const float* item_scale, void* out,
+                      int64_t n_rows_out, float2* aux, float* row_scale, int* err, cudaStream_t s);
+void launch_fp8_item_scale(const float* item_nrm, int64_t n, float* item_scale, cudaStream_t s);
 // dst rows[r] <- src row r, for [n][K] top-K outputs.
 void launch_scatter_topk(const int32_t* src_idx, const double* src_sc, const int32_t* rows, int64_t n, int K,
                          int32_t* dst_idx, double* dst_sc, cudaStream_t s);
@@ -176,6 +181,7 @@ cudaError_t maximus_keys_to_bounds(const uint32_t* keys, int64_t n, float* out, 
 // bound order, n_pad rows per cluster.
 struct MxTc {
   int C = 0, fp = 0, t1 = 0, n_it = 0;
+  int esize = 2;  // bytes per operand element (2: BF16, 1: FP8)
   int64_t n_users = 0, n_items = 0, n_pad = 0, n_rows_max = 0, max_work = 0;
   const int* counts = nullptr;       // [C] users per cluster
   const int* offsets = nullptr;      // [C + 1] first sorted rank of each cluster

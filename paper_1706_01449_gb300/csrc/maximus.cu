@@ -844,7 +844,7 @@ cudaError_t mx_tc_prepare(MxTc& m, const int32_t* user_perm, const void* items_b
   m.items_bf16 = items_bf16;
   m.item_aux = item_aux;
   m.lists = lists;
-  const int words = m.fp * 2 / 16;
+  const int words = m.fp * m.esize / 16;
   mx_pad_layout_kernel<<<1, 32, 0, s>>>(m.counts, m.C, m.pad_off);
   cudaError_t e = cudaMemsetAsync(m.row_user, 0xff, sizeof(int32_t) * m.n_rows_max, s);
   if (e != cudaSuccess) return e;
@@ -879,7 +879,7 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   // the rest of each cluster's list that some member still needs
   const dim3 cgrid(copy_blocks(m.C), (unsigned)m.C);
   mx_items_by_cluster_kernel<<<cgrid, 256, 0, s>>>((const uint4*)m.items_bf16, m.item_aux, m.lists, m.n_items, m.n_pad,
-                                                   m.fp / 8, m.t1, 0, m.cl_end, (uint4*)m.b_rows, m.aux_c, m.pos_c);
+                                                   (m.fp * m.esize / 16), m.t1, 0, m.cl_end, (uint4*)m.b_rows, m.aux_c, m.pos_c);
   *launches += 2;
   // regroup: the users of each cluster in order of the item tiles they
   // need, so that each A tile's walk is close to its users' own need
@@ -891,8 +891,8 @@ cudaError_t mx_tc_pass2(MxTc& m, const int32_t* assign, const float2* user_aux, 
   if (e != cudaSuccess) return e;
   *user_perm = v0;
   mx_row_map_kernel<<<ub, 256, 0, s>>>(v0, nU, m.offsets, m.pad_off, m.C, m.row_user, m.user_row);
-  mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * (m.fp / 8) + 255) / 256), 256, 0, s>>>(
-      (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, m.fp / 8, (uint4*)m.a_rows);
+  mx_gather_bf16_kernel<<<(unsigned)((m.n_rows_max * ((m.fp * m.esize / 16)) + 255) / 256), 256, 0, s>>>(
+      (const uint4*)m.users_bf16, m.row_user, m.n_rows_max, (m.fp * m.esize / 16), (uint4*)m.a_rows);
   mx_tile_end_kernel<<<ub, 256, 0, s>>>(m.ustop, m.user_row, nU, m.work_end);
   mx_work2_keys_kernel<<<wb, 256, 0, s>>>(m.n_work, m.work_end, m.w1 + mw, m.n_pad, mw, m.t1, m.n_it, tile_bits,
                                           m.wkeys[0], m.wvals[0], m.n_work + 1, stats);

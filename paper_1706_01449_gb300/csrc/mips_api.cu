@@ -102,8 +102,10 @@ struct mips_index_s {
   float* item_nrm = nullptr;   // upper bounds of ||i|| [n_items]
   // BF16 operand rows with bound columns
   int fp = 0;
-  void* items_bf16 = nullptr;  // [n_items_pad][fp]
+  void* items_bf16 = nullptr;  // [n_items_pad][fp] tensor-core operand rows (BF16 or E4M3)
   float2* item_aux = nullptr;  // {nhat_i, alpha_i}
+  int esize = 2;               // bytes per operand element: 2 BF16, 1 FP8 E4M3
+  float* item_scale = nullptr;  // FP8: the items' scale s_I (one device float)
   int64_t n_items_pad = 0;
   int num_sms = 0;
   int max_smem = 0;
@@ -243,6 +245,23 @@ int tc_cap(int K, int64_t n, bool chunked) {
   return std::max(base, (int)std::min<int64_t>(grow, n + 64));
 }
 
+// Candidate passes on the tensor cores: BF16 (kind::f16) or FP8 E4M3
+// (kind::f8f6f4) operand rows.
+bool tc_dtype(int d) { return d == MIPS_BF16 || d == MIPS_FP8_E4M3; }
+
+// The users' operand rows for the index's tensor-core dtype; FP8 also
+// writes each user's scale (user_scale) and points the plan at the scales.
+void quant_users(mips_index_t idx, const float* users, int64_t n_users, void* rows, float2* uaux, float* user_scale,
+                 TcParams& p, cudaStream_t s) {
+  if (idx->esize == 1) {
+    launch_quant_fp8(users, n_users, idx->f, idx->fp, 0, nullptr, rows, n_users, uaux, user_scale, idx->err_dev, s);
+    p.user_scale = user_scale;
+    p.item_scale = idx->item_scale;
+  } else {
+    launch_quant_bf16(users, n_users, idx->f, idx->fp, 0, rows, n_users, uaux, idx->err_dev, s);
+  }
+}
+
 // Blocked multiply (Sec. II-C) over the index's items with fused select,
 // then the exact rescore.
 // size_only: lay out the workspace, store the bytes it needs there and
@@ -258,8 +277,9 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   p.n_items = idx->n_items;
   p.f = f;
   p.fp = idx->fp;
+  p.esize = idx->esize;
   p.K = K;
-  const bool use_tc = idx->opt.dtype == MIPS_BF16 && tc_plan(p, idx->max_smem);
+  const bool use_tc = tc_dtype(idx->opt.dtype) && tc_plan(p, idx->max_smem);
   // Few user tiles would leave SMs idle: the item tiles are then split into
   // nch chunks, (user tile, chunk) pairs become the persistent grid's work
   // items, each with its own two sub-lists per user; the rescore takes the
@@ -276,7 +296,9 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   nch = (n_it + tpc - 1) / tpc;
   // BF16: two select threads per user (and chunk), each with its own sub-list
   const int lists = use_tc ? 2 * nch : 1;
-  const int cap = lists == 1 ? cap_for(K, idx->n_items) : tc_cap(K, (int64_t)tpc * tc_items_per_tile() / 2, nch > 1);
+  // (FP8's bound band is about 16 times BF16's: 2^-4 against 2^-8 per entry; its lists are 4 times longer)
+  const int cap = lists == 1 ? cap_for(K, idx->n_items)
+                             : (idx->esize == 1 ? 4 : 1) * tc_cap(K, (int64_t)tpc * tc_items_per_tile() / 2, nch > 1);
   const int64_t nl = n_users * lists;
   idx->ws.reset();
   size_t o_tau = idx->ws.take(sizeof(float) * nl);
@@ -290,11 +312,12 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
   size_t o_tauf = idx->ws.take(sizeof(float) * 2 * n_users);
-  size_t o_ub16 = 0, o_uaux = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0, o_heap = 0;
+  size_t o_ub16 = 0, o_uaux = 0, o_us = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0, o_heap = 0;
   if (use_tc && p.heap_global) o_heap = idx->ws.take(sizeof(float) * idx->num_sms * K * 256);
   if (use_tc) {
-    o_ub16 = idx->ws.take(sizeof(uint16_t) * n_users * idx->fp);
+    o_ub16 = idx->ws.take((size_t)idx->esize * n_users * idx->fp);
     o_uaux = idx->ws.take(sizeof(float2) * n_users);
+    if (idx->esize == 1) o_us = idx->ws.take(sizeof(float) * n_users);
   }
   if (nch > 1) {
     o_cw = idx->ws.take(sizeof(int) * 5 * n_ut * nch);
@@ -325,7 +348,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   } else {
     void* ub16 = idx->ws.at<void>(o_ub16);
     float2* uaux = idx->ws.at<float2>(o_uaux);
-    launch_quant_bf16(users, n_users, f, idx->fp, 0, ub16, n_users, uaux, idx->err_dev, s);
+    quant_users(idx, users, n_users, ub16, uaux, idx->esize == 1 ? idx->ws.at<float>(o_us) : nullptr, p, s);
     MIPS_CUDA(cudaGetLastError());
     idx->launches += 1;
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
@@ -371,7 +394,7 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   idx->launches += 4;  // collect, dot, select, overflow
   if ((st = end_stage(idx, ST_RESCORE, s)) != MIPS_OK) return st;
   idx->last_users = n_users;
-  idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
+  idx->last_dtype = use_tc ? idx->opt.dtype : MIPS_FP32;
   return MIPS_OK;
 }
 
@@ -410,9 +433,10 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   p.n_items = nI;
   p.f = f;
   p.fp = idx->fp;
+  p.esize = idx->esize;
   p.K = K;
   // (TMA row coordinates of the per-cluster item copies are 32-bit)
-  const bool use_tc = idx->opt.dtype == MIPS_BF16 && (int64_t)C * round_up(nI, 256) < (int64_t)INT32_MAX &&
+  const bool use_tc = tc_dtype(idx->opt.dtype) && (int64_t)C * round_up(nI, 256) < (int64_t)INT32_MAX &&
                       round_up(n_users, 128) + 128ll * C < (int64_t)INT32_MAX && mx_tc_regroup_fits(C, nI) &&
                       tc_plan(p, idx->max_smem);
   Arena& ws = idx->ws;
@@ -430,7 +454,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   // k-means assignment on tcgen05 (BF16 operands) when every centroid stays
   // resident in shared memory
   const int C_km = fitted ? C_fit : C;
-  const bool km_tc = idx->opt.dtype == MIPS_BF16 && km_tc_fits(f, C_km, idx->max_smem);
+  const bool km_tc = idx->opt.dtype != MIPS_FP32 && km_tc_fits(f, C_km, idx->max_smem);
   const int fk = km_tc_row_len(f);
   const size_t o_ukm = km_tc ? ws.take(sizeof(uint16_t) * n_users * fk) : 0;
   const size_t o_ckm = km_tc ? ws.take(sizeof(uint16_t) * (size_t)C_km * fk) : 0;
@@ -459,20 +483,23 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   const int blk = idx->opt.block_items > 0 ? idx->opt.block_items : 4096;
   const int t1 = (int)((blk + 255) / 256) < n_it ? (int)((blk + 255) / 256) : n_it;
   const int64_t n_pad = round_up(nI, 256);
-  const int cap2 = tc_cap(K, (nI + 1) / 2, false);
+  const int cap2 = (idx->esize == 1 ? 4 : 1) * tc_cap(K, (nI + 1) / 2, false);
   const int64_t nl = n_users * 2;
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
          o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0, o_clend = 0,
          o_heapm = 0;
+  size_t o_us = 0;
   if (use_tc) {
-    o_u16 = ws.take(sizeof(uint16_t) * n_users * fp);
+    const size_t es = (size_t)idx->esize;
+    o_u16 = ws.take(es * n_users * fp);
     o_uaux = ws.take(sizeof(float2) * n_users);
+    if (es == 1) o_us = ws.take(sizeof(float) * n_users);
     o_rowu = ws.take(sizeof(int32_t) * n_rows_max);
     o_urow = ws.take(sizeof(int32_t) * n_users);
     o_padoff = ws.take(sizeof(int) * (C + 1));
-    o_arows = ws.take(sizeof(uint16_t) * n_rows_max * fp);
-    o_brows = ws.take(sizeof(uint16_t) * C * n_pad * fp);
+    o_arows = ws.take(es * n_rows_max * fp);
+    o_brows = ws.take(es * C * n_pad * fp);
     o_auxc = ws.take(sizeof(float2) * C * n_pad);
     o_posc = ws.take(sizeof(int32_t) * C * n_pad);
     o_w1 = ws.take(sizeof(int) * 4 * max_work);
@@ -565,6 +592,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     MxTc m;
     m.C = C;
     m.fp = fp;
+    m.esize = idx->esize;
     m.t1 = t1;
     m.n_it = n_it;
     m.n_users = n_users;
@@ -597,7 +625,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     m.wvals[0] = ws.at<int32_t>(o_wv0);
     m.wvals[1] = ws.at<int32_t>(o_wv1);
     m.temp = ws.at<uint32_t>(o_tmp);
-    launch_quant_bf16(users, n_users, f, fp, 0, ws.at<void>(o_u16), n_users, ws.at<float2>(o_uaux), idx->err_dev, s);
+    quant_users(idx, users, n_users, ws.at<void>(o_u16), ws.at<float2>(o_uaux),
+                idx->esize == 1 ? ws.at<float>(o_us) : nullptr, p, s);
     idx->launches += 1;
     MIPS_CUDA(mx_tc_prepare(m, user_perm, idx->items_bf16, idx->item_aux, vals, s, &idx->launches));
     if ((st = end_stage(idx, ST_PREP, s)) != MIPS_OK) return st;
@@ -650,7 +679,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   idx->mx.C = C;
   idx->last_users = n_users;
   idx->last_clusters = C;
-  idx->last_dtype = use_tc ? MIPS_BF16 : MIPS_FP32;
+  idx->last_dtype = use_tc ? idx->opt.dtype : MIPS_FP32;
   return MIPS_OK;
 }
 
@@ -788,6 +817,8 @@ mips_index_t mips::index_worker_clone(mips_index_t src) {
   w->fp = src->fp;
   w->items_bf16 = src->items_bf16;
   w->item_aux = src->item_aux;
+  w->esize = src->esize;
+  w->item_scale = src->item_scale;
   w->n_items_pad = src->n_items_pad;
   w->num_sms = src->num_sms;
   w->max_smem = src->max_smem;
@@ -877,7 +908,7 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   mips_options o;
   mips_default_options(&o);
   if (opt) o = *opt;
-  if (o.dtype != MIPS_FP32 && o.dtype != MIPS_BF16) return fail(MIPS_ERR_UNIMPLEMENTED, "dtype %d not built", o.dtype);
+  if (o.dtype != MIPS_FP32 && !tc_dtype(o.dtype)) return fail(MIPS_ERR_ARG, "dtype %d is not a mips_dtype", o.dtype);
   if (o.kmeans_iters < 0 || o.kmeans_iters > 100) return fail(MIPS_ERR_ARG, "kmeans_iters out of range");
   if (o.block_items < 0) return fail(MIPS_ERR_ARG, "block_items must be >= 0 (0 = default)");
   if (!(o.sample_frac > 0.0 && o.sample_frac <= 1.0)) return fail(MIPS_ERR_ARG, "sample_frac out of range (0,1]");
@@ -935,13 +966,22 @@ mips_status mips_build_index(const float* items_dev, int64_t n_items, int f, int
   launch_gather_rows(items_dev, idx->perm, n_items, f, idx->items, s);
   launch_row_norm_ub(idx->items, n_items, f, idx->item_nrm, idx->err_dev, s);
   BUILD_CUDA(cudaGetLastError());
-  if (o.dtype == MIPS_BF16) {
-    idx->fp = tc_row_len(f);
+  if (tc_dtype(o.dtype)) {
+    const bool f8 = o.dtype == MIPS_FP8_E4M3;
+    idx->esize = f8 ? 1 : 2;
+    idx->fp = f8 ? tc_row_len8(f) : tc_row_len(f);
     idx->n_items_pad = round_up(n_items, tc_items_per_tile());
-    BUILD_CUDA(cudaMalloc(&idx->items_bf16, sizeof(uint16_t) * idx->n_items_pad * idx->fp));
+    BUILD_CUDA(cudaMalloc(&idx->items_bf16, (size_t)idx->esize * idx->n_items_pad * idx->fp));
     BUILD_CUDA(cudaMalloc(&idx->item_aux, sizeof(float2) * idx->n_items_pad));
-    launch_quant_bf16(idx->items, n_items, f, idx->fp, 1, idx->items_bf16, idx->n_items_pad, idx->item_aux,
-                      idx->err_dev, s);
+    if (f8) {  // one item scale from the largest norm bound (item_nrm is sorted, descending)
+      BUILD_CUDA(cudaMalloc(&idx->item_scale, sizeof(float)));
+      launch_fp8_item_scale(idx->item_nrm, n_items, idx->item_scale, s);
+      launch_quant_fp8(idx->items, n_items, f, idx->fp, 1, idx->item_scale, idx->items_bf16, idx->n_items_pad,
+                       idx->item_aux, nullptr, idx->err_dev, s);
+    } else {
+      launch_quant_bf16(idx->items, n_items, f, idx->fp, 1, idx->items_bf16, idx->n_items_pad, idx->item_aux,
+                        idx->err_dev, s);
+    }
     BUILD_CUDA(cudaGetLastError());
     // (tensor maps are made per call: the plan depends on K)
   }
@@ -1002,7 +1042,7 @@ mips_status mips_fit_clusters(mips_index_t idx, const float* users_dev, int64_t 
   size_t o_bits = ws.take(sizeof(uint32_t) * ((n_users + 31) / 32));
   size_t o_assign = ws.take(sizeof(int32_t) * n_users), o_sums = ws.take(sizeof(unsigned long long) * C * f);
   size_t o_cnt = ws.take(sizeof(unsigned) * C), o_amax = ws.take(16), o_scale = ws.take(16);
-  const bool km_tc = idx->opt.dtype == MIPS_BF16 && km_tc_fits(f, C, idx->max_smem);
+  const bool km_tc = idx->opt.dtype != MIPS_FP32 && km_tc_fits(f, C, idx->max_smem);
   const int fk = km_tc_row_len(f);
   const size_t o_ukm = km_tc ? ws.take(sizeof(uint16_t) * n_users * fk) : 0;
   const size_t o_ckm = km_tc ? ws.take(sizeof(uint16_t) * (size_t)C * fk) : 0;
@@ -1447,6 +1487,7 @@ void mips_free_index(mips_index_t idx) {
     cudaFree(idx->item_nrm);
     cudaFree(idx->items_bf16);
     cudaFree(idx->item_aux);
+    cudaFree(idx->item_scale);
   }
   if (idx->copy_stream) cudaStreamDestroy(idx->copy_stream);
   cudaFree(idx->fit_cent);

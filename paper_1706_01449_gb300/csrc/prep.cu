@@ -22,6 +22,7 @@
 // The matching lower bound used by the select is
 //   L = H - 2 A - g (nhat_u nhat_i + A),   A = beta_u nhat_i + nhat_u alpha_i.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 
@@ -178,6 +179,138 @@ __global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f,
     if (row0 + q < n_rows_out) quant_bf16_row(v[q], row0 + q, n, f, fp, role, out, aux, err, lane);
 }
 
+// ---------------------------------------------------------------- FP8 rows
+// E4M3 operand layout (K-major rows of fp = tc_row_len8(f) bytes):
+//   users: [ q(u_k / s_u) .. | RU(beta_u / s_u) | RU(nhat_u / s_u) | 0 .. ],  s_u = nhat_u / 384 per row
+//   items: [ q(i_k / s_I) .. | RU(nhat_i / s_I) | RU(alpha_i / s_I) | 0 .. ], s_I = (max_i nhat_i) / 384
+// q: round to nearest E4M3, saturating; RU: the quotient rounded up, then
+// up to an E4M3 value.  The operands the MMA multiplies are, in input
+// units, u~ = s_u q(u / s_u) and i~ = s_I q(i / s_I), and the bound columns
+// are the BF16 layout's for these u~, i~ (nhat >= max(||x||, ||x~||),
+// beta and alpha >= (||x - x~|| + g nhat)(1 + g)).  A rounded-up column
+// times its scale is at least its input-unit value, so s_u s_I times the
+// accumulator is H >= u~ . i~ + beta_u nhat_i + nhat_u alpha_i >= u^T i as in
+// the BF16 case; aux receives those products (rounded up), so the select's
+// A = beta_u nhat_i + nhat_u alpha_i from aux covers the folded columns and
+// the quantisation error alike, and L = H - 2 A - g (nhat_u nhat_i + A)
+// stays a lower bound.  The scales put every entry and every norm column at
+// most 384 (times 1 + 2^-4 for nhat of a rounded row), below E4M3's 448.
+constexpr float kFp8Inv = 2.6041666e-03f;  // 1 / 384
+
+__device__ __forceinline__ uint8_t e4m3_rn(float x) {
+  return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float e4m3_val(uint8_t q) {
+  const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3);
+  return __half2float(__half(h));
+}
+// x >= 0 rounded up to an E4M3 value (positive encodings are ordered like
+// their values; 0x7e = 448 is the largest finite one).
+__device__ __forceinline__ uint8_t e4m3_ru(float x, int* err) {
+  uint8_t q = e4m3_rn(x);
+  if (e4m3_val(q) < x) {
+    if (q >= 0x7e) atomicOr(err, DEV_ERR_INTERNAL);  // not reached: the scales keep x below 448
+    else ++q;
+  }
+  return q;
+}
+
+// One row whose elements this lane holds in v (element lane + 32 j in v[j]).
+// role 0 (users): the row's own scale, written to row_scale[row]; role 1
+// (items): the scale *item_scale.
+__device__ __forceinline__ void quant_fp8_row(const float (&v)[4], int64_t row, int64_t n, int f, int fp, int role,
+                                              const float* __restrict__ item_scale, uint8_t* __restrict__ out,
+                                              float2* __restrict__ aux, float* __restrict__ row_scale, int* err,
+                                              int lane) {
+  uint8_t* o = out + row * fp;
+  if (row >= n) {  // padding rows
+    for (int k = lane; k < fp; k += 32) o[k] = 0;
+    return;
+  }
+  float amax = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (lane + 32 * j < f) amax = fmaxf(amax, fabsf(v[j]));
+  amax = warp_max(amax);
+  const int e = (amax > 0.f && isfinite(amax)) ? norm_scale_exp(amax) : 0;
+  float ss_x = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (lane + 32 * j < f) {
+      const float xs = scale_pow2(v[j], e);
+      ss_x = __fmaf_rn(xs, xs, ss_x);
+    }
+  ss_x = warp_sum(ss_x);
+  const float nx = amax > 0.f ? unscale_pow2_ru(norm_ub(ss_x + tiny_floor(f), f), e) : 0.f;
+  float sc = role == 0 ? __fmul_rn(nx, kFp8Inv) : *item_scale;
+  if (!(sc > 0.f) || !isfinite(sc)) sc = 1.f;  // the zero row (every entry quantises to 0)
+  float ss_t = 0.f, ss_d = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = lane + 32 * j;
+    if (k < f) {
+      const float x = v[j];
+      const uint8_t q = e4m3_rn(__fdiv_rn(x, sc));
+      const float qv = e4m3_val(q);
+      const float t = __fmul_rn(sc, qv);       // x~ (one rounding)
+      const float d = __fmaf_rn(-sc, qv, x);   // x - x~ (one rounding)
+      const float ts = scale_pow2(t, e), ds = scale_pow2(d, e);
+      ss_t = __fmaf_rn(ts, ts, ss_t);
+      ss_d = __fmaf_rn(ds, ds, ss_d);
+      o[k] = q;
+    }
+  }
+  ss_t = warp_sum(ss_t);
+  ss_d = warp_sum(ss_d);
+  const float g = (float)(fp + 4) * 9.5367432e-07f + (float)f * 8.8817842e-16f;  // 2^-20, 2^-50
+  float nhat = 0.f, errn = 0.f;
+  if (amax > 0.f) {
+    nhat = fmaxf(nx, unscale_pow2_ru(norm_ub(ss_t + tiny_floor(f), f), e));
+    errn = unscale_pow2_ru(norm_ub(ss_d + tiny_floor(f), f), e);
+  }
+  const float eb = __fmul_ru(__fmaf_ru(g, nhat, errn), 1.0f + g);
+  if (lane == 0) {
+    if (!isfinite(ss_x) || !isfinite(nhat)) atomicOr(err, DEV_ERR_NONFINITE);
+    const float c0 = role == 0 ? eb : nhat, c1 = role == 0 ? nhat : eb;
+    const uint8_t q0 = e4m3_ru(__fdiv_ru(c0, sc), err), q1 = e4m3_ru(__fdiv_ru(c1, sc), err);
+    o[f] = q0;
+    o[f + 1] = q1;
+    aux[row] = make_float2(__fmul_ru(sc, e4m3_val(q0)), __fmul_ru(sc, e4m3_val(q1)));
+    if (role == 0) row_scale[row] = sc;
+  }
+  for (int k = f + 2 + lane; k < fp; k += 32) o[k] = 0;
+}
+
+// A warp per kQuantRows consecutive rows.
+__global__ void quant_fp8_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role,
+                                 const float* __restrict__ item_scale, uint8_t* __restrict__ out, int64_t n_rows_out,
+                                 float2* __restrict__ aux, float* __restrict__ row_scale, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * kQuantRows;
+  if (row0 >= n_rows_out) return;
+  float v[kQuantRows][4];
+#pragma unroll
+  for (int q = 0; q < kQuantRows; ++q) {
+    const int64_t row = row0 + q;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = lane + 32 * j;
+      v[q][j] = (row < n && k < f) ? x[row * f + k] : 0.f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kQuantRows; ++q)
+    if (row0 + q < n_rows_out)
+      quant_fp8_row(v[q], row0 + q, n, f, fp, role, item_scale, out, aux, row_scale, err, lane);
+}
+
+// s_I from the largest item norm bound (the sorted bounds' first entry).
+__global__ void fp8_item_scale_kernel(const float* __restrict__ item_nrm, int64_t n, float* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float m = n > 0 ? item_nrm[0] : 0.f;
+  out[0] = (m > 0.f && isfinite(m)) ? __fmul_rn(m, kFp8Inv) : 1.f;
+}
+
 __global__ void gather_rows_kernel(const float* __restrict__ x, const int32_t* __restrict__ perm,
                                    int64_t n, int f, float* __restrict__ out) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,6 +414,18 @@ void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void*
   const int64_t rows_per_block = 8 * kQuantRows;
   quant_bf16_kernel<<<(unsigned)((n_rows_out + rows_per_block - 1) / rows_per_block), 8 * 32, 0, s>>>(
       x, n, f, fp, role, (__nv_bfloat16*)out_bf16, n_rows_out, aux, err);
+}
+
+void launch_quant_fp8(const float* x, int64_t n, int f, int fp, int role, const float* item_scale, void* out,
+                      int64_t n_rows_out, float2* aux, float* row_scale, int* err, cudaStream_t s) {
+  if (n_rows_out <= 0) return;
+  const int64_t rows_per_block = 8 * kQuantRows;
+  quant_fp8_kernel<<<(unsigned)((n_rows_out + rows_per_block - 1) / rows_per_block), 8 * 32, 0, s>>>(
+      x, n, f, fp, role, item_scale, (uint8_t*)out, n_rows_out, aux, row_scale, err);
+}
+
+void launch_fp8_item_scale(const float* item_nrm, int64_t n, float* item_scale, cudaStream_t s) {
+  fp8_item_scale_kernel<<<1, 32, 0, s>>>(item_nrm, n, item_scale);
 }
 
 void launch_gather_rows(const float* x, const int32_t* perm, int64_t n, int f, float* out, cudaStream_t s) {

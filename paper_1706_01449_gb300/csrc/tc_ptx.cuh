@@ -120,6 +120,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+// One FP8 MMA (E4M3 x E4M3 -> FP32, kind::f8f6f4, K = 32); ACC as for
+// mma_bf16.
+template <int ACC>
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "n"(ACC)
+      : "memory");
+}
+
 // K steps (K = 16 each) of one operand row, at most: two full 64-element
 // chunks and a 32-element tail (f = 128 needs 8 + 1).
 constexpr int kMaxSteps = 10;
@@ -127,12 +139,18 @@ constexpr int kMaxSteps = 10;
 // The N MMAs of one item load, fully unrolled: a single thread issues them
 // back to back, so a loop, a branch or a computed predicate per MMA would
 // add issue time the tensor pipe waits for.  boff: the load's ring stage.
-template <int N>
+template <int N, bool F8 = false>
 __device__ __forceinline__ void mma_steps(uint32_t d, const uint64_t (&a_d)[kMaxSteps],
                                           const uint64_t (&b_d)[kMaxSteps], uint64_t boff, uint32_t idesc) {
-  mma_bf16<0>(d, a_d[0], b_d[0] + boff, idesc);
+  if constexpr (F8) {
+    mma_f8<0>(d, a_d[0], b_d[0] + boff, idesc);
 #pragma unroll
-  for (int s = 1; s < N; ++s) mma_bf16<1>(d, a_d[s], b_d[s] + boff, idesc);
+    for (int s = 1; s < N; ++s) mma_f8<1>(d, a_d[s], b_d[s] + boff, idesc);
+  } else {
+    mma_bf16<0>(d, a_d[0], b_d[0] + boff, idesc);
+#pragma unroll
+    for (int s = 1; s < N; ++s) mma_bf16<1>(d, a_d[s], b_d[s] + boff, idesc);
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {

@@ -89,6 +89,7 @@ struct TcUser {
   int n_cand;
   int ut;         // current work item (tag of the published threshold)
   float beta_u, nhat_u;  // bound columns of this user (prep.cu)
+  float au;              // FP8: user_scale[u] * item_scale, the accumulator's unit
   float d[KR > 0 ? KR : 1];
 };
 
@@ -115,6 +116,7 @@ struct TcSel {
   int slot, pslot;    // this thread's column and its partner's (the other half of the same user)
   unsigned* tau_glob;  // this user's shared threshold (item-chunked scan) or null
   float g;            // accumulation-error factor of prep.cu
+  bool f8;            // FP8 operands: accumulator entries are scaled (hv)
   __device__ __forceinline__ float* qh() const { return qbase + slot; }  // qh()[t * kEpiThreads]
   __device__ __forceinline__ volatile unsigned long long* tau(int sl) const {
     return (volatile unsigned long long*)(qbase + kTauOfs) + sl;
@@ -122,6 +124,18 @@ struct TcSel {
   __device__ __forceinline__ volatile int* seed_tag(int sl) const { return (volatile int*)qbase + kSeedTagOfs + sl; }
   __device__ __forceinline__ volatile float* seed_list(int sl) const { return qbase + kSeedListOfs + sl; }
 };
+
+// An accumulator entry in input units: BF16 entries are scores already;
+// FP8 entries count in units of au = s_u s_I.  The scaled value gets an
+// upward margin of 2^-21 of its size for the roundings of au and of the
+// product (2^-24 each), so it stays an upper bound; the map is increasing,
+// so the maximum of scaled entries is the scaled maximum.
+template <int KR>
+__device__ __forceinline__ float hv(const TcUser<KR>& s, const TcSel& c, float raw) {
+  if (!c.f8) return raw;
+  const float t = s.au * raw;
+  return __fmaf_rn(fabsf(t), 4.76837158203125e-07f, t);  // 2^-21
+}
 
 template <int KR>
 __device__ __forceinline__ void topk_init(TcUser<KR>& s, const TcSel& c) {
@@ -238,7 +252,7 @@ __device__ __forceinline__ void seed8_heap(TcUser<KR>& s, const TcSel& c, const 
                                            int valid, const float2* aux) {
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float L = col0 + q < valid ? tc_lower(s, c, __uint_as_float(r[q]), aux[col0 + q]) : kNegInf;
+    const float L = col0 + q < valid ? tc_lower(s, c, hv(s, c, __uint_as_float(r[q])), aux[col0 + q]) : kNegInf;
     if (L > s.tau) s.tau = heap_replace_min(c.heap, kEpiThreads, c.K, L);
   }
 }
@@ -266,7 +280,7 @@ __device__ __forceinline__ void seed8_reg(TcUser<KR>& s, const TcSel& c, const u
   float L[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q)
-    L[q] = col0 + q < valid ? tc_lower(s, c, __uint_as_float(r[q]), aux[col0 + q]) : kNegInf;
+    L[q] = col0 + q < valid ? tc_lower(s, c, hv(s, c, __uint_as_float(r[q])), aux[col0 + q]) : kNegInf;
   float hi, lo;
   top2_of8(L, hi, lo);
   if constexpr (KR == 1) {
@@ -376,7 +390,7 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
   for (int gi = 0; gi < kHalfN / 16; ++gi) {
     if (!((halves >> (gi >> 2)) & 1u)) continue;  // warp-uniform
     uint32_t v[16];
-    const float mg = tmem_ldmax16(taddr + 16 * gi, v);
+    const float mg = hv(s, c, tmem_ldmax16(taddr + 16 * gi, v));
     const bool hit = mg >= s.tau_eff;
     if (!__any_sync(kFull, hit)) continue;
     const int col0 = 16 * gi;
@@ -386,7 +400,7 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
       const int nv = valid - col0;  // columns of the group below `valid`
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float x = __uint_as_float(v[q]);
+        const float x = hv(s, c, __uint_as_float(v[q]));
         stage[q * kEpiThreads] = x;
         mask |= (x >= t && q < nv) ? (1u << q) : 0u;
       }
@@ -620,11 +634,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       bool ok_init = true;
-      // instruction descriptor: D = F32, A = B = BF16, both K-major, N, M
-      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(sub_rows >> 3) << 17) |
-                             ((uint32_t)(kTileM >> 4) << 24);
+      // instruction descriptor: D = F32, A = B = BF16 (kind::f16 format 1) or
+      // E4M3 (kind::f8f6f4 format 0), both K-major, N, M
+      const bool f8 = p.esize == 1;
+      const uint32_t ab_fmt = f8 ? 0u : ((1u << 7) | (1u << 10));
+      const uint32_t idesc = (1u << 4) | ab_fmt | ((uint32_t)(sub_rows >> 3) << 17) | ((uint32_t)(kTileM >> 4) << 24);
       const uint32_t sbo = 8 * p.row_bytes;
-      const int ksteps = p.row_bytes / 32;  // K = 16 BF16 = 32 bytes per MMA
+      const int ksteps = p.row_bytes / 32;  // 32 bytes per MMA: K = 16 BF16 or K = 32 E4M3
       // descriptors of the first A chunk and of ring stage 0; every other
       // operand is a fixed address offset, added to the 14-bit address field
       // (addresses >> 4), as is the 32-byte step of each K = 16 slice
@@ -676,17 +692,32 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
             const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
             const uint64_t boff = (uint64_t)(st * stage16);
-            switch (nst) {
-              case 1: mma_steps<1>(d, a_d, b_d, boff, idesc); break;
-              case 2: mma_steps<2>(d, a_d, b_d, boff, idesc); break;
-              case 3: mma_steps<3>(d, a_d, b_d, boff, idesc); break;
-              case 4: mma_steps<4>(d, a_d, b_d, boff, idesc); break;
-              case 5: mma_steps<5>(d, a_d, b_d, boff, idesc); break;
-              case 6: mma_steps<6>(d, a_d, b_d, boff, idesc); break;
-              case 7: mma_steps<7>(d, a_d, b_d, boff, idesc); break;
-              case 8: mma_steps<8>(d, a_d, b_d, boff, idesc); break;
-              case 9: mma_steps<9>(d, a_d, b_d, boff, idesc); break;
-              default: mma_steps<10>(d, a_d, b_d, boff, idesc); break;
+            if (f8) {
+              switch (nst) {
+                case 1: mma_steps<1, true>(d, a_d, b_d, boff, idesc); break;
+                case 2: mma_steps<2, true>(d, a_d, b_d, boff, idesc); break;
+                case 3: mma_steps<3, true>(d, a_d, b_d, boff, idesc); break;
+                case 4: mma_steps<4, true>(d, a_d, b_d, boff, idesc); break;
+                case 5: mma_steps<5, true>(d, a_d, b_d, boff, idesc); break;
+                case 6: mma_steps<6, true>(d, a_d, b_d, boff, idesc); break;
+                case 7: mma_steps<7, true>(d, a_d, b_d, boff, idesc); break;
+                case 8: mma_steps<8, true>(d, a_d, b_d, boff, idesc); break;
+                case 9: mma_steps<9, true>(d, a_d, b_d, boff, idesc); break;
+                default: mma_steps<10, true>(d, a_d, b_d, boff, idesc); break;
+              }
+            } else {
+              switch (nst) {
+                case 1: mma_steps<1>(d, a_d, b_d, boff, idesc); break;
+                case 2: mma_steps<2>(d, a_d, b_d, boff, idesc); break;
+                case 3: mma_steps<3>(d, a_d, b_d, boff, idesc); break;
+                case 4: mma_steps<4>(d, a_d, b_d, boff, idesc); break;
+                case 5: mma_steps<5>(d, a_d, b_d, boff, idesc); break;
+                case 6: mma_steps<6>(d, a_d, b_d, boff, idesc); break;
+                case 7: mma_steps<7>(d, a_d, b_d, boff, idesc); break;
+                case 8: mma_steps<8>(d, a_d, b_d, boff, idesc); break;
+                case 9: mma_steps<9>(d, a_d, b_d, boff, idesc); break;
+                default: mma_steps<10>(d, a_d, b_d, boff, idesc); break;
+              }
             }
             mma_commit(&ctl->b_empty[st]);
             if (++st == p.stages) {
@@ -722,6 +753,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     c.slot = slot;
     c.pslot = (c2 ^ 1) * kTileM + row;
     c.g = p.g;
+    c.f8 = p.esize == 1;
+    const float item_scale = c.f8 ? *p.item_scale : 0.f;
     long long g = 0;  // item tiles processed: the accumulator and aux-ring sequence
     bool ok = true;
     unsigned long long emitted = 0, slow = 0;
@@ -741,6 +774,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       s.ut = wi;
       s.beta_u = 0.f;
       s.nhat_u = 0.f;
+      s.au = 1.f;
       const int lbase = (MX && p.work.l_base) ? p.work.l_base[wk.q] : 0;
       const int64_t list = (active ? u : 0) * (int64_t)o.lists + lbase + c2;
       const bool restoring = MX && p.work.restore && wk.tb > 0;
@@ -752,6 +786,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const float2 ua = user_aux[u];
         s.beta_u = ua.x;
         s.nhat_u = ua.y;
+        if (c.f8) s.au = __fmul_rn(p.user_scale[u], item_scale);
         if (restoring) {  // continue a walk: restore the select state
           s.n_cand = o.n_cand[list];
           const float* src = o.topl + list * (int64_t)p.K;
@@ -810,7 +845,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         unsigned halves = 0;
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
-          const float m = tmem_ldmax64(taddr + 64 * h);
+          const float m = hv(s, c, tmem_ldmax64(taddr + 64 * h));
           halves |= __any_sync(kFull, m >= s.tau_eff) ? (1u << h) : 0u;
         }
         if (halves) {

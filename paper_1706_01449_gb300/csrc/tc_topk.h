@@ -35,7 +35,12 @@ struct TcWork {
 
 struct TcParams {
   int64_t n_users, n_items;
-  int f, fp, K;
+  int f, fp, K;   // fp: operand row length in elements
+  int esize;      // bytes per operand element: 2 (BF16, kind::f16) or 1 (FP8 E4M3, kind::f8f6f4)
+  // FP8 only: every accumulator entry times user_scale[u] * item_scale[0]
+  // (per-row user scale, one item scale) is the score in input units
+  const float* user_scale;
+  const float* item_scale;
   int kc;         // full K chunks per operand row
   int row_bytes;  // bytes of one full chunk row: 32, 64 or 128 (= swizzle span)
   int row_elems;  // BF16 elements of one full chunk row
@@ -69,14 +74,31 @@ inline int tc_row_len(int f) {
   return full + 64;
 }
 
-// Fill chunking, swizzle and stages for this problem so the shared memory
-// fits; returns false if no configuration fits.
+// FP8 operand row length (E4M3 elements = bytes) for dimension f: f + 2
+// bound columns padded to 32, 64 or 128, or above 128 to whole 128-element
+// chunks plus a 32- or 64-element tail chunk when that covers the rest.
+inline int tc_row_len8(int f) {
+  const int n = f + 2;
+  if (n <= 32) return 32;
+  if (n <= 64) return 64;
+  if (n <= 128) return 128;
+  const int full = n / 128 * 128, rem = n - full;
+  if (rem == 0) return full;
+  if (rem <= 32) return full + 32;
+  if (rem <= 64) return full + 64;
+  return full + 128;
+}
+
+// Fill chunking, swizzle and stages for this problem (p.fp, p.esize) so the
+// shared memory fits; returns false if no configuration fits.
 bool tc_plan(TcParams& p, int max_smem);
 size_t tc_smem_bytes(const TcParams& p);
 
-// K-major BF16 operand map [rows][fp], boxes of row_bytes / 2 elements x
-// box_rows rows, swizzled by row_bytes (32, 64 or 128).
-bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows);
+// K-major operand map [rows][fp] of esize-byte elements (2: BF16, 1: bytes),
+// boxes of row_bytes / esize elements x box_rows rows, swizzled by row_bytes
+// (32, 64 or 128).
+bool tc_make_map(CUtensorMap* map, const void* base, int64_t rows, int fp, int row_bytes, int box_rows,
+                 int esize = 2);
 // The full-chunk map and, when p.tail_bytes > 0, the tail-chunk map (else a
 // copy of the first) of one operand.
 bool tc_make_maps(CUtensorMap* map, CUtensorMap* tail, const void* base, int64_t rows, const TcParams& p,

@@ -59,8 +59,8 @@ def test_argument_errors_need_no_gpu():
         assert lib.mips_build_index(fake, 10, 4, 2, ctypes.byref(o2), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG, field
     o2 = mips.Options()
     lib.mips_default_options(ctypes.byref(o2))
-    o2.dtype = mips.DTYPES.get("fp8", 2)
-    assert lib.mips_build_index(fake, 10, 4, 2, ctypes.byref(o2), None, ctypes.byref(h)) == mips.MIPS_ERR_UNIMPLEMENTED
+    o2.dtype = 7  # not a mips_dtype
+    assert lib.mips_build_index(fake, 10, 4, 2, ctypes.byref(o2), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
     assert lib.mips_build_index(fake, 10, 4, 4097, ctypes.byref(opt), None, ctypes.byref(h)) == mips.MIPS_ERR_ARG
     assert lib.mips_topk(None, fake, 4, 1, fake, fake, None) == mips.MIPS_ERR_ARG
     assert lib.mips_topk_maximus(None, fake, 4, 1, fake, fake, None) == mips.MIPS_ERR_ARG

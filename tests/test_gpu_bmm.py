@@ -13,7 +13,7 @@ from parity_util import check_against_oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-DTYPES = ["fp32", "bf16"]
+DTYPES = ["fp32", "bf16", "fp8"]
 
 
 def _dtype_or_skip(dtype, I, **kw):

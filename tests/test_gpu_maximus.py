@@ -55,14 +55,14 @@ def run_maximus(U, I, K, C, dtype="fp32", iters=3, seed=0, block_items=0):
     return idx.cpu().numpy(), sc.cpu().numpy(), st, bufs, bmm_idx.cpu().numpy(), bmm_sc.cpu().numpy()
 
 
-@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 0), ("bf16", 256)])
+@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 0), ("bf16", 256), ("fp8", 0), ("fp8", 256)])
 @pytest.mark.parametrize("C,K", [(8, 10), (16, 1), (4, 50)])
 def test_maximus_exact_and_bounds(C, K, dtype, block):
     """bf16 runs the tensor-core walk: pass 1 over the first block of every
     list (4096 items, or one 256-item tile), pass 2 over the rest."""
     U, I = clustered(3000, 2000, 16, seed=C + K)
     idx, sc, st, b, bidx, bsc = run_maximus(U, I, K, C, dtype=dtype, block_items=block)
-    assert st["dtype"] == (1 if dtype == "bf16" else 0)
+    assert st["dtype"] == mips.DTYPES[dtype]  # the tensor-core path of that dtype was taken
     ref = oracle.topk(U, I, K)
     check_against_oracle(U, I, K, idx, sc, ref=ref)
     assert (idx == bidx).all() and (sc == bsc).all()
@@ -95,7 +95,7 @@ def test_maximus_exact_and_bounds(C, K, dtype, block):
     assert st["pairs_scored"] == b["visited"].sum()
 
 
-@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 512)])
+@pytest.mark.parametrize("dtype,block", [("fp32", 0), ("bf16", 512), ("fp8", 512)])
 def test_maximus_prunes_on_clustered_users(dtype, block):
     U, I = clustered(4000, 6000, 12, seed=11, n_dirs=8, noise=0.1)
     idx, sc, st, b, _, _ = run_maximus(U, I, 5, 8, dtype=dtype, block_items=block)
@@ -118,7 +118,7 @@ def test_kmeans_invariants():
     assert d.shape == (U.shape[0], cent.shape[0])
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "fp8"])
 def test_spherical_kmeans(dtype):
     """kmeans_spherical (Sec. III-A): exact results; every centroid is the unit
     vector along its members' mean (of the last assignment step)."""
@@ -141,7 +141,7 @@ def test_spherical_kmeans(dtype):
     index.close()
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+@pytest.mark.parametrize("dtype", ["fp32", "bf16", "fp8"])
 def test_maximus_degenerate_cases(dtype):
     rng = np.random.default_rng(1)
     base = rng.integers(-3, 4, size=(50, 6)).astype(np.float32)

@@ -37,8 +37,8 @@ def tiny_users(f, seed):
     return U.astype(np.float32)
 
 
-@pytest.mark.parametrize("method,dtype", [("bmm", "bf16"), ("bmm", "fp32"), ("maximus", "bf16"),
-                                          ("maximus", "fp32")])
+@pytest.mark.parametrize("method,dtype", [("bmm", "bf16"), ("bmm", "fp32"), ("bmm", "fp8"), ("maximus", "bf16"),
+                                          ("maximus", "fp32"), ("maximus", "fp8")])
 @pytest.mark.parametrize("K", [1, 10])
 def test_tiny_and_zero_users_exact(method, dtype, K):
     f = 24
@@ -74,8 +74,8 @@ def neg_e1_users(f, seed):
     return np.concatenate([D, U]).astype(np.float32)
 
 
-@pytest.mark.parametrize("method,dtype", [("bmm", "bf16"), ("bmm", "fp32"), ("maximus", "bf16"),
-                                          ("maximus", "fp32")])
+@pytest.mark.parametrize("method,dtype", [("bmm", "bf16"), ("bmm", "fp32"), ("bmm", "fp8"), ("maximus", "bf16"),
+                                          ("maximus", "fp32"), ("maximus", "fp8")])
 @pytest.mark.parametrize("K", [1, 10])
 def test_tiny_items_exact(method, dtype, K):
     f = 24
