@@ -68,7 +68,8 @@ def parse(argv=None):
                    help="Maximus / selector: keep --clusters and the default block instead of mips_autotune")
     p.add_argument("--legs", default="bmm,fp32,fp8",
                    help="extra forms timed after the main steps on the same inputs: comma list of bmm (BF16 "
-                        "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply); 'none' for none")
+                        "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply), fp8 (the main method on an "
+                        "FP8 E4M3 index); 'none' for none")
     p.add_argument("--leg-steps", type=int, default=3)
     p.add_argument("--users", type=int, default=0,
                    help="use only the first N users (profiling captures; not the benchmark workload)")
