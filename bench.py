@@ -66,10 +66,11 @@ def parse(argv=None):
     p.add_argument("--clusters", type=int, default=64, help="|C| when the autotuner is off")
     p.add_argument("--no-autotune", action="store_true",
                    help="Maximus / selector: keep --clusters and the default block instead of mips_autotune")
-    p.add_argument("--legs", default="bmm,fp32,fp8",
+    p.add_argument("--legs", default="bmm,fp32,fp8,arms",
                    help="extra forms timed after the main steps on the same inputs: comma list of bmm (BF16 "
                         "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply), fp8 (the main method on an "
-                        "FP8 E4M3 index); 'none' for none")
+                        "FP8 E4M3 index), arms (the multi-arm selector over BF16, FP8 and FP32 indexes); 'none' for "
+                        "none")
     p.add_argument("--leg-steps", type=int, default=3)
     p.add_argument("--users", type=int, default=0,
                    help="use only the first N users (profiling captures; not the benchmark workload)")
@@ -567,8 +568,31 @@ def main(argv=None):
     for leg in leg_names:
         if leg == args.method and dtype == "bf16":
             continue
-        if leg not in ("bmm", "maximus", "fp32", "fp8"):
+        if leg not in ("bmm", "maximus", "fp32", "fp8", "arms"):
             raise SystemExit(f"unknown leg {leg}")
+        if leg == "arms":  # the multi-arm selector over BF16, FP8 and FP32 indexes of the same items
+            oi = torch.empty_like(out_idx)
+            osc = torch.empty_like(out_sc)
+            extra = [mips.build_index(I_d, clusters=args.clusters, dtype=d) for d in ("fp8", "fp32")]
+            arms_rep = {}
+
+            def astep():
+                arms_rep.update(mips.select_arms([index] + extra, U_d, K, 0, oi, osc, stream=stream)[2])
+            lms, _, _, _ = timed_steps(astep, 1, args.leg_steps, stream, flush, index, mips)
+            names = {0: "fp32", 1: "bf16", 2: "fp8"}
+            arms = [{"dtype": names[a["dtype"]], "method": "maximus" if a["method"] else "bmm",
+                     "est_ms_all_users": a["est_mean"] * 1e3, "ci95_ms": a["est_ci"] * 1e3, "rounds": a["rounds"],
+                     "dropped": bool(a["dropped"])} for a in arms_rep["arms"]]
+            legs["arms"] = {"value": nU / (statistics.mean(lms) / 1e3), "unit": "users/s",
+                            "ms_per_step": statistics.mean(lms), "steps": args.leg_steps, "warmup": 1,
+                            "same_result_as_main": bool(torch.equal(oi, out_idx) and torch.equal(osc, out_sc)),
+                            "choice": arms[arms_rep["choice"]], "separated": bool(arms_rep["separated"]),
+                            "rounds": arms_rep["rounds"], "sample_users": arms_rep["sample_users"],
+                            "overhead_frac": arms_rep["t_sample"] / arms_rep["t_total"], "arms": arms}
+            for x in extra:
+                x.close()
+            del oi, osc
+            continue
         oi = torch.empty_like(out_idx)
         osc = torch.empty_like(out_sc)
         if leg == "fp32":

@@ -156,6 +156,54 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
                         int32_t* out_idx_dev, double* out_score_dev, void* stream,
                         mips_select_report* rep);
 
+/* One arm of mips_select_arms: a candidate pass (the dtype of one of the
+ * given indexes) with one method. */
+typedef struct {
+  int index;        /* position of its index in the indexes argument */
+  int dtype;        /* mips_dtype of that index */
+  int method;       /* 0 blocked multiply (mips_topk), 1 Maximus (mips_topk_maximus) */
+  int rounds;       /* timings of the sample taken */
+  double est_mean;  /* predicted seconds for all n_users, mean over its timings */
+  double est_ci;    /* half-width of the 95% confidence interval of that mean
+                     * (Student t, rounds - 1 degrees of freedom; 0 below 2 rounds) */
+  int dropped;      /* 1: no longer timed once its interval lay above the best arm's */
+} mips_arm_report;
+
+#define MIPS_MAX_ARMS 16
+
+typedef struct {
+  int n_arms;
+  mips_arm_report arm[MIPS_MAX_ARMS];
+  int choice;             /* arm that finished the remaining users */
+  int separated;          /* 1: the chosen arm's interval lay below every other arm's */
+  int rounds;             /* rounds run (every live arm timed once per round) */
+  int64_t sample_users;   /* users in the timed sample */
+  double t_sample;        /* seconds of device time spent timing arms on the sample */
+  double t_total;         /* seconds of device time of the whole call */
+} mips_arms_report;
+
+/*
+ * Multi-arm Optimus (Sec. IV, with more arms than the paper's two): the arms
+ * are every given index (built on the same items, e.g. with the FP32, BF16
+ * and FP8 candidate passes) times {blocked multiply, Maximus}.  A seeded
+ * user sample (as mips_select's) is timed on every arm in rounds; each
+ * timing is extrapolated to all users (blocked multiply: per user;
+ * Maximus: the sample's k-means per user, bounds and sort once, the rest
+ * per user).  The paper's early stop, a t-test on per-user times, does not
+ * apply to arms that batch users, as all of these do; instead, after every
+ * round from the third on, an arm whose interval lies above the best arm's
+ * is dropped, and the rounds stop once the best arm's interval lies below
+ * every remaining one (or after max_rounds, 3..16; 0 = 6).  The chosen arm's
+ * sample results are kept and it computes the remaining users; every arm
+ * is exact, so any choice gives the same top-K.  Synchronises the stream.
+ * Every index must hold the same items (not checked: same f and n_items
+ * are) and live on the current device; the call runs on indexes[0]'s
+ * stream order (the others' earlier calls are waited for).  rep may be NULL.
+ */
+mips_status mips_select_arms(const mips_index_t* indexes, int n_indexes, const float* users_dev, int64_t n_users,
+                             int K, int max_rounds, int32_t* out_idx_dev, double* out_score_dev, void* stream,
+                             mips_arms_report* rep);
+
 /* Result of mips_autotune. */
 typedef struct {
   int clusters;            /* chosen |C|, now the index's */

@@ -788,6 +788,178 @@ mips_status run_select(mips_index_t idx, const float* users, int64_t n_users, in
   return MIPS_OK;
 }
 
+// Two-sided 95% quantile of Student's t with d = 1 .. 15 degrees of freedom
+// (the textbook table).
+double t975(int d) {
+  static const double q[16] = {0.0,   12.706, 4.303, 3.182, 2.776, 2.571, 2.447, 2.365,
+                               2.306, 2.262,  2.228, 2.201, 2.179, 2.160, 2.145, 2.131};
+  return d < 1 ? 0.0 : q[d < 15 ? d : 15];
+}
+
+// One timed run of arm (index, method) on n users: returns the device
+// seconds, and for Maximus the stage times of the run.
+mips_status time_arm(mips_index_t idx, int method, const float* users, int64_t n, int K, int32_t* oi, double* os,
+                     cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, double* secs, mips_stats* st_out) {
+  for (int i = 0; i < kStages; ++i) idx->stage_ran[i] = false;
+  idx->n_order = 0;
+  idx->last_stage = -1;
+  MIPS_CUDA(cudaEventRecord(e0, s));
+  MIPS_CUDA(cudaEventRecord(idx->ev[0], s));
+  mips_status st = method == 1 ? run_maximus(idx, users, n, K, oi, os, s) : run_bmm(idx, users, n, K, oi, os, s);
+  if (st != MIPS_OK) return st;
+  MIPS_CUDA(cudaEventRecord(e1, s));
+  MIPS_CUDA(cudaEventSynchronize(e1));
+  *secs = elapsed_ms(e0, e1) * 1e-3;
+  if (st_out) return mips_get_stats(idx, st_out);
+  return MIPS_OK;
+}
+
+mips_status run_select_arms(const mips_index_t* ix, int n_ix, const float* users, int64_t n_users, int K,
+                            int max_rounds, int32_t* out_idx, double* out_score, cudaStream_t s,
+                            mips_arms_report* rep) {
+  mips_index_t idx0 = ix[0];
+  const int f = idx0->f;
+  const int rounds_max = max_rounds <= 0 ? 6 : max_rounds;
+  // the sample: as mips_select's (the requested fraction, at least two waves
+  // of user tiles per SM, seeded affine split)
+  const int64_t floor_users = 2ll * idx0->num_sms * 128;
+  int64_t ns = (int64_t)ceil(idx0->opt.sample_frac * (double)n_users);
+  if (ns < floor_users) ns = floor_users;
+  if (ns > n_users) ns = n_users;
+  uint64_t a = 1, b = 0;
+  affine_sample(n_users, idx0->opt.seed ^ 0x5EEDull, &a, &b);
+  const int64_t nr = n_users - ns;
+  const int n_arms = 2 * n_ix;
+  Arena& w = idx0->ws_sel;
+  w.reset();
+  size_t o_keys = w.take(4 * n_users), o_ids = w.take(4 * n_users), o_keys2 = w.take(4 * n_users),
+         o_ids2 = w.take(4 * n_users), o_tmp = w.take(radix_sort_temp_bytes(n_users, 1));
+  size_t o_su = w.take(sizeof(float) * ns * f), o_ru = w.take(sizeof(float) * (nr > 0 ? nr : 1) * f);
+  size_t o_ri = w.take(4 * (nr > 0 ? nr : 1) * K), o_rs = w.take(8 * (nr > 0 ? nr : 1) * K);
+  size_t o_ai[MIPS_MAX_ARMS], o_as[MIPS_MAX_ARMS];
+  for (int k = 0; k < n_arms; ++k) {
+    o_ai[k] = w.take(4 * ns * K);
+    o_as[k] = w.take(8 * ns * K);
+  }
+  MIPS_CUDA(w.ensure(w.used, s));
+  uint32_t* keys = w.at<uint32_t>(o_keys);
+  int32_t* ids = w.at<int32_t>(o_ids);
+  uint32_t* keys2 = w.at<uint32_t>(o_keys2);
+  int32_t* ids2 = w.at<int32_t>(o_ids2);
+  launch_sample_keys(n_users, a, b, ns, keys, ids, s);
+  MIPS_CUDA(radix_sort_pairs(keys, ids, keys2, ids2, n_users, 1, 0, 8, w.at<uint32_t>(o_tmp), s, nullptr));
+  const int32_t* sample_ids = ids;
+  const int32_t* rest_ids = ids + ns;
+  launch_gather_rows(users, sample_ids, ns, f, w.at<float>(o_su), s);
+  if (nr > 0) launch_gather_rows(users, rest_ids, nr, f, w.at<float>(o_ru), s);
+  MIPS_CUDA(cudaGetLastError());
+
+  cudaEvent_t ev[4];
+  for (auto& x : ev) MIPS_CUDA(cudaEventCreate(&x));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+    }
+  } eg{ev};
+  MIPS_CUDA(cudaEventRecord(ev[2], s));
+  mips_arms_report r{};
+  r.n_arms = n_arms;
+  r.sample_users = ns;
+  std::vector<std::vector<double>> est(n_arms);
+  mips_status st;
+  // one untimed run per arm first: workspace growth and first-launch costs
+  // are not the arm's
+  for (int k = 0; k < n_arms; ++k) {
+    double t;
+    if ((st = time_arm(ix[k / 2], k & 1, w.at<float>(o_su), ns, K, w.at<int32_t>(o_ai[k]), w.at<double>(o_as[k]), s,
+                       ev[0], ev[1], &t, nullptr)) != MIPS_OK)
+      return st;
+  }
+  auto mean_of = [&](int k) {
+    double m = 0.0;
+    for (double x : est[k]) m += x;
+    return m / (double)est[k].size();
+  };
+  auto ci_of = [&](int k) {
+    const int n = (int)est[k].size();
+    if (n < 2) return 0.0;
+    const double m = mean_of(k);
+    double v = 0.0;
+    for (double x : est[k]) v += (x - m) * (x - m);
+    return t975(n - 1) * sqrt(v / (double)(n - 1)) / sqrt((double)n);
+  };
+  for (int rd = 0; rd < rounds_max; ++rd) {
+    for (int k = 0; k < n_arms; ++k) {
+      if (r.arm[k].dropped) continue;
+      mips_index_t ik = ix[k / 2];
+      const int method = k & 1;
+      double t = 0.0;
+      mips_stats ms{};
+      if ((st = time_arm(ik, method, w.at<float>(o_su), ns, K, w.at<int32_t>(o_ai[k]), w.at<double>(o_as[k]), s,
+                         ev[0], ev[1], &t, method == 1 ? &ms : nullptr)) != MIPS_OK)
+        return st;
+      r.t_sample += t;
+      double e;
+      if (method == 1) {  // construction: k-means grows with the users, bounds and sort do not
+        const double c_i = (ms.ms_kmeans * (double)n_users / (double)ns + ms.ms_bounds + ms.ms_sort) * 1e-3;
+        const double q_i = (t - (ms.ms_kmeans + ms.ms_bounds + ms.ms_sort) * 1e-3) / (double)ns;
+        e = c_i + (double)n_users * q_i;
+      } else {
+        e = t * (double)n_users / (double)ns;
+      }
+      est[k].push_back(e);
+      r.arm[k].rounds = (int)est[k].size();
+    }
+    r.rounds = rd + 1;
+    if (rd + 1 < 3) continue;
+    int best = -1;
+    for (int k = 0; k < n_arms; ++k)
+      if (!r.arm[k].dropped && (best < 0 || mean_of(k) < mean_of(best))) best = k;
+    const double hi_best = mean_of(best) + ci_of(best);
+    bool all_sep = true;
+    for (int k = 0; k < n_arms; ++k) {
+      if (k == best || r.arm[k].dropped) continue;
+      if (mean_of(k) - ci_of(k) > hi_best) r.arm[k].dropped = 1;
+      else all_sep = false;
+    }
+    if (all_sep) {
+      r.separated = 1;
+      break;
+    }
+  }
+  int choice = 0;
+  for (int k = 0; k < n_arms; ++k) {
+    mips_arm_report& ar = r.arm[k];
+    ar.index = k / 2;
+    ar.dtype = ix[k / 2]->opt.dtype;
+    ar.method = k & 1;
+    ar.est_mean = mean_of(k);
+    ar.est_ci = ci_of(k);
+  }
+  for (int k = 1; k < n_arms; ++k)
+    if (r.arm[k].est_mean < r.arm[choice].est_mean) choice = k;
+  r.choice = choice;
+  // the chosen arm's sample results (every arm is exact), then the rest with it
+  launch_scatter_topk(w.at<int32_t>(o_ai[choice]), w.at<double>(o_as[choice]), sample_ids, ns, K, out_idx,
+                      out_score, s);
+  mips_index_t ic = ix[choice / 2];
+  if (nr > 0) {
+    double t;
+    if ((st = time_arm(ic, choice & 1, w.at<float>(o_ru), nr, K, w.at<int32_t>(o_ri), w.at<double>(o_rs), s, ev[0],
+                       ev[1], &t, nullptr)) != MIPS_OK)
+      return st;
+    launch_scatter_topk(w.at<int32_t>(o_ri), w.at<double>(o_rs), rest_ids, nr, K, out_idx, out_score, s);
+  }
+  MIPS_CUDA(cudaGetLastError());
+  MIPS_CUDA(cudaEventRecord(ev[3], s));
+  MIPS_CUDA(cudaEventSynchronize(ev[3]));
+  r.t_total = elapsed_ms(ev[2], ev[3]) * 1e-3;
+  for (int i = 0; i < n_ix; ++i) ix[i]->last_users = n_users;
+  if (rep) *rep = r;
+  return MIPS_OK;
+}
+
 mips_status check_call(mips_index_t idx, const void* users, int64_t n_users, int K, const void* oi,
                        const void* os) {
   if (!idx) return fail(MIPS_ERR_ARG, "null index");
@@ -1087,6 +1259,33 @@ mips_status mips_select(mips_index_t idx, const float* users_dev, int64_t n_user
   if ((st = begin_call(idx, s)) != MIPS_OK) return st;
   if ((st = run_select(idx, users_dev, n_users, K, out_idx_dev, out_score_dev, s, rep)) != MIPS_OK) return st;
   return end_call(idx, s);
+}
+
+mips_status mips_select_arms(const mips_index_t* indexes, int n_indexes, const float* users_dev, int64_t n_users,
+                             int K, int max_rounds, int32_t* out_idx_dev, double* out_score_dev, void* stream,
+                             mips_arms_report* rep) {
+  g_err.clear();
+  if (!indexes || n_indexes < 1 || n_indexes > MIPS_MAX_ARMS / 2)
+    return fail(MIPS_ERR_ARG, "n_indexes out of range [1,%d]", MIPS_MAX_ARMS / 2);
+  if (max_rounds != 0 && (max_rounds < 3 || max_rounds > 16)) return fail(MIPS_ERR_ARG, "max_rounds out of range");
+  mips_status st = check_call(indexes[0], users_dev, n_users, K, out_idx_dev, out_score_dev);
+  if (st != MIPS_OK) return st;
+  for (int i = 1; i < n_indexes; ++i) {
+    if (!indexes[i]) return fail(MIPS_ERR_ARG, "null index %d", i);
+    if (indexes[i]->f != indexes[0]->f || indexes[i]->n_items != indexes[0]->n_items ||
+        indexes[i]->device != indexes[0]->device)
+      return fail(MIPS_ERR_ARG, "index %d differs from index 0 in f, n_items or device", i);
+    if ((st = check_device(indexes[i])) != MIPS_OK) return st;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int i = 0; i < n_indexes; ++i)
+    if ((st = begin_call(indexes[i], s)) != MIPS_OK) return st;
+  if ((st = run_select_arms(indexes, n_indexes, users_dev, n_users, K, max_rounds, out_idx_dev, out_score_dev, s,
+                            rep)) != MIPS_OK)
+    return st;
+  for (int i = 0; i < n_indexes; ++i)
+    if ((st = end_call(indexes[i], s)) != MIPS_OK) return st;
+  return MIPS_OK;
 }
 
 mips_status mips_autotune(mips_index_t idx, const float* users_dev, int64_t n_users, int K, void* stream,

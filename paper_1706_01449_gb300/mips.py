@@ -5,7 +5,7 @@ device pointers (from torch tensors), sizes and the current CUDA stream
 through ctypes and turns status codes into exceptions.  There is no CPU
 fallback: if the library is missing or CUDA is unavailable, calls raise.
 
-Names follow the C ABI: build_index, topk, topk_maximus, select,
+Names follow the C ABI: build_index, topk, topk_maximus, select, select_arms,
 topk_host, sync, get_stats, get_buffer, free_index, last_error.
 """
 from __future__ import annotations
@@ -29,7 +29,7 @@ EXPORTS = ("mips_default_options", "mips_build_index", "mips_topk", "mips_topk_m
            "mips_select", "mips_topk_host", "mips_sync", "mips_get_stats", "mips_get_buffer",
            "mips_free_index", "mips_last_error", "mips_version", "mips_topk_noalloc", "mips_topk_graph",
            "mips_autotune", "mips_server_create", "mips_server_submit", "mips_server_wait",
-           "mips_server_destroy", "mips_fit_clusters", "mips_test_expire_next_wait")
+           "mips_server_destroy", "mips_fit_clusters", "mips_test_expire_next_wait", "mips_select_arms")
 
 
 class MipsError(RuntimeError):
@@ -55,6 +55,30 @@ class SelectReport(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+MAX_ARMS = 16
+
+
+class ArmReport(ctypes.Structure):
+    """mips_arm_report: one (index dtype, method) arm of mips_select_arms."""
+    _fields_ = [("index", ctypes.c_int), ("dtype", ctypes.c_int), ("method", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("est_mean", ctypes.c_double), ("est_ci", ctypes.c_double), ("dropped", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ArmsReport(ctypes.Structure):
+    """mips_arms_report: the multi-arm selector's timings and choice."""
+    _fields_ = [("n_arms", ctypes.c_int), ("arm", ArmReport * MAX_ARMS), ("choice", ctypes.c_int),
+                ("separated", ctypes.c_int), ("rounds", ctypes.c_int), ("sample_users", ctypes.c_int64),
+                ("t_sample", ctypes.c_double), ("t_total", ctypes.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "arm"}
+        d["arms"] = [self.arm[i].as_dict() for i in range(self.n_arms)]
+        return d
 
 
 class TuneReport(ctypes.Structure):
@@ -120,6 +144,8 @@ def load():
     lib.mips_fit_clusters.restype = st
     lib.mips_select.argtypes = [P, P, i64, i32, P, P, P, ctypes.POINTER(SelectReport)]
     lib.mips_select.restype = st
+    lib.mips_select_arms.argtypes = [ctypes.POINTER(P), i32, P, i64, i32, i32, P, P, P, ctypes.POINTER(ArmsReport)]
+    lib.mips_select_arms.restype = st
     lib.mips_topk_host.argtypes = [P, P, i64, i32, i32, P, P, P]
     lib.mips_topk_host.restype = st
     lib.mips_topk_graph.argtypes = [P, P, i64, i32, i32, P, P, P]
@@ -308,6 +334,20 @@ def select(index: Index, users, K: int, out_idx=None, out_score=None, stream=Non
     _check(lib.mips_select(index.handle, ctypes.c_void_p(users.data_ptr()), users.shape[0], K,
                            ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
                            _stream_ptr(stream), ctypes.byref(rep)))
+    return out_idx, out_score, rep.as_dict()
+
+
+def select_arms(indexes, users, K: int, max_rounds: int = 0, out_idx=None, out_score=None, stream=None):
+    """Multi-arm selector (mips_select_arms) over indexes built on the same
+    items: returns (idx, score, report dict)."""
+    lib = load()
+    users = _dev_f32(users, "users")
+    out_idx, out_score = _outputs(users.shape[0], K, out_idx, out_score, users.device)
+    handles = (ctypes.c_void_p * len(indexes))(*[ix.handle.value for ix in indexes])
+    rep = ArmsReport()
+    _check(lib.mips_select_arms(handles, len(indexes), ctypes.c_void_p(users.data_ptr()), users.shape[0], K,
+                                max_rounds, ctypes.c_void_p(out_idx.data_ptr()), ctypes.c_void_p(out_score.data_ptr()),
+                                _stream_ptr(stream), ctypes.byref(rep)))
     return out_idx, out_score, rep.as_dict()
 
 
