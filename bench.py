@@ -402,7 +402,8 @@ def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk,
     kms = stats["ms_kernel"] or (stats["ms_walk"] if walked else stats["ms_score"])
     kern = "tc_score_select" if dtype in ("bf16", "fp8") else ("fp32_score_select" if not walked else "maximus_walk")
     key = f"{kern}{' walk' if walked else ''} {dtype} {workload} f={f} K={K}"
-    src = ["tc_topk.cu"] if dtype == "bf16" else ["fp32_topk.cu" if not walked else "maximus.cu"]
+    src = (["tc_topk.cu", "tc_ptx.cuh", "tc_topk.h"] if dtype in ("bf16", "fp8")
+           else ["fp32_topk.cu" if not walked else "maximus.cu"])
     return roofline(dtype, f, scores, kms, hbm, peaks, peak_src, sm, clk, key, src)
 
 
