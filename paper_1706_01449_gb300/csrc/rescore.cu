@@ -44,6 +44,23 @@ __device__ __forceinline__ bool ranks_before(double sa, int ia, double sb, int i
   return sa > sb || (sa == sb && ia < ib);
 }
 
+// Order-preserving 64-bit integer key of a finite double (a larger value has
+// a larger key, and both zeros the key of +0, so equal values keep equal
+// keys): the select's heap ranks with integer compares, as GB300's FP64
+// rate is a small fraction of its integer rate.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ull) b = 0ull;  // -0 -> +0
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_value(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ bool key_before(unsigned long long ka, int ia, unsigned long long kb, int ib) {
+  return ka > kb || (ka == kb && ia < ib);
+}
+
 // Relative score error bound used by the tie check (see the file comment).
 // K-th largest value of the union of m rows of K values, each row sorted
 // descending (m <= kMaxLists): K rounds of taking the largest row head.
@@ -62,6 +79,26 @@ __device__ __forceinline__ float union_kth(const float* __restrict__ rows, int m
       }
     v = bv;
     ++head[best];
+  }
+  return v;
+}
+
+// The same for two rows (a user's two sub-lists), in registers.
+__device__ __forceinline__ float union2_kth(const float* __restrict__ rows, int K) {
+  const float* a = rows;
+  const float* b = rows + K;
+  int ia = 0, ib = 0;
+  float v = __int_as_float(0xff800000);
+  for (int r = 0; r < K; ++r) {
+    const float x = ia < K ? a[ia] : __int_as_float(0xff800000);
+    const float y = ib < K ? b[ib] : __int_as_float(0xff800000);
+    if (x >= y) {
+      v = x;
+      ++ia;
+    } else {
+      v = y;
+      ++ib;
+    }
   }
   return v;
 }
@@ -147,6 +184,35 @@ __device__ __forceinline__ double score_dot2(const float* __restrict__ u, const 
   return dot2_value(acc);
 }
 
+// The same compensated dot with the item row v read 16 bytes at a time: the
+// elements before v's first 16-byte boundary one by one, then eight at a
+// time from two float4 loads, then the rest; the user row element by element
+// (a thread's neighbours score other items of the same users, so its lines
+// are shared).  Same terms in the same order k = 0, 1, ... as score_dot2.
+__device__ __forceinline__ double score_dot2_v4(const float* __restrict__ u, const float* __restrict__ v, int f) {
+  Dot2 acc{0.f, 0.f};
+  int k = 0;
+  const int peel = (int)(((16u - ((unsigned)reinterpret_cast<uintptr_t>(v) & 15u)) & 15u) >> 2);
+  for (; k < peel && k < f; ++k) dot2_step(acc, u[k], v[k]);
+  for (; k + 8 <= f; k += 8) {
+    const float4 b0 = *reinterpret_cast<const float4*>(v + k);
+    const float4 b1 = *reinterpret_cast<const float4*>(v + k + 4);
+    float a[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = u[k + j];
+    dot2_step(acc, a[0], b0.x);
+    dot2_step(acc, a[1], b0.y);
+    dot2_step(acc, a[2], b0.z);
+    dot2_step(acc, a[3], b0.w);
+    dot2_step(acc, a[4], b1.x);
+    dot2_step(acc, a[5], b1.y);
+    dot2_step(acc, a[6], b1.z);
+    dot2_step(acc, a[7], b1.w);
+  }
+  for (; k < f; ++k) dot2_step(acc, u[k], v[k]);
+  return dot2_value(acc);
+}
+
 // Sequential FP64 sum of the exact products (the definition's arithmetic),
 // with the loads of 8 terms issued before their arithmetic.
 __device__ __forceinline__ double score_f64(const float* __restrict__ u, const float* __restrict__ v, int f) {
@@ -170,45 +236,46 @@ __device__ __forceinline__ double score_f64(const float* __restrict__ u, const f
 // column (entry p at [p * T + t]); the root is the key that ranks last, so a
 // new key that ranks before the root replaces it.
 struct KeyHeap {
-  double* s;
+  unsigned long long* s;  // dkey of the score
   int* id;
   int T;
-  __device__ __forceinline__ double sv(int p) const { return s[p * T]; }
+  __device__ __forceinline__ unsigned long long sv(int p) const { return s[p * T]; }
   __device__ __forceinline__ int iv(int p) const { return id[p * T]; }
-  __device__ __forceinline__ void put(int p, double v, int i) {
+  __device__ __forceinline__ void put(int p, unsigned long long v, int i) {
     s[p * T] = v;
     id[p * T] = i;
   }
-  // worse(a, b): a ranks after b
-  __device__ __forceinline__ void sift_down(int p, int n, double v, int i) {
+  // key_before(a, b): a ranks before b
+  __device__ __forceinline__ void sift_down(int p, int n, unsigned long long v, int i) {
     while (true) {
       int c = 2 * p + 1;
       if (c >= n) break;
-      if (c + 1 < n && ranks_before(sv(c), iv(c), sv(c + 1), iv(c + 1))) ++c;  // the worse child
-      if (!ranks_before(v, i, sv(c), iv(c))) break;  // v is already worse than both children
+      if (c + 1 < n && key_before(sv(c), iv(c), sv(c + 1), iv(c + 1))) ++c;  // the worse child
+      if (!key_before(v, i, sv(c), iv(c))) break;  // v is already worse than both children
       put(p, sv(c), iv(c));
       p = c;
     }
     put(p, v, i);
   }
-  __device__ __forceinline__ void push(int& n, int L, double v, int i) {
+  __device__ __forceinline__ void push(int& n, int L, double score, int i) {
+    const unsigned long long v = dkey(score);
     if (n < L) {
       int p = n++;
       while (p > 0) {
         const int q = (p - 1) / 2;
-        if (!ranks_before(sv(q), iv(q), v, i)) break;  // parent already worse
+        if (!key_before(sv(q), iv(q), v, i)) break;  // parent already worse
         put(p, sv(q), iv(q));
         p = q;
       }
       put(p, v, i);
-    } else if (ranks_before(v, i, sv(0), iv(0))) {
+    } else if (key_before(v, i, sv(0), iv(0))) {
       sift_down(0, n, v, i);
     }
   }
   // In place: entries 0..n-1 best first.
   __device__ __forceinline__ void sort(int n) {
     for (int m = n - 1; m > 0; --m) {
-      const double v = sv(m);
+      const unsigned long long v = sv(m);
       const int i = iv(m);
       put(m, sv(0), iv(0));  // the worst of 0..m goes to m
       sift_down(0, m, v, i);
@@ -250,7 +317,8 @@ __global__ void __launch_bounds__(256)
       // largest lower bounds (distinct items, each row descending) the K-th
       // largest of their union is too, and the tightest
       for (int l = 0; l < o.lists; ++l) tau = l == 0 ? o.tau[l0] : fmaxf(tau, o.tau[l0 + l]);
-      if (o.lists > 1 && o.topl && o.topl_sorted) tau = fmaxf(tau, union_kth(o.topl + l0 * K, o.lists, K));
+      if (o.lists > 1 && o.topl && o.topl_sorted)
+        tau = fmaxf(tau, o.lists == 2 ? union2_kth(o.topl + l0 * K, K) : union_kth(o.topl + l0 * K, o.lists, K));
       o.tau_final[2 * u] = tau;
       live = true;
       for (int l = 0; l < o.lists; ++l) {
@@ -312,7 +380,9 @@ __global__ void __launch_bounds__(256)
       o.cand_sc[slot] = 0.0;
       continue;
     }
-    o.cand_sc[slot] = score_dot2(users + u * f, items + (int64_t)pos * f, f);
+    const float* ur = users + u * f;
+    const float* ir = items + (int64_t)pos * f;
+    o.cand_sc[slot] = pairs_ok(ur, ir, f) ? score_dot2(ur, ir, f) : score_dot2_v4(ur, ir, f);
   }
 }
 
@@ -328,7 +398,7 @@ __global__ void __launch_bounds__(128)
   extern __shared__ unsigned char smem_raw[];
   const int T = blockDim.x, t = threadIdx.x;
   const int L = K + 1;  // the K best and the best of the rest
-  double* ls = reinterpret_cast<double*>(smem_raw);  // [L][T]
+  unsigned long long* ls = reinterpret_cast<unsigned long long*>(smem_raw);  // [L][T] score keys
   int* li = reinterpret_cast<int*>(ls + (size_t)L * T);
   const int64_t u = (int64_t)blockIdx.x * T + t;
   unsigned long long n_fp64 = 0;
@@ -371,13 +441,13 @@ __global__ void __launch_bounds__(128)
         if (mode == 1) break;
         const double e2 = 2.0 * rel_e * nu * (double)nmax + rescore_abs_err(f);
         bool amb = false;
-        for (int p = 0; p + 1 < cnt; ++p) amb |= (ls[p * T + t] - ls[(p + 1) * T + t]) <= e2;
+        for (int p = 0; p + 1 < cnt; ++p) amb |= (dkey_value(ls[p * T + t]) - dkey_value(ls[(p + 1) * T + t])) <= e2;
         if (!amb) break;
         ++n_fp64;
       }
       for (int k = 0; k < K; ++k) {
         out_idx[u * K + k] = li[k * T + t];
-        out_score[u * K + k] = ls[k * T + t];
+        out_score[u * K + k] = dkey_value(ls[k * T + t]);
       }
     }
   }
