@@ -1,4 +1,4 @@
-// Fused BF16 blocked multiply + top-K candidate select on tcgen05 tensor
+// Fused BF16 / FP8 blocked multiply + top-K candidate select on tcgen05 tensor
 // cores (the paper's BMM, Sec. II-C, with the per-user selection fused so
 // the |U| x |I| score matrix never leaves the SM), and the same machinery
 // walking Maximus's per-cluster item lists (Sec. III, Algorithm 1).
@@ -25,7 +25,8 @@
 //               tile a bulk copy of its bound columns (and, for list walks,
 //               its item positions) into a small ring the select warps read;
 //   warp 9      MMA issuer (one thread): D = A . B^T with tcgen05.mma
-//               kind::f16 (BF16 x BF16 -> FP32) into one of two TMEM
+//               kind::f16 (BF16 x BF16 -> FP32) or kind::f8f6f4 (E4M3 x
+//               E4M3 -> FP32, entries scaled by s_u s_I) into one of two TMEM
 //               accumulators of 128 lanes x 256 columns, so the MMAs of item
 //               tile j+1 overlap the select of tile j.
 // The select's common case is one max-reducing TMEM load per 64 scores
@@ -44,6 +45,8 @@
 // bounded wait), and TMEM is freed before exit.
 #include <cuda.h>
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "common.cuh"
 #include "tc_ptx.cuh"
@@ -413,6 +416,55 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
   }
 }
 
+// A fresh work item's first item tile, after its seed: every column whose
+// upper bound reaches the filter threshold becomes a candidate.  The seed
+// already took the tile's lower bounds into the top-K, so nothing is
+// inserted and the threshold does not move during the pass: a hit is only
+// stored (position, H), without the offer's lower bound and insertion.
+// Only the 16-column groups of the 64-column halves with a hit in the warp
+// (`halves`) are read again.
+template <int KR, bool MX>
+__device__ __forceinline__ void emit_tile(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid, int32_t pos0,
+                                          const int32_t* pos, unsigned halves) {
+  float* const stage = c.qh();
+  const float t = s.tau_eff;
+#pragma unroll 1
+  for (int gi = 0; gi < kHalfN / 16; ++gi) {
+    if (!((halves >> (gi >> 2)) & 1u)) continue;  // warp-uniform
+    uint32_t v[16];
+    const float mg = hv(s, c, tmem_ldmax16(taddr + 16 * gi, v));
+    const bool hit = mg >= t;
+    if (!__any_sync(kFull, hit)) continue;
+    const int col0 = 16 * gi;
+    unsigned mask = 0;
+    if (hit) {
+      const int nv = valid - col0;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float x = hv(s, c, __uint_as_float(v[q]));
+        stage[q * kEpiThreads] = x;
+        mask |= (x >= t && q < nv) ? (1u << q) : 0u;
+      }
+    }
+    int n = s.n_cand;
+    while (mask) {
+      const int q = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int32_t ip = MX ? pos[col0 + q] : pos0 + col0 + q;
+      if (ip < 0 || ip >= c.n_items) {  // never for consistent lists: flag it rather than emit it
+        atomicOr(c.err, DEV_ERR_INTERNAL);
+        continue;
+      }
+      if (n < c.cap) {
+        c.cand_pos[n] = ip;
+        c.cand_ub[n] = stage[q * kEpiThreads];
+      }
+      ++n;
+    }
+    s.n_cand = n;
+  }
+}
+
 struct WorkItem {
   int a_row;   // first A row of the user tile
   int b_row;   // B row of list rank 0
@@ -666,72 +718,63 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         atomicOr(err, DEV_ERR_INTERNAL);
         ok_init = false;
       }
-      long long g = 0;
-      int st = 0;
-      uint32_t ph = 0;   // ring pass parity
-      int b = 0;         // accumulator of tile g
-      uint32_t aph = 0;  // accumulator pass parity
-      bool ok = ok_init;
-      for (int lt = 0; ok; ++lt) {
-        const int slot = lt % kWQ;
-        ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), gd);
-        if (!ok) break;
-        const int wi = *(volatile int*)&ctl->wq[slot];
-        mbar_arrive(&ctl->wq_empty[slot]);
-        if (wi >= n_work) break;
-        const WorkItem wk = get_work<MX>(p, wi, n_it);
-        ok = mbar_wait(&ctl->a_full, lt & 1, gd);
-        if (!ok) break;
-        tc_fence_after();
-        for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
-          for (int h = 0; h < bs && ok; ++h) {
-            ok = mbar_wait(&ctl->b_full[st], ph, gd);
-            if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, gd);
-            if (!ok) break;
-            tc_fence_after();
-            // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
-            const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
-            const uint64_t boff = (uint64_t)(st * stage16);
-            if (f8) {
-              switch (nst) {
-                case 1: mma_steps<1, true>(d, a_d, b_d, boff, idesc); break;
-                case 2: mma_steps<2, true>(d, a_d, b_d, boff, idesc); break;
-                case 3: mma_steps<3, true>(d, a_d, b_d, boff, idesc); break;
-                case 4: mma_steps<4, true>(d, a_d, b_d, boff, idesc); break;
-                case 5: mma_steps<5, true>(d, a_d, b_d, boff, idesc); break;
-                case 6: mma_steps<6, true>(d, a_d, b_d, boff, idesc); break;
-                case 7: mma_steps<7, true>(d, a_d, b_d, boff, idesc); break;
-                case 8: mma_steps<8, true>(d, a_d, b_d, boff, idesc); break;
-                case 9: mma_steps<9, true>(d, a_d, b_d, boff, idesc); break;
-                default: mma_steps<10, true>(d, a_d, b_d, boff, idesc); break;
-              }
-            } else {
-              switch (nst) {
-                case 1: mma_steps<1>(d, a_d, b_d, boff, idesc); break;
-                case 2: mma_steps<2>(d, a_d, b_d, boff, idesc); break;
-                case 3: mma_steps<3>(d, a_d, b_d, boff, idesc); break;
-                case 4: mma_steps<4>(d, a_d, b_d, boff, idesc); break;
-                case 5: mma_steps<5>(d, a_d, b_d, boff, idesc); break;
-                case 6: mma_steps<6>(d, a_d, b_d, boff, idesc); break;
-                case 7: mma_steps<7>(d, a_d, b_d, boff, idesc); break;
-                case 8: mma_steps<8>(d, a_d, b_d, boff, idesc); break;
-                case 9: mma_steps<9>(d, a_d, b_d, boff, idesc); break;
-                default: mma_steps<10>(d, a_d, b_d, boff, idesc); break;
-              }
-            }
-            mma_commit(&ctl->b_empty[st]);
-            if (++st == p.stages) {
-              st = 0;
-              ph ^= 1u;
-            }
-          }
+      // the issue loop, once per operand type (no type branch per load)
+      auto issue_loop = [&](auto f8_tag) {
+        constexpr bool F8 = decltype(f8_tag)::value;
+        long long g = 0;
+        int st = 0;
+        uint32_t ph = 0;   // ring pass parity
+        int b = 0;         // accumulator of tile g
+        uint32_t aph = 0;  // accumulator pass parity
+        bool ok = ok_init;
+        for (int lt = 0; ok; ++lt) {
+          const int slot = lt % kWQ;
+          ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), gd);
           if (!ok) break;
-          mma_commit(&ctl->acc_full[b]);
-          b ^= 1;
-          if (b == 0) aph ^= 1u;
+          const int wi = *(volatile int*)&ctl->wq[slot];
+          mbar_arrive(&ctl->wq_empty[slot]);
+          if (wi >= n_work) break;
+          const WorkItem wk = get_work<MX>(p, wi, n_it);
+          ok = mbar_wait(&ctl->a_full, lt & 1, gd);
+          if (!ok) break;
+          tc_fence_after();
+          for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
+            for (int h = 0; h < bs && ok; ++h) {
+              ok = mbar_wait(&ctl->b_full[st], ph, gd);
+              if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, gd);
+              if (!ok) break;
+              tc_fence_after();
+              // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
+              const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
+              const uint64_t boff = (uint64_t)(st * stage16);
+              switch (nst) {
+                case 1: mma_steps<1, F8>(d, a_d, b_d, boff, idesc); break;
+                case 2: mma_steps<2, F8>(d, a_d, b_d, boff, idesc); break;
+                case 3: mma_steps<3, F8>(d, a_d, b_d, boff, idesc); break;
+                case 4: mma_steps<4, F8>(d, a_d, b_d, boff, idesc); break;
+                case 5: mma_steps<5, F8>(d, a_d, b_d, boff, idesc); break;
+                case 6: mma_steps<6, F8>(d, a_d, b_d, boff, idesc); break;
+                case 7: mma_steps<7, F8>(d, a_d, b_d, boff, idesc); break;
+                case 8: mma_steps<8, F8>(d, a_d, b_d, boff, idesc); break;
+                case 9: mma_steps<9, F8>(d, a_d, b_d, boff, idesc); break;
+                default: mma_steps<10, F8>(d, a_d, b_d, boff, idesc); break;
+              }
+              mma_commit(&ctl->b_empty[st]);
+              if (++st == p.stages) {
+                st = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
+            mma_commit(&ctl->acc_full[b]);
+            b ^= 1;
+            if (b == 0) aph ^= 1u;
+          }
+          if (ok) mma_commit(&ctl->a_empty);
         }
-        if (ok) mma_commit(&ctl->a_empty);
-      }
+      };
+      if (f8) issue_loop(std::true_type{});
+      else issue_loop(std::false_type{});
       // all MMAs issued by this thread complete before TMEM is released
       mma_commit(&ctl->drain);
       mbar_drain(&ctl->drain, 0);
@@ -827,7 +870,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const int32_t rank0 = j * kTileN + c2 * kHalfN;  // (list) rank of this thread's first column
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
-        if (first) {
+        if (__builtin_expect(first, 0)) {  // (rare paths marked so the common case stays compact)
           ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
           if (!ok) break;
           aux_ready = true;
@@ -848,13 +891,14 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           const float m = hv(s, c, tmem_ldmax64(taddr + 64 * h));
           halves |= __any_sync(kFull, m >= s.tau_eff) ? (1u << h) : 0u;
         }
-        if (halves) {
+        if (__builtin_expect(halves != 0u, 0)) {
           slow += __popc(halves);
           if (!aux_ready) {
             ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
             if (!ok) break;
           }
-          select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves, first);
+          if (first) emit_tile<KR, MX>(s, c, taddr, valid, rank0, pos, halves);
+          else select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves, false);
         }
         tc_fence_before();
         __syncwarp();
