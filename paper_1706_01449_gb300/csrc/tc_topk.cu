@@ -92,7 +92,7 @@ struct TcUser {
   int n_cand;
   int ut;         // current work item (tag of the published threshold)
   float beta_u, nhat_u;  // bound columns of this user (prep.cu)
-  float au;              // FP8: user_scale[u] * item_scale, the accumulator's unit
+  float au, am;          // FP8: user_scale[u] * item_scale (the accumulator's unit) and 2^-21; BF16: 1 and 0
   float d[KR > 0 ? KR : 1];
 };
 
@@ -130,14 +130,14 @@ struct TcSel {
 
 // An accumulator entry in input units: BF16 entries are scores already;
 // FP8 entries count in units of au = s_u s_I.  The scaled value gets an
-// upward margin of 2^-21 of its size for the roundings of au and of the
+// upward margin am = 2^-21 of its size for the roundings of au and of the
 // product (2^-24 each), so it stays an upper bound; the map is increasing,
-// so the maximum of scaled entries is the scaled maximum.
+// so the maximum of scaled entries is the scaled maximum.  No branch: BF16
+// threads hold au = 1 and am = 0, which return the entry itself.
 template <int KR>
-__device__ __forceinline__ float hv(const TcUser<KR>& s, const TcSel& c, float raw) {
-  if (!c.f8) return raw;
+__device__ __forceinline__ float hv(const TcUser<KR>& s, const TcSel&, float raw) {
   const float t = s.au * raw;
-  return __fmaf_rn(fabsf(t), 4.76837158203125e-07f, t);  // 2^-21
+  return __fmaf_rn(fabsf(t), s.am, t);
 }
 
 template <int KR>
@@ -426,43 +426,37 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
 template <int KR, bool MX>
 __device__ __forceinline__ void emit_tile(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid, int32_t pos0,
                                           const int32_t* pos, unsigned halves) {
-  float* const stage = c.qh();
   const float t = s.tau_eff;
+  int n = s.n_cand;
+  bool bad = false;
 #pragma unroll 1
   for (int gi = 0; gi < kHalfN / 16; ++gi) {
     if (!((halves >> (gi >> 2)) & 1u)) continue;  // warp-uniform
     uint32_t v[16];
     const float mg = hv(s, c, tmem_ldmax16(taddr + 16 * gi, v));
-    const bool hit = mg >= t;
-    if (!__any_sync(kFull, hit)) continue;
+    if (!__any_sync(kFull, mg >= t)) continue;
     const int col0 = 16 * gi;
-    unsigned mask = 0;
-    if (hit) {
-      const int nv = valid - col0;
+    const int nv = valid - col0;
+    // every column in turn, each store under its own predicate: the lanes
+    // stay together however their hits are spread
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const float x = hv(s, c, __uint_as_float(v[q]));
-        stage[q * kEpiThreads] = x;
-        mask |= (x >= t && q < nv) ? (1u << q) : 0u;
-      }
-    }
-    int n = s.n_cand;
-    while (mask) {
-      const int q = __ffs(mask) - 1;
-      mask &= mask - 1;
+    for (int q = 0; q < 16; ++q) {
+      const float x = hv(s, c, __uint_as_float(v[q]));
+      const bool hit = x >= t && q < nv;
       const int32_t ip = MX ? pos[col0 + q] : pos0 + col0 + q;
-      if (ip < 0 || ip >= c.n_items) {  // never for consistent lists: flag it rather than emit it
-        atomicOr(c.err, DEV_ERR_INTERNAL);
-        continue;
-      }
-      if (n < c.cap) {
+      const bool in = ip >= 0 && ip < c.n_items;
+      bad |= hit && !in;
+      if (hit && in && n < c.cap) {
         c.cand_pos[n] = ip;
-        c.cand_ub[n] = stage[q * kEpiThreads];
+        c.cand_ub[n] = x;
       }
-      ++n;
+      n += (hit && in) ? 1 : 0;
     }
-    s.n_cand = n;
   }
+  // a position outside the item range is never written by consistent
+  // lists; were one met, it is flagged rather than emitted
+  if (bad) atomicOr(c.err, DEV_ERR_INTERNAL);
+  s.n_cand = n;
 }
 
 struct WorkItem {
@@ -818,6 +812,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       s.beta_u = 0.f;
       s.nhat_u = 0.f;
       s.au = 1.f;
+      s.am = c.f8 ? 4.76837158203125e-07f : 0.f;  // 2^-21
       const int lbase = (MX && p.work.l_base) ? p.work.l_base[wk.q] : 0;
       const int64_t list = (active ? u : 0) * (int64_t)o.lists + lbase + c2;
       const bool restoring = MX && p.work.restore && wk.tb > 0;
