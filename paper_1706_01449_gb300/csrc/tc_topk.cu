@@ -213,39 +213,40 @@ __device__ __forceinline__ void tc_publish(const TcUser<KR>& s, const TcSel& c) 
 
 // One hit: column col of the tile, whose staged upper bound H reached the
 // threshold when it was staged.  Threshold update from its lower bound,
-// then the candidate emission.  Lower bounds at or below the current filter
-// threshold cannot raise it and are not kept.  With emit_only (second pass
-// over a work item's first item tile, whose lower bounds already went
-// through the top-K) only the emission is done, so no item is counted twice.
-// The item's position is pos0 + col, or pos[col] for a walk of a cluster's
-// sorted list (MX).  The three loads (H, the item's bound columns, its
-// position) do not depend on one another and are issued first.
+// then the candidate emission; lower bounds at or below the current filter
+// threshold cannot raise it and are not kept.  The item's position is
+// pos0 + col, or pos[col] for a walk of a cluster's sorted list (MX).  The
+// three loads (H, the item's bound columns, its position) are issued first,
+// and only the rare threshold publication and the stores are conditional:
+// the register top-K takes the lower bound through its branch-free network
+// (-inf when it does not qualify, which changes nothing).
 template <int KR, bool MX>
 __device__ __forceinline__ void tc_offer(TcUser<KR>& s, const TcSel& c, const float* Hp, int col, const float2* aux,
-                                         int32_t pos0, const int32_t* pos, bool emit_only) {
+                                         int32_t pos0, const int32_t* pos) {
   const float H = *Hp;
   const float2 ia = aux[col];
   const int32_t ip = MX ? pos[col] : pos0 + col;
-  if (H < s.tau_eff) return;  // the threshold rose since the hit was staged
-  const float L = emit_only ? kNegInf : tc_lower(s, c, H, ia);
-  if (L > s.tau_eff) {
-    s.tau = topk_insert(s, c, L);
-    if (s.tau > s.tau_eff) {
-      s.tau_eff = s.tau;
-      tc_publish(s, c);
-    }
+  const bool live = H >= s.tau_eff;  // (the threshold may have risen since the hit was staged)
+  const float L = tc_lower(s, c, H, ia);
+  const bool ins = live && L > s.tau_eff;
+  if constexpr (KR > 0) {
+    topk_push(s, ins ? L : kNegInf);
+    s.tau = c.K == KR ? s.d[KR - 1] : topk_kth(s, c.K);
+  } else {
+    if (ins) s.tau = topk_insert(s, c, L);
   }
-  if (H >= s.tau_eff) {
-    if (ip < 0 || ip >= c.n_items) {  // never for consistent lists: flag it rather than emit it
-      atomicOr(c.err, DEV_ERR_INTERNAL);
-      return;
-    }
-    if (s.n_cand < c.cap) {
-      c.cand_pos[s.n_cand] = ip;
-      c.cand_ub[s.n_cand] = H;
-    }
-    ++s.n_cand;
+  if (s.tau > s.tau_eff) {
+    s.tau_eff = s.tau;
+    tc_publish(s, c);
   }
+  const bool em = live && H >= s.tau_eff;
+  const bool in = ip >= 0 && ip < c.n_items;
+  if (em && !in) atomicOr(c.err, DEV_ERR_INTERNAL);  // never for consistent lists: flagged, not emitted
+  if (em && in && s.n_cand < c.cap) {
+    c.cand_pos[s.n_cand] = ip;
+    c.cand_ub[s.n_cand] = H;
+  }
+  s.n_cand += (em && in) ? 1 : 0;
 }
 
 // Seed step of the heap-held top-K for 8 columns col0.. of the first item
@@ -386,8 +387,7 @@ __device__ __forceinline__ bool seed_try_merge(TcUser<KR>& s, const TcSel& c, in
 // bit; no queue counter to wait on).
 template <int KR, bool MX>
 __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint32_t taddr, int valid,
-                                            const float2* aux, int32_t pos0, const int32_t* pos, unsigned halves,
-                                            bool emit_only) {
+                                            const float2* aux, int32_t pos0, const int32_t* pos, unsigned halves) {
   float* const stage = c.qh();
 #pragma unroll 1
   for (int gi = 0; gi < kHalfN / 16; ++gi) {
@@ -411,7 +411,7 @@ __device__ __forceinline__ void select_hits(TcUser<KR>& s, const TcSel& c, uint3
     while (mask) {
       const int q = __ffs(mask) - 1;
       mask &= mask - 1;
-      tc_offer<KR, MX>(s, c, stage + q * kEpiThreads, col0 + q, aux, pos0, pos, emit_only);
+      tc_offer<KR, MX>(s, c, stage + q * kEpiThreads, col0 + q, aux, pos0, pos);
     }
   }
 }
@@ -893,7 +893,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             if (!ok) break;
           }
           if (first) emit_tile<KR, MX>(s, c, taddr, valid, rank0, pos, halves);
-          else select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves, false);
+          else select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves);
         }
         tc_fence_before();
         __syncwarp();
