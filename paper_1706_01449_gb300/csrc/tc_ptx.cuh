@@ -138,18 +138,20 @@ constexpr int kMaxSteps = 10;
 
 // The N MMAs of one item load, fully unrolled: a single thread issues them
 // back to back, so a loop, a branch or a computed predicate per MMA would
-// add issue time the tensor pipe waits for.  boff: the load's ring stage.
+// add issue time the tensor pipe waits for.  aoff, boff: the user-tile slot
+// and the item load's ring stage (descriptor address units).
 template <int N, bool F8 = false>
 __device__ __forceinline__ void mma_steps(uint32_t d, const uint64_t (&a_d)[kMaxSteps],
-                                          const uint64_t (&b_d)[kMaxSteps], uint64_t boff, uint32_t idesc) {
+                                          const uint64_t (&b_d)[kMaxSteps], uint64_t aoff, uint64_t boff,
+                                          uint32_t idesc) {
   if constexpr (F8) {
-    mma_f8<0>(d, a_d[0], b_d[0] + boff, idesc);
+    mma_f8<0>(d, a_d[0] + aoff, b_d[0] + boff, idesc);
 #pragma unroll
-    for (int s = 1; s < N; ++s) mma_f8<1>(d, a_d[s], b_d[s] + boff, idesc);
+    for (int s = 1; s < N; ++s) mma_f8<1>(d, a_d[s] + aoff, b_d[s] + boff, idesc);
   } else {
-    mma_bf16<0>(d, a_d[0], b_d[0] + boff, idesc);
+    mma_bf16<0>(d, a_d[0] + aoff, b_d[0] + boff, idesc);
 #pragma unroll
-    for (int s = 1; s < N; ++s) mma_bf16<1>(d, a_d[s], b_d[s] + boff, idesc);
+    for (int s = 1; s < N; ++s) mma_bf16<1>(d, a_d[s] + aoff, b_d[s] + boff, idesc);
   }
 }
 

@@ -503,7 +503,7 @@ constexpr int kWQ = 4;
 struct Smem {
   uint64_t b_full[kMaxStages];
   uint64_t b_empty[kMaxStages];
-  uint64_t a_full, a_empty;
+  uint64_t a_full[2], a_empty[2];  // user tiles: two slots, so the next one loads during the current one
   uint64_t acc_full[2], acc_empty[2];
   uint64_t aux_full[kAuxSlots], aux_empty[kAuxSlots];
   uint64_t drain;
@@ -536,8 +536,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
   const uint32_t b_chunk = sub_rows * p.row_bytes;  // one K chunk of a load
   const uint32_t a_bytes = p.kc * a_chunk + kTileM * p.tail_bytes;  // user tile (full chunks, then the tail)
   const uint32_t b_bytes = p.kc * b_chunk + sub_rows * p.tail_bytes;  // one ring stage
-  unsigned char* a_tiles = base;                                              // [KC][a_chunk] + tail
-  unsigned char* b_tiles = a_tiles + a_bytes;                                 // [S]([KC][b_chunk] + tail)
+  unsigned char* a_tiles = base;                                              // [2]([KC][a_chunk] + tail)
+  unsigned char* b_tiles = a_tiles + 2 * (size_t)a_bytes;                     // [S]([KC][b_chunk] + tail)
   float2* aux_ring = (float2*)(b_tiles + (size_t)p.stages * b_bytes);        // [kAuxSlots][256]
   int32_t* pos_ring = (int32_t*)(aux_ring + (size_t)kAuxSlots * kTileN);     // [kAuxSlots][256]
   float* heap_smem = (float*)(pos_ring + (size_t)kAuxSlots * kTileN);        // [K][256] (KR = 0)
@@ -561,8 +561,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       mbar_init(&ctl->b_full[s], 1);
       mbar_init(&ctl->b_empty[s], 1);
     }
-    mbar_init(&ctl->a_full, 1);
-    mbar_init(&ctl->a_empty, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&ctl->a_full[a], 1);
+      mbar_init(&ctl->a_empty[a], 1);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->acc_full[b], 1);
       mbar_init(&ctl->acc_empty[b], kEpiWarps);
@@ -623,13 +625,15 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         mbar_arrive(&ctl->wq_full[slot]);
         if (wi >= n_work) break;
         const WorkItem wk = get_work<MX>(p, wi, n_it);
-        if (lt > 0) ok = mbar_wait(&ctl->a_empty, (lt - 1) & 1, gd);
+        const int asl = (int)(na & 1);  // user-tile slot of this work item
+        if (na >= 2) ok = mbar_wait(&ctl->a_empty[asl], (uint32_t)(((na >> 1) - 1) & 1), gd);
         if (!ok) break;
-        mbar_expect_tx(&ctl->a_full, a_bytes);
+        unsigned char* a_dst = a_tiles + (size_t)asl * a_bytes;
+        mbar_expect_tx(&ctl->a_full[asl], a_bytes);
         for (int c = 0; c < p.kc; ++c)
-          tma_load_2d(a_tiles + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full);
+          tma_load_2d(a_dst + (size_t)c * a_chunk, &map_users, c * p.row_elems, wk.a_row, &ctl->a_full[asl]);
         if (p.tail_bytes)
-          tma_load_2d(a_tiles + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full);
+          tma_load_2d(a_dst + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full[asl]);
         ++na;
         for (int j = wk.tb; j < wk.te && ok; ++j) {
           // the tile's bound columns (and list positions) into aux slot at % kAuxSlots,
@@ -669,7 +673,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       if (!ok) {  // drain the operand copies still in flight before the CTA exits
         for (long long gg = (g > p.stages ? g - p.stages : 0); gg < g; ++gg)
           mbar_drain(&ctl->b_full[gg % p.stages], (uint32_t)((gg / p.stages) & 1));
-        if (na > 0) mbar_drain(&ctl->a_full, (uint32_t)((na - 1) & 1));
+        for (long long aa = (na > 2 ? na - 2 : 0); aa < na; ++aa)
+          mbar_drain(&ctl->a_full[aa & 1], (uint32_t)((aa >> 1) & 1));
       }
       // the select warps wait for a tile's bound columns only when they need
       // them: the last copies may still be landing, on either path
@@ -729,7 +734,9 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           mbar_arrive(&ctl->wq_empty[slot]);
           if (wi >= n_work) break;
           const WorkItem wk = get_work<MX>(p, wi, n_it);
-          ok = mbar_wait(&ctl->a_full, lt & 1, gd);
+          const int asl = lt & 1;  // user-tile slot of this work item
+          ok = mbar_wait(&ctl->a_full[asl], (uint32_t)((lt >> 1) & 1), gd);
+          const uint64_t aoff = (uint64_t)(asl * (a_bytes >> 4));
           if (!ok) break;
           tc_fence_after();
           for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
@@ -742,16 +749,16 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
               const uint32_t d = tmem + (uint32_t)(b * kTileN) + (uint32_t)h * sub_rows;
               const uint64_t boff = (uint64_t)(st * stage16);
               switch (nst) {
-                case 1: mma_steps<1, F8>(d, a_d, b_d, boff, idesc); break;
-                case 2: mma_steps<2, F8>(d, a_d, b_d, boff, idesc); break;
-                case 3: mma_steps<3, F8>(d, a_d, b_d, boff, idesc); break;
-                case 4: mma_steps<4, F8>(d, a_d, b_d, boff, idesc); break;
-                case 5: mma_steps<5, F8>(d, a_d, b_d, boff, idesc); break;
-                case 6: mma_steps<6, F8>(d, a_d, b_d, boff, idesc); break;
-                case 7: mma_steps<7, F8>(d, a_d, b_d, boff, idesc); break;
-                case 8: mma_steps<8, F8>(d, a_d, b_d, boff, idesc); break;
-                case 9: mma_steps<9, F8>(d, a_d, b_d, boff, idesc); break;
-                default: mma_steps<10, F8>(d, a_d, b_d, boff, idesc); break;
+                case 1: mma_steps<1, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 2: mma_steps<2, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 3: mma_steps<3, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 4: mma_steps<4, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 5: mma_steps<5, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 6: mma_steps<6, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 7: mma_steps<7, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 8: mma_steps<8, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                case 9: mma_steps<9, F8>(d, a_d, b_d, aoff, boff, idesc); break;
+                default: mma_steps<10, F8>(d, a_d, b_d, aoff, boff, idesc); break;
               }
               mma_commit(&ctl->b_empty[st]);
               if (++st == p.stages) {
@@ -764,7 +771,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
             b ^= 1;
             if (b == 0) aph ^= 1u;
           }
-          if (ok) mma_commit(&ctl->a_empty);
+          if (ok) mma_commit(&ctl->a_empty[asl]);
         }
       };
       if (f8) issue_loop(std::true_type{});
@@ -944,7 +951,7 @@ size_t tc_smem_bytes(const TcParams& p) {
   const size_t heap = p.K > kRegTopK && !p.heap_global ? sizeof(float) * (size_t)p.K * kEpiThreads : 0;
   const size_t a_bytes = (size_t)p.kc * a_chunk + (size_t)kTileM * p.tail_bytes;
   const size_t b_bytes = (size_t)p.kc * b_chunk + sub_rows * p.tail_bytes;
-  return 1024 + a_bytes + (size_t)p.stages * b_bytes + heap +
+  return 1024 + 2 * a_bytes + (size_t)p.stages * b_bytes + heap +
          (sizeof(float2) + sizeof(int32_t)) * kAuxSlots * kTileN + sizeof(float) * kQueue * kEpiThreads +
          sizeof(unsigned long long) * kEpiThreads + 2 * sizeof(int) * kEpiThreads +
          (p.K <= kRegTopK ? 2 * sizeof(float) * (size_t)p.K * kEpiThreads : 0) + sizeof(Smem);
