@@ -437,13 +437,22 @@ __device__ __forceinline__ void emit_tile(TcUser<KR>& s, const TcSel& c, uint32_
     if (!__any_sync(kFull, mg >= t)) continue;
     const int col0 = 16 * gi;
     const int nv = valid - col0;
+    // list walks: the group's 16 positions in four 16-byte loads (the ring
+    // slot and the group start are 16-byte aligned; every lane reads the same)
+    int4 p4[4] = {};
+    if constexpr (MX) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) p4[k] = reinterpret_cast<const int4*>(pos + col0)[k];
+    }
     // every column in turn, each store under its own predicate: the lanes
     // stay together however their hits are spread
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const float x = hv(s, c, __uint_as_float(v[q]));
       const bool hit = x >= t && q < nv;
-      const int32_t ip = MX ? pos[col0 + q] : pos0 + col0 + q;
+      const int4 pq = p4[q >> 2];
+      const int32_t ip = MX ? ((q & 3) == 0 ? pq.x : (q & 3) == 1 ? pq.y : (q & 3) == 2 ? pq.z : pq.w)
+                            : pos0 + col0 + q;
       const bool in = ip >= 0 && ip < c.n_items;
       bad |= hit && !in;
       if (hit && in && n < c.cap) {
