@@ -426,7 +426,7 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
  * roles drain their copies and MMAs, frees the tensor memory and exits, so
  * the context stays usable.  After this call, the next blocked-multiply
  * launch of that kernel in this process (a BF16 mips_topk call) publishes
- * no work item: its MMA thread and select warps wait for one until wait_ns
+ * no work item: its MMA issuers and select warps wait for one until wait_ns
  * nanoseconds pass, and the call's mips_sync reports MIPS_ERR_TIMEOUT (the
  * call's rescore then finds empty candidate lists).  One launch only;
  * later launches are unaffected.  Errors: MIPS_ERR_ARG unless

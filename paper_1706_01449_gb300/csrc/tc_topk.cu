@@ -3,7 +3,7 @@
 // the |U| x |I| score matrix never leaves the SM), and the same machinery
 // walking Maximus's per-cluster item lists (Sec. III, Algorithm 1).
 //
-// Persistent kernel, one CTA per SM, 10 warps, user tiles of 128 rows and
+// Persistent kernel, one CTA per SM, 12 warps, user tiles of 128 rows and
 // item tiles of 256 rows (an M = 128, N = 256 MMA runs at the tensor pipe's
 // full rate):
 //   warps 0-7   select: epilogue warp e reads TMEM lanes 32 * (e % 4) .. +31
@@ -21,14 +21,27 @@
 //               tiles through an S-stage ring (whole tiles, or two 128-row
 //               halves when whole tiles do not fit shared memory; operand
 //               rows of 128-byte chunks plus a 32/64-byte tail chunk, each
-//               with its own tensor map and swizzle), and with each item
-//               tile a bulk copy of its bound columns (and, for list walks,
-//               its item positions) into a small ring the select warps read;
-//   warp 9      MMA issuer (one thread): D = A . B^T with tcgen05.mma
+//               with its own tensor map and swizzle);
+//   warps 9-10  MMA issuers (lane 0 of each): D = A . B^T with tcgen05.mma
 //               kind::f16 (BF16 x BF16 -> FP32) or kind::f8f6f4 (E4M3 x
-//               E4M3 -> FP32, entries scaled by s_u s_I) into one of two TMEM
+//               E4M3 -> FP32, entries scaled by s_u s_I) into two TMEM
 //               accumulators of 128 lanes x 256 columns, so the MMAs of item
-//               tile j+1 overlap the select of tile j.
+//               tile j+1 overlap the select of tile j.  Warp 9 issues the
+//               even item tiles (accumulator 0), warp 10 the odd ones
+//               (accumulator 1): a thread's tcgen05 instructions and barrier
+//               waits queue behind its own MMAs, so one thread leaves the
+//               tensor pipe idle while it waits for and sets up the next
+//               tile; with two, each waits while the other's MMAs run.
+//               (Only where even and odd tiles use disjoint ring stages;
+//               otherwise warp 9 issues every tile.)
+//   warp 11     lane 0 copies each item tile's bound columns (and, for list
+//               walks, its item positions) into a small ring the select
+//               warps read.  Like the MMA issue, the producer's copies are
+//               split over threads so that neither thread's queue of barrier
+//               and copy instructions sets the pace, and so that an item
+//               tile's operand load waits only for its ring stage's MMAs,
+//               not for the select of the tile whose bound-column slot it
+//               reuses.
 // The select's common case is one max-reducing TMEM load per 64 scores
 // (tcgen05.ld.red: the values and each thread's maximum of them) and one
 // warp vote: the operands carry two bound columns, so every accumulator
@@ -40,8 +53,8 @@
 // as the list gives them, claimed round-robin or from a global counter.
 //
 // Every mbarrier wait is bounded (1 s of %globaltimer); on expiry the kernel
-// raises DEV_ERR_TIMEOUT, every role leaves its loop, the MMA thread drains
-// its in-flight MMAs and the producer its in-flight copies (each with a
+// raises DEV_ERR_TIMEOUT, every role leaves its loop, the MMA issuers drain
+// their in-flight MMAs and the producer its in-flight copies (each with a
 // bounded wait), and TMEM is freed before exit.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -56,10 +69,12 @@ namespace mips {
 
 namespace {
 
-constexpr int kWarps = 10;
+constexpr int kWarps = 12;
 constexpr int kEpiWarps = 8;   // warps 0-7 select
 constexpr int kProdWarp = 8;   // producer (lane 0) and TMEM allocation (whole warp)
-constexpr int kMmaWarp = 9;    // MMA issuer (lane 0)
+constexpr int kMmaWarp = 9;    // MMA issuer of accumulator 0 (lane 0)
+constexpr int kMmaWarp2 = 10;  // MMA issuer of accumulator 1 (lane 0)
+constexpr int kAuxWarp = 11;   // bound-column (and list-position) copies (lane 0)
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTileN = 256;    // items per tile (MMA N)
 constexpr int kTileM = 128;    // users per tile (MMA M)
@@ -505,7 +520,7 @@ __device__ __forceinline__ WorkItem get_work(const TcParams& p, int wi, int n_it
 
 // The CTA's work sequence: the producer takes its lt-th work item (static:
 // round-robin over the CTAs; with a work counter: the next unclaimed item)
-// and publishes the index in ring slot lt % kWQ, where the MMA thread and the
+// and publishes the index in ring slot lt % kWQ, where the MMA issuers and the
 // select warps read it; an index >= n_work ends the sequence.
 constexpr int kWQ = 4;
 
@@ -572,7 +587,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&ctl->a_full[a], 1);
-      mbar_init(&ctl->a_empty[a], 1);
+      mbar_init(&ctl->a_empty[a], 2);  // a commit by each MMA issuer
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl->acc_full[b], 1);
@@ -582,10 +597,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       mbar_init(&ctl->aux_full[a], 1);
       mbar_init(&ctl->aux_empty[a], kEpiWarps);
     }
-    mbar_init(&ctl->drain, 1);
+    mbar_init(&ctl->drain, 2);
     for (int w = 0; w < kWQ; ++w) {
       mbar_init(&ctl->wq_full[w], 1);
-      mbar_init(&ctl->wq_empty[w], 1 + kEpiWarps);  // the MMA thread and every select warp
+      mbar_init(&ctl->wq_empty[w], 3 + kEpiWarps);  // the MMA issuers, the bound-column copier, the select warps
     }
     ctl->abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -613,15 +628,14 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_items)) : "memory");
       const int tail_x = p.kc * p.row_elems;  // element column of the tail chunk
       long long g = 0;   // item loads issued so far
-      long long at = 0;  // item tiles whose bound columns (and positions) were copied so far
       long long na = 0;  // user tiles loaded so far
       int st = 0;        // ring stage of load g
       uint32_t ph = 0;   // ring pass parity of load g
       bool ok = true;
       const bool dyn = MX && p.work.next;
-      const uint32_t aux_tx = kAuxBytes + (MX ? kPosBytes : 0u);
       // a test of the bounded waits: publish no work item at all, so that
-      // the MMA thread and the select warps wait for one until the limit
+      // the MMA issuers, the bound-column copier and the select warps wait
+      // for one until the limit
       if (p.test_withhold) ok = false;
       for (int lt = 0; ok; ++lt) {
         // take and publish the next work item
@@ -645,24 +659,6 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           tma_load_2d(a_dst + (size_t)p.kc * a_chunk, &map_users_t, tail_x, wk.a_row, &ctl->a_full[asl]);
         ++na;
         for (int j = wk.tb; j < wk.te && ok; ++j) {
-          // the tile's bound columns (and list positions) into aux slot at % kAuxSlots,
-          // once the select warps are done with the slot's last tile AND that
-          // tile's copy has landed: the select warps wait for a copy only when
-          // they read it, so nothing else orders it before this one (re-arming
-          // the barrier while its previous phase still waits for bytes would
-          // be an arrival too many, and the two copies would overlap)
-          const int as = (int)(at % kAuxSlots);
-          if (at >= kAuxSlots) {
-            const uint32_t prev = (uint32_t)((at / kAuxSlots - 1) & 1);
-            ok = mbar_wait(&ctl->aux_empty[as], prev, gd) &&
-                 mbar_wait(&ctl->aux_full[as], prev, gd);
-          }
-          if (!ok) break;
-          const int64_t row0 = (int64_t)wk.b_row + (int64_t)j * kTileN;
-          mbar_expect_tx(&ctl->aux_full[as], aux_tx);
-          bulk_load(aux_ring + (size_t)as * kTileN, item_aux + row0, kAuxBytes, &ctl->aux_full[as]);
-          if constexpr (MX) bulk_load(pos_ring + (size_t)as * kTileN, p.work.item_pos + row0, kPosBytes, &ctl->aux_full[as]);
-          ++at;
           for (int h = 0; h < bs; ++h, ++g) {  // g: loads issued so far
             if (g >= p.stages) ok = mbar_wait(&ctl->b_empty[st], ph ^ 1u, gd);
             if (!ok) break;
@@ -685,14 +681,60 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         for (long long aa = (na > 2 ? na - 2 : 0); aa < na; ++aa)
           mbar_drain(&ctl->a_full[aa & 1], (uint32_t)((aa >> 1) & 1));
       }
+    }
+  } else if (warp == kAuxWarp) {
+    // ------------------------------------------------------------ bound-column copies
+    if (lane == 0) {
+      long long at = 0;  // item tiles whose bound columns (and positions) were copied so far
+      bool ok = true;
+      const uint32_t aux_tx = kAuxBytes + (MX ? kPosBytes : 0u);
+      for (int lt = 0; ok; ++lt) {
+        const int slot = lt % kWQ;
+        ok = mbar_wait(&ctl->wq_full[slot], (uint32_t)((lt / kWQ) & 1), gd);
+        if (!ok) break;
+        const int wi = *(volatile int*)&ctl->wq[slot];
+        mbar_arrive(&ctl->wq_empty[slot]);
+        if (wi >= n_work) break;
+        const WorkItem wk = get_work<MX>(p, wi, n_it);
+        for (int j = wk.tb; j < wk.te && ok; ++j) {
+          // the tile's bound columns (and list positions) into aux slot at % kAuxSlots,
+          // once the select warps are done with the slot's last tile AND that
+          // tile's copy has landed: the select warps wait for a copy only when
+          // they read it, so nothing else orders it before this one (re-arming
+          // the barrier while its previous phase still waits for bytes would
+          // be an arrival too many, and the two copies would overlap)
+          const int as = (int)(at % kAuxSlots);
+          if (at >= kAuxSlots) {
+            const uint32_t prev = (uint32_t)((at / kAuxSlots - 1) & 1);
+            ok = mbar_wait(&ctl->aux_empty[as], prev, gd) && mbar_wait(&ctl->aux_full[as], prev, gd);
+          }
+          if (!ok) break;
+          const int64_t row0 = (int64_t)wk.b_row + (int64_t)j * kTileN;
+          mbar_expect_tx(&ctl->aux_full[as], aux_tx);
+          bulk_load(aux_ring + (size_t)as * kTileN, item_aux + row0, kAuxBytes, &ctl->aux_full[as]);
+          if constexpr (MX) bulk_load(pos_ring + (size_t)as * kTileN, p.work.item_pos + row0, kPosBytes, &ctl->aux_full[as]);
+          ++at;
+        }
+      }
       // the select warps wait for a tile's bound columns only when they need
       // them: the last copies may still be landing, on either path
       for (long long aa = (at > kAuxSlots ? at - kAuxSlots : 0); aa < at; ++aa)
         mbar_drain(&ctl->aux_full[aa % kAuxSlots], (uint32_t)((aa / kAuxSlots) & 1));
     }
-  } else if (warp == kMmaWarp) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp == kMmaWarp || warp == kMmaWarp2) {
+    // ------------------------------------------------------------ MMA issuers
     if (lane == 0) {
+      const int mine = warp - kMmaWarp;  // the accumulator (item-tile parity) this thread serves
+      // The two issuers split the item tiles by parity only where that also
+      // splits the ring stages: with S a multiple of 2 bs, tile g's loads
+      // take stages bs g .. bs g + bs - 1 (mod S), even tiles and odd tiles
+      // never share a stage, and the one issuer of a stage waits for every
+      // phase of its barriers in turn (a parity wait cannot tell phase k
+      // from phase k + 2, so a thread that skipped phases could take a
+      // stale one for the one it waits for).  Otherwise warp 9 issues every
+      // tile and warp 10 only keeps its part of the work-item and user-tile
+      // protocol.
+      const bool split = p.stages % (2 * bs) == 0;
       bool ok_init = true;
       // instruction descriptor: D = F32, A = B = BF16 (kind::f16 format 1) or
       // E4M3 (kind::f8f6f4 format 0), both K-major, N, M
@@ -749,6 +791,16 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if (!ok) break;
           tc_fence_after();
           for (int j = wk.tb; j < wk.te; ++j, ++g) {  // g: item tiles so far
+            if (split ? b != mine : mine != 0) {  // another issuer's tile: step over its ring stages
+              for (int h = 0; h < bs; ++h)
+                if (++st == p.stages) {
+                  st = 0;
+                  ph ^= 1u;
+                }
+              b ^= 1;
+              if (b == 0) aph ^= 1u;
+              continue;
+            }
             for (int h = 0; h < bs && ok; ++h) {
               ok = mbar_wait(&ctl->b_full[st], ph, gd);
               if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, gd);
@@ -907,9 +959,18 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
           if (!aux_ready) {
             ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
             if (!ok) break;
+            aux_ready = true;
           }
           if (first) emit_tile<KR, MX>(s, c, taddr, valid, rank0, pos, halves);
           else select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves);
+        }
+        // the bound-column slot is released only once its copy has landed,
+        // read or not: the copier runs on its own, and a slot released
+        // before its copy would let the copier's parity waits run a phase
+        // ahead
+        if (!aux_ready) {
+          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
+          if (!ok) break;
         }
         tc_fence_before();
         __syncwarp();
