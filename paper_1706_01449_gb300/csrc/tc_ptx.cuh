@@ -72,6 +72,42 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
   return mbar_wait_slow(bar, parity, gd);
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// The same bounded wait as mbar_wait, spinning on the non-blocking test (no
+// suspend, so no wake-up delay) and looking at the abort flag and the
+// timer once every 64 tests.  For a thread whose wait is on the critical
+// path and that shares its sub-partition with little else.
+__device__ __noinline__ bool mbar_spin_slow(uint64_t* bar, uint32_t parity, Guard gd) {
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_test_wait(bar, parity)) return true;
+    if (*gd.abort_flag) return false;
+    if (globaltimer() - t0 > gd.wait_ns) {
+      *gd.abort_flag = 1;
+      atomicOr(gd.err, DEV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ bool mbar_spin(uint64_t* bar, uint32_t parity, const Guard& gd) {
+  if (mbar_test_wait(bar, parity)) return true;
+  return mbar_spin_slow(bar, parity, gd);
+}
+
 // Wait (bounded) for a phase whose completion nothing else depends on any
 // more: used only to drain copies and MMAs before the CTA exits.
 __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {

@@ -802,8 +802,10 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
               continue;
             }
             for (int h = 0; h < bs && ok; ++h) {
-              ok = mbar_wait(&ctl->b_full[st], ph, gd);
-              if (ok && h == 0 && g >= 2) ok = mbar_wait(&ctl->acc_empty[b], aph ^ 1u, gd);
+              // (spinning waits: an issuer's wait is on the tensor pipe's
+              // critical path, and the thread has nothing else to do)
+              ok = mbar_spin(&ctl->b_full[st], ph, gd);
+              if (ok && h == 0 && g >= 2) ok = mbar_spin(&ctl->acc_empty[b], aph ^ 1u, gd);
               if (!ok) break;
               tc_fence_after();
               // this load's rows go to accumulator columns [h sub_rows, (h + 1) sub_rows)
@@ -913,15 +915,20 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
       const int par = lt & 1;
       for (int j = wk.tb; j < wk.te; ++j, ++g) {
         const int b = (int)(g & 1);
-        // lanes leave together: TMEM loads are warp-collective
-        ok = __all_sync(kFull, mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), gd));
-        if (!ok) break;
-        tc_fence_after();
         const int as = (int)(g % kAuxSlots);
         const uint32_t aph = (uint32_t)((g / kAuxSlots) & 1);
         const float2* aux = aux_ring + (size_t)as * kTileN + c2 * kHalfN;
         const int32_t* pos = pos_ring + (size_t)as * kTileN + c2 * kHalfN;
-        bool aux_ready = false;
+        // the tile's bound columns first (their copy runs up to kAuxSlots
+        // tiles ahead, so this wait is over long before the accumulator's),
+        // read or not: the slot is released only once its copy has landed,
+        // or the copier's parity waits could run a phase ahead
+        ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
+        if (!ok) break;
+        // lanes leave together: TMEM loads are warp-collective
+        ok = __all_sync(kFull, mbar_wait(&ctl->acc_full[b], (uint32_t)((g >> 1) & 1), gd));
+        if (!ok) break;
+        tc_fence_after();
         {  // the partner's threshold, if it is for this work item
           const unsigned long long pt = *c.tau(c.pslot);
           if ((int)(pt >> 32) == wi) s.tau_eff = fmaxf(s.tau_eff, __uint_as_float((uint32_t)pt));
@@ -934,9 +941,6 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         const int valid = (int)min((int64_t)kHalfN, p.n_items - rank0);
         const bool first = j == wk.tb && !restoring;  // a fresh work item's first tile
         if (__builtin_expect(first, 0)) {  // (rare paths marked so the common case stays compact)
-          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
-          if (!ok) break;
-          aux_ready = true;
           seed_tile(s, c, taddr, valid, aux, active);
           if (active) {
             s.tau_eff = fmaxf(s.tau_eff, s.tau);
@@ -956,21 +960,8 @@ __global__ void __launch_bounds__(kWarps * 32, 1)
         }
         if (__builtin_expect(halves != 0u, 0)) {
           slow += __popc(halves);
-          if (!aux_ready) {
-            ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
-            if (!ok) break;
-            aux_ready = true;
-          }
           if (first) emit_tile<KR, MX>(s, c, taddr, valid, rank0, pos, halves);
           else select_hits<KR, MX>(s, c, taddr, valid, aux, rank0, pos, halves);
-        }
-        // the bound-column slot is released only once its copy has landed,
-        // read or not: the copier runs on its own, and a slot released
-        // before its copy would let the copier's parity waits run a phase
-        // ahead
-        if (!aux_ready) {
-          ok = __all_sync(kFull, mbar_wait(&ctl->aux_full[as], aph, gd));
-          if (!ok) break;
         }
         tc_fence_before();
         __syncwarp();
