@@ -398,10 +398,10 @@ mips_status mips_get_buffer(mips_index_t idx, const char* name, const void** dev
  *
  * Scratch comes from one static device array of 32 MiB per GPU, reserved
  * when the library's code is loaded on that GPU and held until the process
- * exits.  A call needs 8 n_items + n_users (20 + 20 cap) bytes of it plus
- * at most 4 KiB of counters and alignment padding, where cap = max(4K + 96,
+ * exits.  A call needs 8 n_items + n_users (28 + 28 cap) bytes of it plus
+ * at most 5 KiB of counters and alignment padding, where cap = max(4K + 96,
  * K (2 + ln(n_items / K)) + 96) is the candidate slots per user (K = 10:
- * about 8,700 users against 17,770 items); larger calls return
+ * about 6,200 users against 17,770 items); larger calls return
  * MIPS_ERR_ARG (split the users).  A user whose candidates overflow its
  * slots is scored exhaustively (still exact, slower).  Limits as
  * mips_topk: 1 <= f <= 128, 1 <= K <= min(n_items, 128).

@@ -92,22 +92,28 @@ struct SelectOut {
   // users whose candidate list overflowed, for the exhaustive rescore
   int32_t* ovf_list;   // [n_users]
   int* ovf_count;      // one counter, zero before the rescore
-  // rescore scratch: valid candidate slots, their exact scores, thresholds
-  uint32_t* work;      // [n_users * lists * cap]
+  // rescore scratch: the work list (the slots of the candidates that reach
+  // their user's threshold, each user's run contiguous), then per work entry
+  // w its exact score, the item's id and norm bound (written in work order,
+  // so the final select reads its user's run in one piece)
+  uint32_t* work;      // [n_users * lists * cap] candidate slot of entry w
   int* work_count;     // one counter
-  double* cand_sc;     // [n_users * lists][cap]
-  float* tau_final;    // [n_users][2]: the rescore threshold, ||u||^2
+  double* cand_sc;     // [n_users * lists * cap] exact score of entry w
+  float* tau_final;    // [n_users][2]: entry 2u + 1 = ||u||^2 as the collect kernel summed it (2u unused)
   // optional ([n_users], zeroed): the largest threshold any select thread of
   // the user published, as order-preserving bits; threads scanning other
   // item chunks of the same user raise their filter to it
   unsigned* tau_glob = nullptr;
+  int32_t* w_id = nullptr;   // [n_users * lists * cap] item id (perm) of entry w; -1: a bad position
+  float* w_nrm = nullptr;    // [n_users * lists * cap] the item's norm bound
+  int* u_work = nullptr;     // [n_users][2] the user's run in the work list: first entry, count
 };
 
 // Bytes of rescore scratch (ovf list, work list, scores, thresholds, counters)
 // for n_users users with `lists` sub-lists of `cap` candidates each.
 inline size_t rescore_scratch_bytes(int64_t n_users, int lists, int cap) {
   const size_t slots = (size_t)n_users * lists * cap;
-  return 4 * (size_t)n_users + 4 * slots + 8 * slots + 8 * (size_t)n_users + 1024;
+  return 4 * (size_t)n_users + 4 * slots + 8 * slots + 8 * (size_t)n_users + 8 * slots + 8 * (size_t)n_users + 2048;
 }
 bool fp32_supported(int f, int K);
 cudaError_t launch_fp32_score_select(const float* users, int64_t n_users, int f, const float* items,

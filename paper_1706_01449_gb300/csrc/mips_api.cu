@@ -311,6 +311,8 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
   size_t o_work = idx->ws.take(sizeof(uint32_t) * nl * cap);
   size_t o_workc = idx->ws.take(sizeof(int));
   size_t o_sc = idx->ws.take(sizeof(double) * nl * cap);
+  size_t o_wid = idx->ws.take(sizeof(int32_t) * nl * cap), o_wnrm = idx->ws.take(sizeof(float) * nl * cap);
+  size_t o_uwork = idx->ws.take(sizeof(int) * 2 * n_users);
   size_t o_tauf = idx->ws.take(sizeof(float) * 2 * n_users);
   size_t o_ub16 = 0, o_uaux = 0, o_us = 0, o_cw = 0, o_cnw = 0, o_crow = 0, o_cpos = 0, o_ctau = 0, o_heap = 0;
   if (use_tc && p.heap_global) o_heap = idx->ws.take(sizeof(float) * idx->num_sms * K * 256);
@@ -337,6 +339,9 @@ mips_status run_bmm(mips_index_t idx, const float* users, int64_t n_users, int K
                lists >= 2 ? idx->ws.at<float>(o_topl) : nullptr, 1,
                idx->ws.at<int32_t>(o_ovf), idx->ws.at<int>(o_ovfc), idx->ws.at<uint32_t>(o_work),
                idx->ws.at<int>(o_workc), idx->ws.at<double>(o_sc), idx->ws.at<float>(o_tauf)};
+  so.w_id = idx->ws.at<int32_t>(o_wid);
+  so.w_nrm = idx->ws.at<float>(o_wnrm);
+  so.u_work = idx->ws.at<int>(o_uwork);
   mips_status st;
   if (!use_tc) {
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
@@ -475,6 +480,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_ovf = ws.take(sizeof(int32_t) * n_users), o_ovfc = ws.take(sizeof(int));
   size_t o_work = ws.take(sizeof(uint32_t) * n_users * cap1), o_workc = ws.take(sizeof(int));
   size_t o_sc = ws.take(sizeof(double) * n_users * cap1), o_tauf = ws.take(sizeof(float) * 2 * n_users);
+  size_t o_wid = ws.take(sizeof(int32_t) * n_users * cap1), o_wnrm = ws.take(sizeof(float) * n_users * cap1);
+  size_t o_uwork = ws.take(sizeof(int) * 2 * n_users);
   // tensor-core walk buffers: BF16 user rows grouped by cluster (each
   // cluster padded to whole 128-row tiles), per-cluster BF16 item copies in
   // bound order, two work lists, two-list select state
@@ -488,7 +495,7 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
   size_t o_u16 = 0, o_uaux = 0, o_rowu = 0, o_urow = 0, o_padoff = 0, o_arows = 0, o_brows = 0, o_auxc = 0,
          o_posc = 0, o_w1 = 0, o_w2 = 0, o_nw = 0, o_wend = 0, o_tau2 = 0, o_n2 = 0, o_pos2 = 0, o_ub2 = 0,
          o_topl = 0, o_work2 = 0, o_sc2 = 0, o_ustop = 0, o_wk0 = 0, o_wk1 = 0, o_wv0 = 0, o_wv1 = 0, o_clend = 0,
-         o_heapm = 0;
+         o_heapm = 0, o_wid2 = 0, o_wnrm2 = 0;
   size_t o_us = 0;
   if (use_tc) {
     const size_t es = (size_t)idx->esize;
@@ -513,6 +520,8 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     o_topl = ws.take(sizeof(float) * nl * K);
     o_work2 = ws.take(sizeof(uint32_t) * nl * cap2);
     o_sc2 = ws.take(sizeof(double) * nl * cap2);
+    o_wid2 = ws.take(sizeof(int32_t) * nl * cap2);
+    o_wnrm2 = ws.take(sizeof(float) * nl * cap2);
     o_ustop = ws.take(sizeof(int32_t) * n_users);
     o_clend = ws.take(sizeof(int) * C);
     if (p.heap_global) o_heapm = ws.take(sizeof(float) * idx->num_sms * K * 256);
@@ -575,6 +584,9 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     SelectOut so{ws.at<float>(o_tau), ws.at<int>(o_n), ws.at<int32_t>(o_pos), ws.at<float>(o_ub), cap, 1, nullptr, 0,
                  ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc), ws.at<uint32_t>(o_work), ws.at<int>(o_workc),
                  ws.at<double>(o_sc), ws.at<float>(o_tauf)};
+    so.w_id = ws.at<int32_t>(o_wid);
+    so.w_nrm = ws.at<float>(o_wnrm);
+    so.u_work = ws.at<int>(o_uwork);
     if ((st = mark_kernel(idx, s)) != MIPS_OK) return st;
     MIPS_CUDA(maximus_walk(users, f, idx->items, idx->item_nrm, nI, vals, ws.at<float>(o_bounds), user_perm,
                            ws.at<int>(o_off), ws.at<int>(o_toff), C, K, so, ws.at<int32_t>(o_vis), ws.at<int>(o_wc),
@@ -637,6 +649,9 @@ mips_status run_maximus(mips_index_t idx, const float* users, int64_t n_users, i
     SelectOut so{ws.at<float>(o_tau2), ws.at<int>(o_n2), ws.at<int32_t>(o_pos2), ws.at<float>(o_ub2), cap2, 2,
                  ws.at<float>(o_topl), 1, ws.at<int32_t>(o_ovf), ws.at<int>(o_ovfc),
                  ws.at<uint32_t>(o_work2), ws.at<int>(o_workc), ws.at<double>(o_sc2), ws.at<float>(o_tauf)};
+    so.w_id = ws.at<int32_t>(o_wid2);
+    so.w_nrm = ws.at<float>(o_wnrm2);
+    so.u_work = ws.at<int>(o_uwork);
     p.n_users = n_users;
     p.mode = 1;
     if (p.heap_global) p.heap_mem = ws.at<float>(o_heapm);

@@ -13,7 +13,7 @@
 // Limits and sharing (also stated in include/mips.h):
 //   * the scratch is kNoAllocScratchBytes (32 MiB) on every GPU that loads
 //     the library, held until the process exits;
-//   * a call needs 8 n_items + n_users (20 + 20 cap) bytes plus at most 4 KiB
+//   * a call needs 8 n_items + n_users (28 + 28 cap) bytes plus at most 5 KiB
 //     of counters and alignment padding, cap = max(4K + 96, K (2 + ln(n_items
 //     / K)) + 96) candidate slots per user (the FP32 blocked multiply's list
 //     capacity: the expected number of K-th-largest records of a stream of
@@ -107,7 +107,8 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
   const int cap = list_cap(K, n_items);
   const size_t slots = (size_t)n_users * cap;
   const size_t need = up256(sizeof(DevStats)) + up256(sizeof(int)) * 3 + up256(4 * (size_t)n_items) * 2 +
-                      up256(4 * (size_t)n_users) * 3 + up256(8 * (size_t)n_users) + up256(4 * slots) * 3 + up256(8 * slots);
+                      up256(4 * (size_t)n_users) * 3 + up256(8 * (size_t)n_users) * 2 + up256(4 * slots) * 5 +
+                      up256(8 * slots);
   if (need > kNoAllocScratchBytes)
     return report(MIPS_ERR_ARG, "problem needs %zu scratch bytes, the static scratch holds %zu (use fewer users per call)",
                   need, kNoAllocScratchBytes);
@@ -147,6 +148,12 @@ mips_status mips_topk_noalloc(const float* items_dev, int64_t n_items, const flo
   p += up256(sizeof(int));
   so.cand_sc = (double*)p;
   p += up256(8 * slots);
+  so.w_id = (int32_t*)p;
+  p += up256(4 * slots);
+  so.w_nrm = (float*)p;
+  p += up256(4 * slots);
+  so.u_work = (int*)p;
+  p += up256(8 * (size_t)n_users);
   so.tau_final = (float*)p;
 
   // counters and the error word must start at zero; the rest is overwritten

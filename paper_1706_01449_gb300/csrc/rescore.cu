@@ -8,11 +8,14 @@
 //       bounds are given, the K-th largest of their union (the entries
 //       belong to distinct items, so this is a valid lower bound on the
 //       user's K-th score) -- and the slots of the candidates whose upper
-//       bound H reaches tau, appended to a work list;
-//   (B) dot, thread per listed candidate: its compensated FP32 dot product
-//       (Dot2, common.cuh), so every lane of a warp has work;
+//       bound H reaches tau, appended to a work list (each user's run in
+//       one piece, its first entry and length noted per user);
+//   (B) dot, thread per work entry: its compensated FP32 dot product
+//       (Dot2, common.cuh), so every lane of a warp has work, stored in
+//       work order with the item's id and norm bound (the two gathers by
+//       item position happen here, where they overlap across lanes);
 //   (C) select, thread per user: the K + 1 best keys (score desc, item id
-//       asc) in a shared-memory heap, sorted;
+//       asc) of its work run in a shared-memory heap, sorted;
 //   * tie check: every adjacent pair of that list is compared against the
 //     score error bound
 //       e = (2 gamma_2f gamma_f + (f + 2) 2^-53) nhat_u nhat_i_max  (x 2 margin),
@@ -319,7 +322,6 @@ __global__ void __launch_bounds__(256)
       for (int l = 0; l < o.lists; ++l) tau = l == 0 ? o.tau[l0] : fmaxf(tau, o.tau[l0 + l]);
       if (o.lists > 1 && o.topl && o.topl_sorted)
         tau = fmaxf(tau, o.lists == 2 ? union2_kth(o.topl + l0 * K, K) : union_kth(o.topl + l0 * K, o.lists, K));
-      o.tau_final[2 * u] = tau;
       live = true;
       for (int l = 0; l < o.lists; ++l) {
         const float* cu = o.cand_ub + (l0 + l) * (int64_t)o.cap;
@@ -339,6 +341,10 @@ __global__ void __launch_bounds__(256)
   int base = 0;
   if (lane == 31 && total) base = atomicAdd(o.work_count, total);
   base = __shfl_sync(kFull, base, 31) + incl - nvalid;
+  if (u < n_users) {  // the user's run in the work list (read by the select for live users)
+    o.u_work[2 * u] = base;
+    o.u_work[2 * u + 1] = live ? nvalid : 0;
+  }
   if (live && nvalid) {
     const int64_t l0 = u * o.lists;
     for (int l = 0; l < o.lists; ++l) {
@@ -366,9 +372,11 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 // (a position outside [0, n_items) is never written by the score kernels;
 // if one is read -- a score kernel that gave up on a bounded wait leaves its
-// lists unfinished -- it is flagged and skipped rather than dereferenced)
+// lists unfinished -- it is flagged, and its entry gets id -1, which the
+// select skips, rather than being dereferenced)
 __global__ void __launch_bounds__(256)
-    rescore_dot_kernel(const float* __restrict__ users, int f, const float* __restrict__ items, int64_t n_items,
+    rescore_dot_kernel(const float* __restrict__ users, int f, const float* __restrict__ items,
+                       const int32_t* __restrict__ perm, const float* __restrict__ item_nrm, int64_t n_items,
                        SelectOut o, int* err) {
   const int count = *o.work_count;
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
@@ -377,12 +385,18 @@ __global__ void __launch_bounds__(256)
     const int32_t pos = o.cand_pos[slot];
     if (pos < 0 || pos >= n_items) {
       atomicOr(err, DEV_ERR_INTERNAL);
-      o.cand_sc[slot] = 0.0;
+      o.cand_sc[w] = 0.0;
+      o.w_id[w] = -1;
+      o.w_nrm[w] = 0.f;
       continue;
     }
+    const int32_t id = perm[pos];
+    const float nrm = item_nrm[pos];
     const float* ur = users + u * f;
     const float* ir = items + (int64_t)pos * f;
-    o.cand_sc[slot] = pairs_ok(ur, ir, f) ? score_dot2(ur, ir, f) : score_dot2_v4(ur, ir, f);
+    o.cand_sc[w] = pairs_ok(ur, ir, f) ? score_dot2(ur, ir, f) : score_dot2_v4(ur, ir, f);
+    o.w_id[w] = id;
+    o.w_nrm[w] = nrm;
   }
 }
 
@@ -391,8 +405,7 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
     rescore_select_kernel(const float* __restrict__ users, int64_t n_users, int f,
-                          const float* __restrict__ items, const int32_t* __restrict__ perm,
-                          const float* __restrict__ item_nrm, int64_t n_items, int K, SelectOut o,
+                          const float* __restrict__ items, int K, SelectOut o,
                           int32_t* __restrict__ out_idx,
                           double* __restrict__ out_score, DevStats* stats, int* err) {
   extern __shared__ unsigned char smem_raw[];
@@ -411,27 +424,20 @@ __global__ void __launch_bounds__(128)
     // zero users are done; overflowed and tiny users belong to the warp kernel
     if (ss >= kTinyNorm2 && !over) {
       const double nu = (double)__fsqrt_rn(ss) * (1.0 + (double)(f + 2) * 1.1920929e-07);
-      const float tau = o.tau_final[2 * u];
       const double rel_e = rescore_rel_err(f);
+      // the candidates that reach the threshold: the user's run of the work list
+      const int w0 = o.u_work[2 * u], nw = o.u_work[2 * u + 1];
       KeyHeap heap{ls + t, li + t, T};
       for (int mode = 0; mode < 2; ++mode) {
         int cnt = 0;
         float nmax = 0.f;
-        for (int l = 0; l < o.lists; ++l) {
-          const int64_t row = (l0 + l) * (int64_t)o.cap;
-          const int nl = o.n_cand[l0 + l];
-          for (int c = 0; c < nl; ++c) {
-            if (o.cand_ub[row + c] < tau) continue;
-            const int32_t pos = o.cand_pos[row + c];
-            if (pos < 0 || pos >= n_items) {  // (as in the dot kernel)
-              atomicOr(err, DEV_ERR_INTERNAL);
-              continue;
-            }
-            const double v =
-                mode == 0 ? o.cand_sc[row + c] : score_f64(ur, items + (int64_t)pos * f, f);
-            nmax = fmaxf(nmax, item_nrm[pos]);
-            heap.push(cnt, L, v, perm[pos]);
-          }
+        for (int w = w0; w < w0 + nw; ++w) {
+          const int32_t id = o.w_id[w];
+          if (id < 0) continue;  // a bad position, flagged by the dot kernel
+          const double v =
+              mode == 0 ? o.cand_sc[w] : score_f64(ur, items + (int64_t)o.cand_pos[o.work[w]] * f, f);
+          nmax = fmaxf(nmax, o.w_nrm[w]);
+          heap.push(cnt, L, v, id);
         }
         heap.sort(cnt);
         if (cnt < K) {  // cannot happen: K lower bounds back tau
@@ -604,16 +610,15 @@ cudaError_t launch_rescore(const float* users, int64_t n_users, int f, const flo
   if (e != cudaSuccess) return e;
   rescore_collect_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, K, o, out_idx,
                                                                             out_score, stats);
-  rescore_dot_kernel<<<sm_count() * 8, 256, 0, s>>>(users, f, items_sorted, n_items, o, err);
+  rescore_dot_kernel<<<sm_count() * 8, 256, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, o, err);
   // threads per block so that the per-thread lists of K + 1 keys fit in 96 KiB
   int T = 128;
   while (T > 32 && (size_t)T * (K + 1) * 12 > 96 * 1024) T -= 32;
   const size_t smem = (size_t)T * (K + 1) * 12;
   e = cudaFuncSetAttribute(rescore_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  rescore_select_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, perm,
-                                                                           item_nrm_ub, n_items, K, o, out_idx, out_score,
-                                                                           stats, err);
+  rescore_select_kernel<<<(unsigned)((n_users + T - 1) / T), T, smem, s>>>(users, n_users, f, items_sorted, K, o,
+                                                                           out_idx, out_score, stats, err);
   rescore_warp_kernel<<<sm_count() * 2, kWarpsPerBlock * 32, 0, s>>>(users, f, items_sorted, perm, item_nrm_ub, n_items, K,
                                                              o.ovf_list, o.ovf_count, out_idx, out_score, stats,
                                                              err);

@@ -53,10 +53,10 @@ def test_noalloc_matches_topk_two_calls_in_a_row():
 
 
 def _max_users(n_items, f, K):
-    """Largest n_users the documented scratch rule admits (32 MiB; 4 KiB of
+    """Largest n_users the documented scratch rule admits (32 MiB; 5 KiB of
     counters and padding counted in full)."""
     cap = max(4 * K + 96, min(math.ceil(K * (2 + math.log(n_items / K))) + 96, n_items + 96))
-    return (32 * 2**20 - 8 * n_items - 4096) // (20 + 20 * cap)
+    return (32 * 2**20 - 8 * n_items - 5120) // (28 + 28 * cap)
 
 
 def test_noalloc_size_rule_is_the_documented_one():
