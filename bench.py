@@ -65,7 +65,9 @@ def parse(argv=None):
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--clusters", type=int, default=64, help="|C| when the autotuner is off")
     p.add_argument("--no-autotune", action="store_true",
-                   help="Maximus / selector: keep --clusters and the default block instead of mips_autotune")
+                   help="Maximus / selector: keep --clusters and --block-items instead of mips_autotune")
+    p.add_argument("--block-items", type=int, default=0,
+                   help="Maximus item block B when the autotuner is off (0: the library default)")
     p.add_argument("--legs", default="bmm,fp32,fp8,arms",
                    help="extra forms timed after the main steps on the same inputs: comma list of bmm (BF16 "
                         "blocked multiply), maximus, fp32 (FP32 CUDA-core blocked multiply), fp8 (the main method on an "
@@ -464,7 +466,8 @@ def main(argv=None):
     index = None
     for cand in (["bf16", "fp32"] if dtype == "auto" else [dtype]):
         try:
-            index = mips.build_index(I_d, clusters=args.clusters, dtype=cand, kmeans_spherical=args.kmeans_spherical)
+            index = mips.build_index(I_d, clusters=args.clusters, dtype=cand, kmeans_spherical=args.kmeans_spherical,
+                                     block_items=args.block_items)
             dtype = cand
             break
         except mips.MipsError as e:
