@@ -263,29 +263,67 @@ __global__ void normalize_rows_kernel(float* __restrict__ cent, int C, int f) {
 // subnormal squares make the computed cosine unreliable (the rescore scores
 // those users exhaustively whatever the walk did); a centroid that small
 // gives -1 (theta_b = pi).
-__global__ void cosb_kernel(const float* __restrict__ users, int64_t n_users, int f, const int32_t* __restrict__ assign,
-                            const float* __restrict__ cent, uint32_t* __restrict__ cosb_ord) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= n_users) return;
-  const int j = assign[u];
-  const float* ur = users + u * f;
-  const float* cr = cent + (int64_t)j * f;
-  float d = 0.f, su = 0.f, sc = 0.f;
-  for (int k = 0; k < f; ++k) {
-    d = __fmaf_rn(ur[k], cr[k], d);
-    su = __fmaf_rn(ur[k], ur[k], su);
-    sc = __fmaf_rn(cr[k], cr[k], sc);
+//
+// Eight lanes per user, four users per warp at a time: lane l of a group
+// sums elements l, l + 8, ... with FMA and three shuffle steps add the
+// group's partial sums (any summation order keeps each factor's relative
+// error below the (f + 2) 2^-24 the margin allows).  The rescore decides
+// "below 2^-100" from its own sequential sum, which can differ from this
+// one in the last bits; a user is left out here only below 2^-100 (1 -
+// 2^-8), so every user the rescore trusts is counted (one counted in
+// addition only lowers the minimum).  Each block keeps its members' minima
+// per cluster in shared memory (C <= kCosbShared) and sends one atomicMin
+// per cluster it met.
+constexpr int kCosbShared = 1024;
+
+__global__ void __launch_bounds__(256)
+    cosb_kernel(const float* __restrict__ users, int64_t n_users, int f, const int32_t* __restrict__ assign,
+                const float* __restrict__ cent, int C, uint32_t* __restrict__ cosb_ord) {
+  __shared__ uint32_t smin[kCosbShared];
+  const bool in_smem = C <= kCosbShared;
+  if (in_smem)
+    for (int j = threadIdx.x; j < C; j += blockDim.x) smin[j] = 0xffffffffu;  // (above every cosine's bits)
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u4 = warp * 4; u4 < n_users; u4 += n_warps * 4) {  // (warp-uniform: the shuffles need every lane)
+    const int64_t u = u4 + (lane >> 3);
+    const bool valid = u < n_users;
+    const int j = valid ? assign[u] : 0;
+    const float* ur = users + (valid ? u : 0) * f;
+    const float* cr = cent + (int64_t)j * f;
+    float d = 0.f, su = 0.f, sc = 0.f;
+    if (valid)
+      for (int k = sub; k < f; k += 8) {
+        const float x = ur[k], y = cr[k];
+        d = __fmaf_rn(x, y, d);
+        su = __fmaf_rn(x, x, su);
+        sc = __fmaf_rn(y, y, sc);
+      }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      d += __shfl_xor_sync(0xffffffffu, d, o);
+      su += __shfl_xor_sync(0xffffffffu, su, o);
+      sc += __shfl_xor_sync(0xffffffffu, sc, o);
+    }
+    if (!valid || sub != 0 || su < kTinySq * 0.99609375f) continue;
+    float c;
+    if (sc < kTinySq) {
+      c = -1.f;
+    } else {
+      // each factor carries a relative error below (f + 2) 2^-24; |cos| <= 1
+      c = __fdiv_rn(d, __fsqrt_rn(su) * __fsqrt_rn(sc)) - (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
+      c = fmaxf(c, -1.f);
+    }
+    if (in_smem) atomicMin(&smin[j], f2ord(c));
+    else atomicMin(cosb_ord + j, f2ord(c));
   }
-  if (su < kTinySq) return;
-  float c;
-  if (sc < kTinySq) {
-    c = -1.f;
-  } else {
-    // each factor carries a relative error below (f + 2) 2^-24; |cos| <= 1
-    c = __fdiv_rn(d, __fsqrt_rn(su) * __fsqrt_rn(sc)) - (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
-    c = fmaxf(c, -1.f);
+  if (in_smem) {
+    __syncthreads();
+    for (int j = threadIdx.x; j < C; j += blockDim.x)
+      if (smin[j] != 0xffffffffu) atomicMin(cosb_ord + j, smin[j]);
   }
-  atomicMin(cosb_ord + j, f2ord(c));
 }
 
 // CBound of every (cluster, item): key = float_desc_key(bound) (sorts
@@ -1127,7 +1165,10 @@ cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int
                            const float* items, const float* item_nrm, int64_t n_items, uint32_t* cosb_ord,
                            uint32_t* keys, int32_t* vals, float* cosb_f, cudaStream_t s, int* launches) {
   cosb_init_kernel<<<(C + 127) / 128, 128, 0, s>>>(cosb_ord, C);
-  cosb_kernel<<<(unsigned)((n_users + 255) / 256), 256, 0, s>>>(users, n_users, f, assign, cent, cosb_ord);
+  {  // four users per warp; at most 8 blocks of 256 threads per SM, fewer for small inputs
+    const int64_t blocks = std::min<int64_t>((n_users + 31) / 32, (int64_t)sm_count() * 8);
+    cosb_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(users, n_users, f, assign, cent, C, cosb_ord);
+  }
   const size_t smem = sizeof(float) * (cb_items_floats(f) + (size_t)f * kCbChunk + kCbChunk);
   cudaError_t e = cudaFuncSetAttribute(cbound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

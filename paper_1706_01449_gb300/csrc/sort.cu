@@ -8,8 +8,11 @@
 //
 // Each 8-bit pass is three kernels:
 //   hist    one block per (tile of 4096 elements, segment): digit counts;
-//   scan    one block per segment: exclusive scan over [digit][tile], so a
-//           digit's elements from earlier tiles come first;
+//   scan    in two steps, exclusive over [digit][tile] so that a digit's
+//           elements from earlier tiles come first: one warp per (segment,
+//           digit) row scans that digit's tile counts and keeps the row's
+//           total, then one block per segment scans its 256 totals into
+//           each digit's first output slot (the scatter adds the two);
 //   scatter one block per (tile, segment): 16 rounds of 256 consecutive
 //           elements; within a round each element's rank among equal digits
 //           comes from __match_any_sync inside its warp plus the counts of
@@ -38,52 +41,59 @@ __global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t n, 
   for (int d = threadIdx.x; d < kDigits; d += kThreads) hist[((int64_t)seg * kDigits + d) * nb + b] = h[d];
 }
 
-// In-place exclusive scan of the segment's [kDigits][nb] counts.
-__global__ void radix_scan_kernel(uint32_t* __restrict__ hist, int nb) {
-  __shared__ uint32_t warp_sums[32];
-  __shared__ uint32_t carry;
-  uint32_t* h = hist + (int64_t)blockIdx.x * kDigits * nb;
-  const int64_t total = (int64_t)kDigits * nb;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int64_t base = 0; base < total; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    const uint32_t v = i < total ? h[i] : 0;
+// Scan, step 1: warp per (segment, digit) row of nb tile counts, in place,
+// exclusive within the row; the row's total goes to totals[seg][digit].
+__global__ void radix_rowscan_kernel(uint32_t* __restrict__ hist, int nb, int n_rows, uint32_t* __restrict__ totals) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // seg * kDigits + digit
+  const int lane = threadIdx.x & 31;
+  if (row >= n_rows) return;
+  uint32_t* h = hist + (int64_t)row * nb;
+  uint32_t carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int b = b0 + lane;
+    const uint32_t v = b < nb ? h[b] : 0u;
     uint32_t x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane == 31) warp_sums[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      uint32_t s = lane < nw ? warp_sums[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += y;
-      }
-      if (lane < nw) warp_sums[lane] = s;
-    }
-    __syncthreads();
-    const uint32_t before = (w > 0 ? warp_sums[w - 1] : 0) + carry;
-    if (i < total) h[i] = before + x - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = before + x;
-    __syncthreads();
+    if (b < nb) h[b] = carry + x - v;
+    carry += __shfl_sync(0xffffffffu, x, 31);
   }
+  if (lane == 0) totals[row] = carry;
+}
+
+// Scan, step 2: block (kDigits threads) per segment, exclusive scan of the
+// digit totals in place: each digit's first output slot in the segment.
+__global__ void radix_digitscan_kernel(uint32_t* __restrict__ totals) {
+  __shared__ uint32_t warp_sums[kDigits / 32];
+  uint32_t* t = totals + (int64_t)blockIdx.x * kDigits;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t v = t[threadIdx.x];
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  uint32_t before = 0;
+  for (int ww = 0; ww < w; ++ww) before += warp_sums[ww];
+  t[threadIdx.x] = before + x - v;
 }
 
 __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
                                      uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n,
-                                     int shift, const uint32_t* __restrict__ offsets, int nb) {
+                                     int shift, const uint32_t* __restrict__ offsets, int nb,
+                                     const uint32_t* __restrict__ digit_base) {
   __shared__ uint32_t base[kDigits];                       // next output slot per digit
   __shared__ uint16_t warp_cnt[kThreads / 32][kDigits];    // this round's per-warp digit counts
   const int b = blockIdx.x, seg = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kDigits; d += kThreads) base[d] = offsets[((int64_t)seg * kDigits + d) * nb + b];
+  for (int d = threadIdx.x; d < kDigits; d += kThreads)
+    base[d] = digit_base[seg * kDigits + d] + offsets[((int64_t)seg * kDigits + d) * nb + b];
   const int64_t off = (int64_t)seg * n;
   const int64_t lo = (int64_t)b * kTile, hi = min(n, lo + kTile);
   for (int64_t r0 = lo; r0 < hi; r0 += kThreads) {
@@ -132,7 +142,7 @@ __global__ void float_desc_keys_kernel(const float* __restrict__ x, int64_t n, u
 
 size_t radix_sort_temp_bytes(int64_t n, int n_seg) {
   const int nb = (int)((n + kTile - 1) / kTile);
-  return sizeof(uint32_t) * (size_t)kDigits * nb * n_seg;
+  return sizeof(uint32_t) * (size_t)kDigits * (nb + 1) * n_seg;  // counts [seg][digit][tile], then totals [seg][digit]
 }
 
 cudaError_t radix_sort_pairs(uint32_t*& keys, int32_t*& vals, uint32_t*& keys_alt, int32_t*& vals_alt, int64_t n,
@@ -140,13 +150,16 @@ cudaError_t radix_sort_pairs(uint32_t*& keys, int32_t*& vals, uint32_t*& keys_al
   if (n <= 0 || n_seg <= 0) return cudaSuccess;
   const int nb = (int)((n + kTile - 1) / kTile);
   dim3 grid(nb, n_seg);
+  const int n_rows = n_seg * kDigits;
+  uint32_t* totals = temp + (size_t)n_rows * nb;
   for (int shift = begin_bit; shift < end_bit; shift += 8) {
     radix_hist_kernel<<<grid, kThreads, 0, s>>>(keys, n, shift, temp, nb);
-    radix_scan_kernel<<<n_seg, 1024, 0, s>>>(temp, nb);
-    radix_scatter_kernel<<<grid, kThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift, temp, nb);
+    radix_rowscan_kernel<<<(n_rows + 7) / 8, 256, 0, s>>>(temp, nb, n_rows, totals);
+    radix_digitscan_kernel<<<n_seg, kDigits, 0, s>>>(totals);
+    radix_scatter_kernel<<<grid, kThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, n, shift, temp, nb, totals);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (launches) *launches += 3;
+    if (launches) *launches += 4;
     uint32_t* tk = keys;
     keys = keys_alt;
     keys_alt = tk;
