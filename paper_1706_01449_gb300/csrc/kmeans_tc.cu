@@ -205,16 +205,25 @@ __global__ void __launch_bounds__(kKmWarps * 32, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
 }
 
-// Users as BF16 rows [u, 1, 0 ..] of fk elements.
+// Users as BF16 rows [u, 1, 0 ..] of fk elements: a thread per 8-element
+// chunk (one 16-byte store), a block per 256 / (fk / 8) whole rows, so the
+// row and chunk come from 32-bit arithmetic on the thread index.
 __global__ void km_users_bf16_kernel(const float* __restrict__ users, int64_t n, int f, int fk,
                                      __nv_bfloat16* __restrict__ out) {
-  const int64_t total = n * fk;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t u = e / fk;
-    const int k = (int)(e - u * fk);
-    const float x = k < f ? users[u * f + k] : (k == f ? 1.f : 0.f);
-    out[e] = __float2bfloat16_rn(x);
+  const int cpr = fk / 8;                        // chunks per row (fk is a multiple of 64)
+  const int rows_per_block = blockDim.x / cpr;
+  const int r = threadIdx.x / cpr, c = threadIdx.x - r * cpr;
+  if (r >= rows_per_block) return;
+  const int64_t u = (int64_t)blockIdx.x * rows_per_block + r;
+  if (u >= n) return;
+  const float* ur = users + u * f;
+  __align__(16) __nv_bfloat16 q[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = 8 * c + i;
+    q[i] = __float2bfloat16_rn(k < f ? ur[k] : (k == f ? 1.f : 0.f));
   }
+  reinterpret_cast<uint4*>(out + u * fk)[c] = *reinterpret_cast<const uint4*>(q);
 }
 
 // Centroids as BF16 rows [c_j, -||c_j||^2 / 2, 0 ..] (hn2 = ||c_j||^2 / 2).
@@ -245,7 +254,8 @@ bool km_tc_fits(int f, int C, int max_smem) {
 cudaError_t km_tc_users(const float* users, int64_t n_users, int f, uint16_t* users_km, cudaStream_t s) {
   if (n_users <= 0) return cudaSuccess;
   const int fk = km_tc_row_len(f);
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_users * fk + 255) / 256, (int64_t)sm_count() * 8));
+  const int rows_per_block = 256 / (fk / 8);  // fk <= 192 (f <= 128): at least 10 rows
+  const unsigned blocks = (unsigned)((n_users + rows_per_block - 1) / rows_per_block);
   km_users_bf16_kernel<<<blocks, 256, 0, s>>>(users, n_users, f, fk, (__nv_bfloat16*)users_km);
   return cudaGetLastError();
 }

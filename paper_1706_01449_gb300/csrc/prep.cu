@@ -91,46 +91,65 @@ __global__ void row_norm_ub_kernel(const float* __restrict__ x, int64_t n, int f
   }
 }
 
-// Rows per warp of the quantisation kernel: the loads of all of them are
-// issued before any row's arithmetic (f <= 128: four elements per lane).
+// Rows per warp of the FP8 quantisation kernel: the loads of all of them
+// are issued before any row's arithmetic (f <= 128: four elements per lane).
 constexpr int kQuantRows = 4;
 
-// One row whose elements this lane holds in v (element lane + 32 j in v[j]).
-__device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row, int64_t n, int f, int fp, int role,
-                                               __nv_bfloat16* __restrict__ out, float2* __restrict__ aux, int* err,
-                                               int lane) {
+// BF16 operand rows, eight lanes per row (a warp quantises four rows at
+// once; a whole warp per row spent most of its issue slots on the
+// per-row reductions): lane s of a row's group holds elements s, s + 8, ..
+// (up to 16 of them: f <= 128).  The sums are taken per lane and then over
+// the group by three shuffle steps; the norm bounds allow a relative error
+// of f 2^-24 for any order of summation.
+__global__ void __launch_bounds__(256)
+    quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role, __nv_bfloat16* __restrict__ out,
+                      int64_t n_rows_out, float2* __restrict__ aux, int* err) {
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  if (row >= n_rows_out) return;  // (whole groups: a group's lanes share the row)
+  const unsigned gm = 0xFFu << (lane & 24);  // this row's eight lanes
   __nv_bfloat16* o = out + row * fp;
   if (row >= n) {  // padding rows
-    for (int k = lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
+    for (int k = sub; k < fp; k += 8) o[k] = __float2bfloat16_rn(0.f);
     return;
+  }
+  const float* r = x + row * f;
+  float v[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int k = sub + 8 * j;
+    v[j] = k < f ? r[k] : 0.f;
   }
   float amax = 0.f;
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if (lane + 32 * j < f) amax = fmaxf(amax, fabsf(v[j]));
-  amax = warp_max(amax);
+  for (int j = 0; j < 16; ++j) amax = fmaxf(amax, fabsf(v[j]));
+#pragma unroll
+  for (int o2 = 4; o2 > 0; o2 >>= 1) amax = fmaxf(amax, __shfl_xor_sync(gm, amax, o2));
   // sums over the row scaled by 2^e (largest |entry| in [1/2, 1)); a
   // non-finite or zero row keeps e = 0 (the non-finite check below flags it)
   const int e = (amax > 0.f && isfinite(amax)) ? norm_scale_exp(amax) : 0;
   float ss_x = 0.f, ss_t = 0.f, ss_d = 0.f;
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int k = lane + 32 * j;
+  for (int j = 0; j < 16; ++j) {
+    const int k = sub + 8 * j;
     if (k < f) {
-      const float x = v[j];
-      const __nv_bfloat16 q = __float2bfloat16_rn(x);
+      const float xv = v[j];
+      const __nv_bfloat16 q = __float2bfloat16_rn(xv);
       const float t = __bfloat162float(q);
-      const float d = __fsub_rn(x, t);  // exact: t is x rounded to 8 significant bits
-      const float xs = scale_pow2(x, e), ts = scale_pow2(t, e), ds = scale_pow2(d, e);
+      const float d = __fsub_rn(xv, t);  // exact: t is xv rounded to 8 significant bits
+      const float xs = scale_pow2(xv, e), ts = scale_pow2(t, e), ds = scale_pow2(d, e);
       ss_x = __fmaf_rn(xs, xs, ss_x);
       ss_t = __fmaf_rn(ts, ts, ss_t);
       ss_d = __fmaf_rn(ds, ds, ss_d);
       o[k] = q;
     }
   }
-  ss_x = warp_sum(ss_x);
-  ss_t = warp_sum(ss_t);
-  ss_d = warp_sum(ss_d);
+#pragma unroll
+  for (int o2 = 4; o2 > 0; o2 >>= 1) {
+    ss_x += __shfl_xor_sync(gm, ss_x, o2);
+    ss_t += __shfl_xor_sync(gm, ss_t, o2);
+    ss_d += __shfl_xor_sync(gm, ss_d, o2);
+  }
   const float g = (float)(fp + 4) * 9.5367432e-07f + (float)f * 8.8817842e-16f;  // 2^-20, 2^-50
   // the zero row keeps 0 bounds (its scores are exactly 0); otherwise the
   // largest scaled square is at least 1/4, and the floor covers subnormal
@@ -140,12 +159,12 @@ __device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row,
     nhat = unscale_pow2_ru(fmaxf(norm_ub(ss_x + tiny_floor(f), f), norm_ub(ss_t + tiny_floor(f), f)), e);
     errn = unscale_pow2_ru(norm_ub(ss_d + tiny_floor(f), f), e);
   }
-  __nv_bfloat16 nhat_b = __float2bfloat16_ru(nhat);
-  __nv_bfloat16 eb_b = __float2bfloat16_ru(__fmul_ru(__fmaf_ru(g, nhat, errn), 1.0f + g));
-  if (lane == 0) {
+  const __nv_bfloat16 nhat_b = __float2bfloat16_ru(nhat);
+  const __nv_bfloat16 eb_b = __float2bfloat16_ru(__fmul_ru(__fmaf_ru(g, nhat, errn), 1.0f + g));
+  if (sub == 0) {
     if (!isfinite(ss_x) || !isfinite(__bfloat162float(nhat_b))) atomicOr(err, DEV_ERR_NONFINITE);
     if (role == 0) {
-      o[f] = eb_b;      // beta_u
+      o[f] = eb_b;        // beta_u
       o[f + 1] = nhat_b;  // nhat_u
       aux[row] = make_float2(__bfloat162float(eb_b), __bfloat162float(nhat_b));
     } else {
@@ -154,29 +173,7 @@ __device__ __forceinline__ void quant_bf16_row(const float (&v)[4], int64_t row,
       aux[row] = make_float2(__bfloat162float(nhat_b), __bfloat162float(eb_b));
     }
   }
-  for (int k = f + 2 + lane; k < fp; k += 32) o[k] = __float2bfloat16_rn(0.f);
-}
-
-// A warp per kQuantRows consecutive rows.
-__global__ void quant_bf16_kernel(const float* __restrict__ x, int64_t n, int f, int fp, int role,
-                                  __nv_bfloat16* __restrict__ out, int64_t n_rows_out,
-                                  float2* __restrict__ aux, int* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * kQuantRows;
-  if (row0 >= n_rows_out) return;
-  float v[kQuantRows][4];
-#pragma unroll
-  for (int q = 0; q < kQuantRows; ++q) {
-    const int64_t row = row0 + q;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = lane + 32 * j;
-      v[q][j] = (row < n && k < f) ? x[row * f + k] : 0.f;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < kQuantRows; ++q)
-    if (row0 + q < n_rows_out) quant_bf16_row(v[q], row0 + q, n, f, fp, role, out, aux, err, lane);
+  for (int k = f + 2 + sub; k < fp; k += 8) o[k] = __float2bfloat16_rn(0.f);
 }
 
 // ---------------------------------------------------------------- FP8 rows
@@ -411,8 +408,8 @@ void launch_row_norm_ub(const float* x, int64_t n, int f, float* nrm_ub, int* er
 void launch_quant_bf16(const float* x, int64_t n, int f, int fp, int role, void* out_bf16,
                        int64_t n_rows_out, float2* aux, int* err, cudaStream_t s) {
   if (n_rows_out <= 0) return;
-  const int64_t rows_per_block = 8 * kQuantRows;
-  quant_bf16_kernel<<<(unsigned)((n_rows_out + rows_per_block - 1) / rows_per_block), 8 * 32, 0, s>>>(
+  const int64_t rows_per_block = 256 / 8;  // eight lanes per row
+  quant_bf16_kernel<<<(unsigned)((n_rows_out + rows_per_block - 1) / rows_per_block), 256, 0, s>>>(
       x, n, f, fp, role, (__nv_bfloat16*)out_bf16, n_rows_out, aux, err);
 }
 
