@@ -393,7 +393,7 @@ def run_serve(args):
                       "saturated_requests_per_s": sat_rate, "loads": loads}), flush=True)
 
 
-def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk, workload):
+def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk, workload, walk_cfg=None):
     """Roofline of the call's dominant kernel from its counters: the fused
     score + select kernel (every (user, item) pair), or the Maximus walk
     (the pairs it scored).  Algorithmic bytes: user rows and item rows once
@@ -404,6 +404,8 @@ def score_roofline(dtype, walked, f, nU, nI, K, stats, peaks, peak_src, sm, clk,
     kms = stats["ms_kernel"] or (stats["ms_walk"] if walked else stats["ms_score"])
     kern = "tc_score_select" if dtype in ("bf16", "fp8") else ("fp32_score_select" if not walked else "maximus_walk")
     key = f"{kern}{' walk' if walked else ''} {dtype} {workload} f={f} K={K}"
+    if walked and walk_cfg:  # the walk's traffic depends on |C| and the item block
+        key += f" C={walk_cfg[0]} B={walk_cfg[1]}"
     src = (["tc_topk.cu", "tc_ptx.cuh", "tc_topk.h"] if dtype in ("bf16", "fp8")
            else ["fp32_topk.cu" if not walked else "maximus.cu"])
     return roofline(dtype, f, scores, kms, hbm, peaks, peak_src, sm, clk, key, src)
@@ -563,7 +565,8 @@ def main(argv=None):
         nU_sel = nU - last_report.get("sample_users", 0)
     else:
         nU_sel = nU
-    rl = score_roofline(dtype, walked, f, nU_sel, nI, K, st_main, peaks, peak_src, sm, clk, args.workload)
+    main_cfg = (stats.get("clusters"), tune["block_items"] if tune else (args.block_items or 4096))
+    rl = score_roofline(dtype, walked, f, nU_sel, nI, K, st_main, peaks, peak_src, sm, clk, args.workload, main_cfg)
     rl["launches_per_step"] = 2 if walked else 1
 
     # the other forms, same inputs, same run (one GPU only)
@@ -609,14 +612,16 @@ def main(argv=None):
         else:
             idx_l = index
             l_method, l_dtype, l_graph, n_warm = leg, dtype, use_graph, 2
+        l_block = args.block_items or 4096
         if l_method == "maximus" and leg != "fp32" and not args.no_autotune:
-            mips.autotune(idx_l, U_d, K, stream=stream)
+            l_block = mips.autotune(idx_l, U_d, K, stream=stream)["block_items"]
         lstep = make_step(idx_l, l_method, oi, osc, l_graph)
         lms, lkms, _, lst = timed_steps(lstep, n_warm, args.leg_steps, stream, flush, idx_l, mips)
         lst = dict(lst)
         lst["ms_kernel"] = statistics.mean(lkms)
         l_walk = l_method == "maximus"
-        lrl = score_roofline(l_dtype, l_walk, f, nU, nI, K, lst, peaks, peak_src, sm, clk, args.workload)
+        lrl = score_roofline(l_dtype, l_walk, f, nU, nI, K, lst, peaks, peak_src, sm, clk, args.workload,
+                             (lst.get("clusters"), l_block))
         legs[leg] = {"value": nU / (statistics.mean(lms) / 1e3), "unit": "users/s", "ms_per_step": statistics.mean(lms),
                      "steps": args.leg_steps, "warmup": n_warm, "candidate_pass": l_dtype, "method": l_method,
                      "candidates_per_user": lst.get("cand_emitted", 0) / nU, "rescored_per_user":
