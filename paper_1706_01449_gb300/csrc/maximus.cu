@@ -173,57 +173,65 @@ __global__ void kmeans_accum_smem_kernel(const float* __restrict__ users, int64_
     if (km_cnt[e]) atomicAdd(&counts[j0 + e], km_cnt[e]);
 }
 
-// The same sums with warp-private partial sums: warp w of the block owns
-// rows [C][f] (and counts [C]) of shared memory, lane l adds dimensions l,
-// l + 32, .. of each of the warp's users to its cluster's row with plain
-// adds (one lane per address, users in order), then the block sums its
-// warps' copies and adds each (cluster, dimension) to the global sums once.
+// The same sums with partial sums private to a group of G = ceil(f / 32)
+// warps: group c of the block owns rows [C][f] (and counts [C]) of shared
+// memory, and its warp g adds dimensions 32 g + lane of each of the group's
+// users to its cluster's row with plain adds (one lane per address, users in
+// order; the G warps of a group touch disjoint dimensions, so they need no
+// atomics); then the block sums its groups' copies and adds each (cluster,
+// dimension) to the global sums once.  One copy per G warps instead of one
+// per warp: the copies are what limits the warps an SM holds.
 // Integer sums: the same result as kmeans_accum_kernel in any order.
 __global__ void kmeans_accum_warp_kernel(const float* __restrict__ users, int64_t n_users, int f,
                                          const int32_t* __restrict__ assign, int C, const float* __restrict__ scale,
-                                         unsigned long long* __restrict__ sums, unsigned int* __restrict__ counts) {
-  extern __shared__ unsigned long long kw_acc[];  // [warps][C][f]
-  const int nwb = blockDim.x / 32;
+                                         unsigned long long* __restrict__ sums, unsigned int* __restrict__ counts,
+                                         int G) {
+  extern __shared__ unsigned long long kw_acc[];  // [groups][C][f]
+  const int ngb = (blockDim.x / 32) / G;          // groups per block
   const int64_t cf = (int64_t)C * f;
-  unsigned int* kw_cnt = (unsigned int*)(kw_acc + nwb * cf);  // [warps][C]
-  for (int64_t e = threadIdx.x; e < nwb * cf; e += blockDim.x) kw_acc[e] = 0ull;
-  for (int e = threadIdx.x; e < nwb * C; e += blockDim.x) kw_cnt[e] = 0u;
+  unsigned int* kw_cnt = (unsigned int*)(kw_acc + ngb * cf);  // [groups][C]
+  for (int64_t e = threadIdx.x; e < ngb * cf; e += blockDim.x) kw_acc[e] = 0ull;
+  for (int e = threadIdx.x; e < ngb * C; e += blockDim.x) kw_cnt[e] = 0u;
   __syncthreads();
   const int w = threadIdx.x / 32, lane = threadIdx.x & 31;
-  unsigned long long* acc = kw_acc + w * cf;
-  unsigned int* cnt = kw_cnt + w * C;
+  const int grp = w / G, gk = w - grp * G;
+  const int k = 32 * gk + lane;  // this lane's dimension
+  unsigned long long* acc = kw_acc + grp * cf;
+  unsigned int* cnt = kw_cnt + grp * C;
   const float sc = scale[0];
-  // each warp takes 8 consecutive users at a time: their cluster ids and
+  // each group takes 8 consecutive users at a time: their cluster ids and
   // row values are loaded before any add, so the loads overlap
   constexpr int kU = 8;
-  const int64_t step = (int64_t)gridDim.x * nwb * kU;
-  for (int64_t u0 = ((int64_t)blockIdx.x * nwb + w) * kU; u0 < n_users; u0 += step) {
-    int j[kU];
+  const int64_t step = (int64_t)gridDim.x * ngb * kU;
+  if (grp < ngb) {
+    for (int64_t u0 = ((int64_t)blockIdx.x * ngb + grp) * kU; u0 < n_users; u0 += step) {
+      int j[kU];
 #pragma unroll
-    for (int r = 0; r < kU; ++r) j[r] = u0 + r < n_users ? assign[u0 + r] : -1;
-    for (int k = lane; k < f; k += 32) {
-      float x[kU];
+      for (int r = 0; r < kU; ++r) j[r] = u0 + r < n_users ? assign[u0 + r] : -1;
+      if (k < f) {
+        float x[kU];
 #pragma unroll
-      for (int r = 0; r < kU; ++r) x[r] = j[r] >= 0 ? users[(u0 + r) * f + k] : 0.f;
+        for (int r = 0; r < kU; ++r) x[r] = j[r] >= 0 ? users[(u0 + r) * f + k] : 0.f;
 #pragma unroll
-      for (int r = 0; r < kU; ++r)
-        if (j[r] >= 0) acc[(int64_t)j[r] * f + k] += (unsigned long long)__float2ll_rn(x[r] * sc);
-    }
-    if (lane == 0) {
+        for (int r = 0; r < kU; ++r)
+          if (j[r] >= 0) acc[(int64_t)j[r] * f + k] += (unsigned long long)__float2ll_rn(x[r] * sc);
+      }
+      if (gk == 0 && lane == 0) {
 #pragma unroll
-      for (int r = 0; r < kU; ++r)
-        if (j[r] >= 0) cnt[j[r]] += 1u;
+        for (int r = 0; r < kU; ++r)
+          if (j[r] >= 0) cnt[j[r]] += 1u;
+      }
     }
   }
   __syncthreads();
   for (int64_t e = threadIdx.x; e < cf; e += blockDim.x) {
     unsigned long long t = 0ull;
-    for (int ww = 0; ww < nwb; ++ww) t += kw_acc[ww * cf + e];
+    for (int gg = 0; gg < ngb; ++gg) t += kw_acc[gg * cf + e];
     if (t) atomicAdd(&sums[e], t);
   }
   for (int e = threadIdx.x; e < C; e += blockDim.x) {
     unsigned int t = 0u;
-    for (int ww = 0; ww < nwb; ++ww) t += kw_cnt[ww * C + e];
+    for (int gg = 0; gg < ngb; ++gg) t += kw_cnt[gg * C + e];
     if (t) atomicAdd(&counts[e], t);
   }
 }
@@ -1125,21 +1133,23 @@ cudaError_t maximus_kmeans(const float* users, int64_t n_users, int f, int C, in
     e = cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * C * f, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, sizeof(unsigned int) * C, s);
     if (e != cudaSuccess) return e;
-    // warp-private partial sums of 8, 4 or 2 warps per block, when they fit
+    // partial sums private to groups of G = ceil(f / 32) warps (each warp a
+    // 32-dimension slice): 8, 4 or 2 groups per block, when they fit
     int max_smem = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t per_warp = (size_t)C * f * 8 + (size_t)C * 4;
-    int nwb = 8;
-    while (nwb >= 2 && (size_t)nwb * per_warp > (size_t)max_smem) nwb /= 2;
-    if (nwb >= 2) {
-      const size_t smem = (size_t)nwb * per_warp;
+    const int G = (f + 31) / 32;
+    const size_t per_group = (size_t)C * f * 8 + (size_t)C * 4;
+    int ngb = std::max(1, 8 / G);  // groups per block: at most 8 warps (f <= 32: one warp per group)
+    while (ngb >= 2 && (size_t)ngb * per_group > (size_t)max_smem) ngb /= 2;
+    if (ngb >= 2 || (ngb == 1 && G > 1 && per_group <= (size_t)max_smem)) {
+      const size_t smem = (size_t)ngb * per_group;
       e = cudaFuncSetAttribute(kmeans_accum_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      const int per_sm = std::max<int>(1, (int)((size_t)max_smem / smem));
+      const int per_sm = std::max<int>(1, (int)((size_t)228 * 1024 / (smem + 1024)));
       const unsigned bx = (unsigned)std::max<int64_t>(
-          1, std::min<int64_t>((n_users + 8 * nwb - 1) / (8 * nwb), (int64_t)sm_count() * std::min(per_sm, 4)));
-      kmeans_accum_warp_kernel<<<bx, nwb * 32, smem, s>>>(users, n_users, f, assign, C, scale, sums, counts);
+          1, std::min<int64_t>((n_users + 8 * ngb - 1) / (8 * ngb), (int64_t)sm_count() * std::min(per_sm, 8)));
+      kmeans_accum_warp_kernel<<<bx, ngb * G * 32, smem, s>>>(users, n_users, f, assign, C, scale, sums, counts, G);
     } else if ((size_t)C * f * 8 + (size_t)C * 4 <= 96 * 1024) {
       // all partial sums fit one block's shared memory
       const size_t smem = (size_t)C * f * 8 + (size_t)C * 4;
