@@ -347,21 +347,24 @@ __host__ __device__ __forceinline__ size_t cb_items_floats(int f) {  // rounded 
 }
 
 // ni: the item's norm bound from row_norm_ub_kernel (power-of-two scaled
-// sums, valid at any magnitude; 0 only for the zero item).
-__device__ __forceinline__ float cbound_value(float d, float sc, float si, float ni, float y, int f) {
+// sums, valid at any magnitude; 0 only for the zero item).  rsc = sqrt(sc),
+// rsi = sqrt(si) and sy = sqrt((1 - y)(1 + y)) depend only on the centroid
+// or only on the item, so the caller computes them once (the same roundings
+// as computing them here).
+__device__ __forceinline__ float cbound_value(float d, float sc, float si, float ni, float y, int f, float rsc,
+                                              float rsi, float sy) {
   float g;
   if (ni == 0.f) {
     g = 0.f;  // zero item: bound 0 = its score
   } else if (sc < kTinySq || si < kTinySq || y <= -1.f) {
     g = 1.f;  // theta_b = pi, or a cosine FP32 cannot evaluate reliably: no pruning
   } else {
-    float x = __fdiv_rn(d, __fsqrt_rn(sc) * __fsqrt_rn(si)) + (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
+    float x = __fdiv_rn(d, rsc * rsi) + (float)(2 * f + 8) * 5.9604645e-08f * 2.f;
     x = fminf(x, 1.f);
     if (x >= y) {
       g = 1.f;
     } else {
       const float sx = __fsqrt_rn((1.f - x) * (1.f + x));
-      const float sy = __fsqrt_rn((1.f - y) * (1.f + y));
       g = fminf(1.f, __fmaf_rn(x, y, sx * sy) + 9.5367432e-07f);  // + 2^-20
     }
   }
@@ -377,7 +380,10 @@ __global__ void __launch_bounds__(kCbItems)
   extern __shared__ __align__(16) float cb_smem[];
   float* it = cb_smem;                                  // [f][kCbItems + 1]
   float* ct = it + cb_items_floats(f);                  // [f][kCbChunk], 16-byte aligned
-  float* cn2 = ct + (size_t)f * kCbChunk;               // [kCbChunk]
+  float* cn2 = ct + (size_t)f * kCbChunk;               // [kCbChunk] ||c||^2
+  float* crs = cn2 + kCbChunk;                          // [kCbChunk] sqrt(||c||^2)
+  float* cy = crs + kCbChunk;                           // [kCbChunk] cos_b of the centroid's cluster
+  float* csy = cy + kCbChunk;                           // [kCbChunk] sqrt((1 - y)(1 + y))
   const int t = threadIdx.x;
   const int64_t i0 = (int64_t)blockIdx.x * kCbItems;
   const int j0 = blockIdx.y * kCbChunk;
@@ -396,9 +402,14 @@ __global__ void __launch_bounds__(kCbItems)
     float sc = 0.f;
     for (int k = 0; k < f; ++k) sc = __fmaf_rn(ct[k * kCbChunk + t], ct[k * kCbChunk + t], sc);
     cn2[t] = sc;
+    crs[t] = __fsqrt_rn(sc);
+    const float y = t < nc ? ord2f(cosb_ord[j0 + t]) : 1.f;
+    cy[t] = y;
+    csy[t] = __fsqrt_rn((1.f - y) * (1.f + y));
   }
   float si = 0.f;
   for (int k = 0; k < f; ++k) si = __fmaf_rn(it[k * (kCbItems + 1) + t], it[k * (kCbItems + 1) + t], si);
+  const float rsi = __fsqrt_rn(si);
   __syncthreads();
   if (t >= rows) return;
   const int64_t i = i0 + t;
@@ -422,9 +433,9 @@ __global__ void __launch_bounds__(kCbItems)
     for (int q = 0; q < 8; ++q) {
       if (jj + q < nc) {
         const int j = j0 + jj + q;
-        const float y = ord2f(cosb_ord[j]);
         const int64_t o = (int64_t)j * n_items + i;
-        keys[o] = float_desc_key(cbound_value(d[q], cn2[jj + q], si, ni, y, f));
+        keys[o] = float_desc_key(
+            cbound_value(d[q], cn2[jj + q], si, ni, cy[jj + q], f, crs[jj + q], rsi, csy[jj + q]));
         vals[o] = (int32_t)i;
       }
     }
@@ -1179,7 +1190,7 @@ cudaError_t maximus_bounds(const float* users, int64_t n_users, int f, const int
     const int64_t blocks = std::min<int64_t>((n_users + 31) / 32, (int64_t)sm_count() * 8);
     cosb_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(users, n_users, f, assign, cent, C, cosb_ord);
   }
-  const size_t smem = sizeof(float) * (cb_items_floats(f) + (size_t)f * kCbChunk + kCbChunk);
+  const size_t smem = sizeof(float) * (cb_items_floats(f) + (size_t)f * kCbChunk + 4 * kCbChunk);
   cudaError_t e = cudaFuncSetAttribute(cbound_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((n_items + kCbItems - 1) / kCbItems), (unsigned)((C + kCbChunk - 1) / kCbChunk));

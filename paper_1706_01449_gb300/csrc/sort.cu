@@ -96,9 +96,11 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const
     base[d] = digit_base[seg * kDigits + d] + offsets[((int64_t)seg * kDigits + d) * nb + b];
   const int64_t off = (int64_t)seg * n;
   const int64_t lo = (int64_t)b * kTile, hi = min(n, lo + kTile);
+  // the per-warp counts start at zero; after each round the lanes that set
+  // an entry clear it again, so no round clears the whole array
+  for (int e = threadIdx.x; e < (kThreads / 32) * kDigits; e += kThreads) (&warp_cnt[0][0])[e] = 0;
+  __syncthreads();
   for (int64_t r0 = lo; r0 < hi; r0 += kThreads) {
-    for (int e = threadIdx.x; e < (kThreads / 32) * kDigits; e += kThreads) (&warp_cnt[0][0])[e] = 0;
-    __syncthreads();
     const int64_t i = r0 + threadIdx.x;
     const bool live = i < hi;
     uint32_t key = 0;
@@ -127,6 +129,8 @@ __global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const
       base[dd] += t;
     }
     __syncthreads();
+    if (live && rank == 0) warp_cnt[w][d] = 0;  // (read by all above)
+    __syncwarp();  // the warp's next-round counts land after its resets
   }
 }
 
