@@ -13,10 +13,11 @@
 //           digit) row scans that digit's tile counts and keeps the row's
 //           total, then one block per segment scans its 256 totals into
 //           each digit's first output slot (the scatter adds the two);
-//   scatter one block per (tile, segment): 16 rounds of 256 consecutive
-//           elements; within a round each element's rank among equal digits
-//           comes from __match_any_sync inside its warp plus the counts of
-//           the warps before it, so the order of equal digits is kept.
+//   scatter one block per (tile, segment): a stable sort of the tile by
+//           digit in shared memory (each warp ranks a contiguous eighth of
+//           the tile with __match_any_sync and its own digit counters, so
+//           the order of equal digits is kept), then the sorted tile goes
+//           out in runs of equal digits, each contiguous in the output.
 #include "internal.h"
 
 namespace mips {
@@ -84,53 +85,100 @@ __global__ void radix_digitscan_kernel(uint32_t* __restrict__ totals) {
   t[threadIdx.x] = before + x - v;
 }
 
-__global__ void radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
-                                     uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n,
-                                     int shift, const uint32_t* __restrict__ offsets, int nb,
-                                     const uint32_t* __restrict__ digit_base) {
-  __shared__ uint32_t base[kDigits];                       // next output slot per digit
-  __shared__ uint16_t warp_cnt[kThreads / 32][kDigits];    // this round's per-warp digit counts
+// Scatter of one tile of kTile elements: a stable local sort by digit in
+// shared memory, then the copy out.  Warp w owns elements [512 w, 512 w +
+// 512) of the tile (lane l: 512 w + 32 r + l, r = 0..15) and ranks them in
+// order with __match_any_sync and warp-private digit counters (no block
+// barrier); the counters, summed over the warps in order, give every warp
+// its first slot per digit.  The sorted tile holds keys and tile indices;
+// the copy out reads each value by its index (the tile's values are a
+// 16 KB range) and writes runs of equal digits, each contiguous in the
+// output, instead of one element per 32-byte sector.
+constexpr int kScatterWarps = kThreads / 32;
+constexpr int kPerWarp = kTile / kScatterWarps;  // 512
+static_assert(kThreads == kDigits, "the scatter's digit pass runs a thread per digit");
+
+__global__ void __launch_bounds__(kThreads, 3)
+    radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+                         uint32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out, int64_t n, int shift,
+                         const uint32_t* __restrict__ offsets, int nb, const uint32_t* __restrict__ digit_base) {
+  __shared__ uint32_t skeys[kTile];
+  __shared__ uint16_t sidx[kTile];
+  __shared__ uint16_t srank[16][kThreads];          // each element's rank among its warp's equal digits
+  __shared__ uint32_t cnt[kScatterWarps][kDigits];  // counts, then each warp's first tile slot per digit
+  __shared__ uint32_t lbase[kDigits];               // the digit's first slot in the sorted tile
+  __shared__ uint32_t gbase[kDigits];               // the digit's first output slot of this tile
+  __shared__ uint32_t wsum[kScatterWarps];
   const int b = blockIdx.x, seg = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int d = threadIdx.x; d < kDigits; d += kThreads)
-    base[d] = digit_base[seg * kDigits + d] + offsets[((int64_t)seg * kDigits + d) * nb + b];
   const int64_t off = (int64_t)seg * n;
-  const int64_t lo = (int64_t)b * kTile, hi = min(n, lo + kTile);
-  // the per-warp counts start at zero; after each round the lanes that set
-  // an entry clear it again, so no round clears the whole array
-  for (int e = threadIdx.x; e < (kThreads / 32) * kDigits; e += kThreads) (&warp_cnt[0][0])[e] = 0;
-  __syncthreads();
-  for (int64_t r0 = lo; r0 < hi; r0 += kThreads) {
-    const int64_t i = r0 + threadIdx.x;
-    const bool live = i < hi;
-    uint32_t key = 0;
-    int32_t val = 0;
-    uint32_t d = kDigits;  // dead lanes get a digit of their own
-    if (live) {
-      key = keys_in[off + i];
-      val = vals_in[off + i];
-      d = (key >> shift) & 0xFF;
-    }
+  const int64_t lo = (int64_t)b * kTile;
+  const int len = (int)min((int64_t)kTile, n - lo);
+  for (int d = lane; d < kDigits; d += 32) cnt[w][d] = 0u;
+  __syncwarp();
+  uint32_t key[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = w * kPerWarp + 32 * r + lane;
+    const bool live = i < len;
+    key[r] = live ? keys_in[off + lo + i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = w * kPerWarp + 32 * r + lane;
+    const bool live = i < len;
+    const uint32_t d = live ? (key[r] >> shift) & 0xFFu : (uint32_t)kDigits;  // dead lanes: a digit of their own
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(peers & ((1u << lane) - 1));
-    if (live && rank == 0) warp_cnt[w][d] = (uint16_t)__popc(peers);
-    __syncthreads();
-    if (live) {
-      uint32_t before = 0;
-      for (int ww = 0; ww < w; ++ww) before += warp_cnt[ww][d];
-      const uint32_t pos = base[d] + before + rank;
-      keys_out[off + pos] = key;
-      vals_out[off + pos] = val;
+    const unsigned below = peers & ((1u << lane) - 1u);
+    const uint32_t before = live ? cnt[w][d] : 0u;  // this warp's earlier elements of digit d
+    srank[r][threadIdx.x] = (uint16_t)(before + __popc(below));
+    __syncwarp();
+    if (live && below == 0u) cnt[w][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // thread d: the tile's count of digit d, an exclusive scan over the digits,
+  // then the warps' first slots in warp order
+  const int d = threadIdx.x;
+  uint32_t tc = 0;
+#pragma unroll
+  for (int ww = 0; ww < kScatterWarps; ++ww) tc += cnt[ww][d];
+  uint32_t x = tc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  uint32_t lb = x - tc;
+  for (int ww = 0; ww < w; ++ww) lb += wsum[ww];
+  lbase[d] = lb;
+  gbase[d] = digit_base[seg * kDigits + d] + offsets[((int64_t)seg * kDigits + d) * nb + b];
+  uint32_t run = lb;
+#pragma unroll
+  for (int ww = 0; ww < kScatterWarps; ++ww) {
+    const uint32_t c = cnt[ww][d];
+    cnt[ww][d] = run;
+    run += c;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int i = w * kPerWarp + 32 * r + lane;
+    if (i < len) {
+      const uint32_t pos = cnt[w][(key[r] >> shift) & 0xFFu] + srank[r][threadIdx.x];
+      skeys[pos] = key[r];
+      sidx[pos] = (uint16_t)i;
     }
-    __syncthreads();
-    for (int dd = threadIdx.x; dd < kDigits; dd += kThreads) {
-      uint32_t t = 0;
-      for (int ww = 0; ww < kThreads / 32; ++ww) t += warp_cnt[ww][dd];
-      base[dd] += t;
-    }
-    __syncthreads();
-    if (live && rank == 0) warp_cnt[w][d] = 0;  // (read by all above)
-    __syncwarp();  // the warp's next-round counts land after its resets
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < len; p += kThreads) {
+    const uint32_t k = skeys[p];
+    const uint32_t dd = (k >> shift) & 0xFFu;
+    const int64_t q = off + (int64_t)(gbase[dd] + ((uint32_t)p - lbase[dd]));
+    keys_out[q] = k;
+    vals_out[q] = vals_in[off + lo + sidx[p]];
   }
 }
 
