@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(256)
 // ([f][32], read eight at a time); every dot product, item norm and
 // centroid norm is summed sequentially over k with FMA.
 constexpr int kCbItems = 128, kCbChunk = 32;
+static_assert(kCbChunk % 16 == 0, "the CBound kernel takes sixteen centroids at a time");
 
 __host__ __device__ __forceinline__ size_t cb_items_floats(int f) {  // rounded to 4 floats (float4 reads after it)
   return ((size_t)f * (kCbItems + 1) + 3) & ~(size_t)3;
@@ -414,23 +415,23 @@ __global__ void __launch_bounds__(kCbItems)
   if (t >= rows) return;
   const int64_t i = i0 + t;
   const float ni = item_nrm[i];
-  for (int jj = 0; jj < nc; jj += 8) {  // eight centroids at a time: eight independent sums
-    float d[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int jj = 0; jj < nc; jj += 16) {  // sixteen centroids at a time: sixteen independent sums
+    float d[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) d[q] = 0.f;
     for (int k = 0; k < f; ++k) {
       const float v = it[k * (kCbItems + 1) + t];
-      const float4 ca = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj);
-      const float4 cb = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj + 4);
-      d[0] = __fmaf_rn(ca.x, v, d[0]);
-      d[1] = __fmaf_rn(ca.y, v, d[1]);
-      d[2] = __fmaf_rn(ca.z, v, d[2]);
-      d[3] = __fmaf_rn(ca.w, v, d[3]);
-      d[4] = __fmaf_rn(cb.x, v, d[4]);
-      d[5] = __fmaf_rn(cb.y, v, d[5]);
-      d[6] = __fmaf_rn(cb.z, v, d[6]);
-      d[7] = __fmaf_rn(cb.w, v, d[7]);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const float4 c4 = *reinterpret_cast<const float4*>(ct + k * kCbChunk + jj + 4 * h);
+        d[4 * h + 0] = __fmaf_rn(c4.x, v, d[4 * h + 0]);
+        d[4 * h + 1] = __fmaf_rn(c4.y, v, d[4 * h + 1]);
+        d[4 * h + 2] = __fmaf_rn(c4.z, v, d[4 * h + 2]);
+        d[4 * h + 3] = __fmaf_rn(c4.w, v, d[4 * h + 3]);
+      }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 16; ++q) {
       if (jj + q < nc) {
         const int j = j0 + jj + q;
         const int64_t o = (int64_t)j * n_items + i;
