@@ -40,6 +40,23 @@ def test_traffic_record_follows_the_kernel_source():
     assert b.traffic_for("no such kernel", d[key]["source_hash"]) is None
 
 
+def test_walk_traffic_is_keyed_on_clusters_and_block():
+    # a walk's DRAM traffic depends on |C| and the item block: the record of
+    # one configuration is not reported for another
+    b = load_bench()
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        d = json.load(fh)
+    stats = {"pairs_scored": 10 ** 9, "cand_emitted": 10 ** 6, "ms_kernel": 5.0}
+    args = ("bf16", True, 51, 10 ** 6, 624961, 10, stats, PEAKS, "measured", 152, 2070.0, "kdd-1000000x624961")
+    key = "tc_score_select walk bf16 kdd-1000000x624961 f=51 K=10 C=32 B=1024"
+    assert key in d
+    r = b.score_roofline(*args, (32, 1024))
+    if d[key]["source_hash"] == b.kernel_source_hash(["tc_topk.cu", "tc_ptx.cuh", "tc_topk.h"]):
+        assert r["traffic"] == d[key]["bytes_per_launch"]
+    assert b.score_roofline(*args, (1024, 1024))["traffic"] is None
+    assert b.score_roofline(*args, (32, 4096))["traffic"] is None
+
+
 def test_reference_arm_prints_one_json_line():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                           "--warmup", "0", "--workload", "small-2048x1024-f32"],
