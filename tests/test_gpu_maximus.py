@@ -103,9 +103,14 @@ def test_maximus_prunes_on_clustered_users(dtype, block):
     assert b["visited"].mean() < 0.5 * I.shape[0]
 
 
-def test_kmeans_invariants():
-    U, I = clustered(2500, 300, 8, seed=3)
-    _, _, _, b, _, _ = run_maximus(U, I, 3, 12)
+@pytest.mark.parametrize("f,dtype", [(8, "fp32"), (51, "bf16"), (70, "bf16"), (100, "fp32")])
+def test_kmeans_invariants(f, dtype):
+    # f = 8, 51, 70, 100: the centroid sums run in groups of 1, 2, 3 and 4
+    # warps (one warp per 32 dimensions); every final centroid is its
+    # members' mean, and the answer stays exact
+    U, I = clustered(2500, 300, f, seed=3)
+    idx, sc, _, b, _, _ = run_maximus(U, I, 3, 12, dtype=dtype)
+    check_against_oracle(U, I, 3, idx, sc)
     U64, cent = U.astype(np.float64), b["centroids"].astype(np.float64)
     d = ((U64[:, None, :] - cent[None, :, :]) ** 2).sum(-1)
     a = b["assign"]
